@@ -1,0 +1,138 @@
+/*
+ * kx.h -- C ABI of the GB300-native chemistry source-term library.
+ *
+ * The library evaluates, for one reaction mechanism and a batch of
+ * thermochemical states (T, p, Y_k), the quantities of the KinetiX method
+ * (arXiv 2411.02640, Appendix A): net species production rates
+ * (Sec. A.2), mixture heat capacity and enthalpy (Sec. A.1) and
+ * mixture-averaged transport properties (Sec. A.3.5).  kx_load_mechanism
+ * reads a mechanism file, emits CUDA C++ specialised to that mechanism
+ * (constants as immediates, reaction loops fully unrolled) and compiles it
+ * for sm_103a with NVRTC; the other calls launch the compiled kernels.
+ *
+ * Conventions shared by every call below:
+ *   - Every array argument is a DEVICE pointer to float64 data that the
+ *     caller owns and keeps alive until the stream work completes.  State
+ *     arrays are structure-of-arrays: T[n] in K, p[n] in Pa and Y[N_s][ld]
+ *     (species-major, mass fractions, point index contiguous, ld >= n).
+ *     Per-species outputs use the same [N_s][ld] layout.
+ *   - Units are SI with kmol: W in kg/kmol, concentrations in kmol/m^3,
+ *     production rates in kmol/(m^3 s).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) and return after enqueueing; a launch failure is
+ *     returned at once.  n == 0 is a no-op that returns KX_OK.
+ *   - Y need not be normalised: concentrations use
+ *     C_k = (p/(R T)) (Y_k/W_k) / sum_j (Y_j/W_j).
+ *   - A point with T <= 0, p <= 0 or a non-finite T or p gets NaN in every
+ *     output; nothing traps.  Non-finite Y propagates as NaN.
+ *   - A handle may be used from several host threads and streams at once.
+ *   - Errors: every call returns a kx_status; kx_last_error() gives a
+ *     message for the calling thread's last failure.
+ */
+#ifndef KX_H
+#define KX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kx_mech* kx_handle;
+
+typedef enum {
+  KX_OK = 0,
+  KX_ERR_IO = 1,            /* mechanism file cannot be read */
+  KX_ERR_PARSE = 2,         /* malformed mechanism file */
+  KX_ERR_UNBALANCED = 3,    /* a reaction does not conserve atoms */
+  KX_ERR_ARG = 4,           /* null pointer, bad size or bad option */
+  KX_ERR_OOM = 5,           /* host or device allocation failed */
+  KX_ERR_COMPILE = 6,       /* NVRTC failed on the emitted source */
+  KX_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  KX_ERR_TIMEOUT = 8,       /* a host-side wait ran past its deadline */
+  KX_ERR_NONFINITE_INPUT = 9,
+  KX_ERR_UNSUPPORTED = 10   /* feature not available for this mechanism */
+} kx_status;
+
+typedef enum {
+  KX_FP64 = 0,   /* every operation in float64 */
+  KX_MIXED = 1   /* float32 bulk arithmetic; float64 for the Gibbs sums of
+                    ln K_c, the forward-minus-reverse difference and the
+                    production-rate accumulation (production rates); float32
+                    mixing rules (transport) */
+} kx_precision;
+
+/* Load options; a zero-initialised struct (or NULL) selects the defaults. */
+typedef struct {
+  int diff_mode;      /* 0 default (symmetric), 1 symmetric D_kj pairs, 2 full matrix */
+  int kc_mode;        /* 0 default (log space: k_r = exp(ln k_f - ln K_c)),
+                         1 per-species exp(-G_k/RT) products, one division per reaction */
+  int maxrreg;        /* register cap per thread for the generated kernels; 0 = compiler choice */
+  int block;          /* threads per block; 0 = 128 */
+  int lazy;           /* 0: compile every kernel at load (in parallel); 1: on first use */
+  int verbose;        /* 1: print compile times and register/spill counts to stderr */
+  const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
+} kx_options;
+
+/* Parse, validate and compile a mechanism (file format KXMECH 1).  On
+ * success *out owns the mechanism; free it with kx_free_mechanism. */
+kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* out);
+
+/* Release a handle.  The caller must have synchronised every stream that
+ * still has work of this handle in flight. */
+kx_status kx_free_mechanism(kx_handle h);
+
+/* Species and reaction counts; W (may be NULL) receives N_s molecular
+ * weights in kg/kmol. */
+kx_status kx_mechanism_info(kx_handle h, int* n_species, int* n_reactions, double* W);
+
+/* Net production rates wdot[N_s][ld] (Sec. A.2: Eq. (arrhenius), third-body
+ * and falloff modifiers Eq. (c_i) and (blend), Eq. (K_p), Eq. (r_i) and the
+ * stoichiometric sum wdot_k = sum_i nu_ki R_i). */
+kx_status kx_production_rates(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                              double* wdot, int64_t n, kx_precision precision, void* stream);
+
+/* Rates of progress q[N_r][ld] of every reaction, R_i = c_i r_i (Sec. A.2),
+ * the per-reaction quantity the paper validates as "reaction rates"
+ * (Table 3). */
+kx_status kx_rates_of_progress(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                               double* q, int64_t n, kx_precision precision, void* stream);
+
+/* Mass-based mixture cp[n] in J/(kg K) and h[n] in J/kg from the NASA-7
+ * blocks (Sec. A.1: c_p = sum_k Y_k C_p,k / W_k, h = sum_k Y_k H_k / W_k).
+ * p is accepted for symmetry and not used. */
+kx_status kx_thermo(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                    double* cp, double* hmass, int64_t n, void* stream);
+
+/* Mixture-averaged transport (Sec. A.3.5): Wilke/Bird viscosity mu[n] in
+ * Pa s, Mathur conductivity lambda[n] in W/(m K) and diffusion coefficients
+ * Dk[N_s][ld] in m^2/s (Eq. (mix_diff)), from the ln T polynomial fits of
+ * ln eta_k, ln lambda_k and ln D_kj (Sec. A.3.4), D_kj scaled by p_atm/p.
+ * A species whose partners all have X_j = 0 gets its self-diffusion D_kk. */
+kx_status kx_transport(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                       double* mu, double* lambda, double* Dk, int64_t n, kx_precision precision, void* stream);
+
+/* Vector-Jacobian product of the production rates at fixed p: for each
+ * point, gT = sum_k v_k d wdot_k/dT and gY[j] = sum_k v_k d wdot_k/dY_j,
+ * with v[N_s][ld] and gY[N_s][ld].  The paper lists the analytical
+ * Jacobian as future work (Sec. 4); this is its adjoint form.  FP64. */
+kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                  const double* v, double* gT, double* gY, int64_t n, void* stream);
+
+/* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
+ * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
+ * "transport_fp64", "transport_mixed", "vjp".  Any output pointer may be
+ * NULL.  fp64_ops/fp32_ops/exps: the emitter's per-point operation counts. */
+kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes,
+                         double* compile_seconds, double* fp64_ops, double* fp32_ops, double* exps);
+
+const char* kx_status_string(kx_status s);
+
+/* Message of the calling thread's last failed call (empty if none). */
+const char* kx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KX_H */
