@@ -71,6 +71,9 @@ typedef struct {
   int block;          /* threads per block; 0 = 128 */
   int lazy;           /* 0: compile every kernel at load (in parallel); 1: on first use */
   int verbose;        /* 1: print compile times and register/spill counts to stderr */
+  int libmath;        /* 1: CUDA's exp/log in the float64 kernels instead of the library's own */
+  int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);
+                         launch calls on such a handle return KX_ERR_UNSUPPORTED */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 

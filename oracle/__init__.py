@@ -46,6 +46,7 @@ def lib() -> ctypes.CDLL:
         L.ora_reaction_detail.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D]
         L.ora_rates_of_progress.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long,
                                             ctypes.c_int]
+        L.ora_reaction_gross.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
         L.ora_gross_scale.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
         L.ora_thermo.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, _D, ctypes.c_long, ctypes.c_int]
         L.ora_species_transport.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D, _D]
@@ -108,6 +109,13 @@ class Oracle:
         q = np.zeros((self.nr, n))
         self.L.ora_rates_of_progress(self.h, _p(T), _p(p), _p(Y), n, _p(q), n, nthreads or self.nthreads)
         return q
+
+    def reaction_gross(self, T, p, Y, nthreads: Optional[int] = None):
+        T, p, Y = self._state(T, p, Y)
+        n = T.shape[0]
+        g = np.zeros((self.nr, n))
+        self.L.ora_reaction_gross(self.h, _p(T), _p(p), _p(Y), n, _p(g), n, nthreads or self.nthreads)
+        return g
 
     def reaction_detail(self, T: float, p: float, Y):
         Y = np.ascontiguousarray(Y, np.float64)

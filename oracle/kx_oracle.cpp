@@ -477,6 +477,23 @@ int ora_rates_of_progress(void* h, const double* T, const double* p, const doubl
   return 0;
 }
 
+// Per-reaction gross scale |c_i| max(|k_f prod C^nu'|, |k_r prod C^nu''|),
+// [nr][ld]: the size of the two terms whose difference is q_i.
+int ora_reaction_gross(void* h, const double* T, const double* p, const double* Y, long ld, double* out,
+                       long n, int nthreads) {
+  Mech& m = *static_cast<Mech*>(h);
+  parallel(n, nthreads, [&](long a, long b) {
+    std::vector<double> y(m.ns), w(m.ns);
+    std::vector<Detail> det(m.nr);
+    for (long i = a; i < b; ++i) {
+      for (int k = 0; k < m.ns; ++k) y[k] = Y[k * ld + i];
+      production_rates(m, T[i], p[i], y.data(), w.data(), det.data());
+      for (int r = 0; r < m.nr; ++r) out[r * ld + i] = std::fabs(det[r].c) * std::max(std::fabs(det[r].Rf), std::fabs(det[r].Rr));
+    }
+  });
+  return 0;
+}
+
 int ora_reaction_detail(void* h, double T, double p, const double* Y, double* out) {
   Mech& m = *static_cast<Mech*>(h);
   std::vector<double> w(m.ns);

@@ -1,0 +1,435 @@
+// C ABI of the kx library: mechanism handles, NVRTC compilation of the
+// emitted kernels for sm_103a with an on-disk cubin cache, and launches.
+//
+// The runtime is the CUDA runtime API linked statically, so the shared
+// library loads on machines without a GPU (for builds and CPU tests) and
+// talks to whatever driver is present when a kernel is first launched.
+// Kernels are loaded as context-independent libraries (cudaLibraryLoadData)
+// and launched with cudaLaunchKernel on the caller's stream.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kx_internal.h"
+
+#define KX_VERSION "kx-1.0"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kx_status fail(kx_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+kx_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(KX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Kernel {
+  std::string name;            // e.g. "wdot_fp64"
+  std::string entry;           // extern "C" symbol in the emitted source
+  kx::KernelKind kind;
+  kx::EmitOptions eopt;
+  kx::OpCounts ops;
+  std::string source;
+  std::vector<char> cubin;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t fn = nullptr;
+  double compile_seconds = 0;
+  int registers = -1, local_bytes = -1;
+  int max_blocks = 0;          // resident blocks for a persistent grid (per device 0 at load)
+  int smem = 0;                // dynamic shared memory per block, bytes
+  int device = -1;
+  std::mutex mu;
+  bool ready = false;
+  kx_status status = KX_OK;
+  std::string error;
+};
+
+}  // namespace
+
+struct kx_mech {
+  kx::Mechanism m;
+  kx_options opt{};
+  std::string cache_dir;
+  std::vector<std::unique_ptr<Kernel>> kernels;
+};
+
+namespace {
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ULL) {
+  for (unsigned char ch : s) { h ^= ch; h *= 1099511628211ULL; }
+  return h;
+}
+
+std::string default_cache_dir() {
+  if (const char* e = std::getenv("KX_CACHE_DIR")) return e;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/kx";
+}
+
+void mkdirs(const std::string& path) {
+  std::string cur;
+  std::stringstream ss(path);
+  std::string part;
+  if (!path.empty() && path[0] == '/') cur = "/";
+  while (std::getline(ss, part, '/')) {
+    if (part.empty()) continue;
+    cur += part + "/";
+    mkdir(cur.c_str(), 0755);
+  }
+}
+
+bool read_file(const std::string& p, std::vector<char>& out) {
+  std::ifstream f(p, std::ios::binary);
+  if (!f) return false;
+  out.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+  return !out.empty();
+}
+
+void write_file_atomic(const std::string& p, const std::vector<char>& data) {
+  std::string tmp = p + "." + std::to_string(getpid()) + "." +
+                    std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id())) + ".tmp";
+  {
+    std::ofstream f(tmp, std::ios::binary);
+    if (!f) return;
+    f.write(data.data(), (std::streamsize)data.size());
+  }
+  std::rename(tmp.c_str(), p.c_str());
+}
+
+void parse_ptxas_info(const std::string& log, int& regs, int& spill) {
+  // "ptxas info    : Used 255 registers, ..."  and "N bytes spill stores"
+  size_t p = log.rfind("Used ");
+  if (p != std::string::npos) regs = std::atoi(log.c_str() + p + 5);
+  size_t q = log.find("bytes spill stores");
+  if (q != std::string::npos) {
+    size_t b = log.rfind(',', q);
+    size_t s = (b == std::string::npos) ? log.rfind('\n', q) : b;
+    spill = std::atoi(log.c_str() + (s == std::string::npos ? 0 : s + 1));
+  }
+}
+
+// Emit + compile (or fetch from the cache) one kernel.  Host only.
+kx_status compile_kernel(kx_mech* h, Kernel& k) {
+  auto t0 = std::chrono::steady_clock::now();
+  k.source = kx::emit_kernel(h->m, k.kind, k.eopt, k.entry, &k.ops);
+  if (k.source.empty()) return fail(KX_ERR_UNSUPPORTED, "kernel " + k.name + " is not available");
+  std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  if (h->opt.libmath) opts.push_back("-DKX_LIBMATH");
+  if (h->opt.maxrreg > 0) opts.push_back("--maxrregcount=" + std::to_string(h->opt.maxrreg));
+  std::string key = std::string(KX_VERSION) + "\n";
+  for (auto& o : opts) key += o + "\n";
+  int ver_major = 0, ver_minor = 0;
+  nvrtcVersion(&ver_major, &ver_minor);
+  key += std::to_string(ver_major) + "." + std::to_string(ver_minor) + "\n" + k.source;
+  char hex[32];
+  std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key));
+  const std::string base = h->cache_dir + "/" + k.name + "-" + hex;
+  std::vector<char> info;
+  if (read_file(base + ".cubin", k.cubin)) {
+    if (read_file(base + ".log", info)) {
+      std::string log(info.begin(), info.end());
+      parse_ptxas_info(log, k.registers, k.local_bytes);
+    }
+  } else {
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, k.source.c_str(), (k.name + ".cu").c_str(), 0, nullptr, nullptr) != NVRTC_SUCCESS)
+      return fail(KX_ERR_COMPILE, "nvrtcCreateProgram failed");
+    std::vector<const char*> copts;
+    for (auto& o : opts) copts.push_back(o.c_str());
+    nvrtcResult rc = nvrtcCompileProgram(prog, (int)copts.size(), copts.data());
+    size_t log_size = 0;
+    nvrtcGetProgramLogSize(prog, &log_size);
+    std::string log(log_size, '\0');
+    if (log_size) nvrtcGetProgramLog(prog, &log[0]);
+    if (rc != NVRTC_SUCCESS) {
+      nvrtcDestroyProgram(&prog);
+      if (h->opt.verbose) std::fprintf(stderr, "kx: compile of %s failed:\n%s\n", k.name.c_str(), log.c_str());
+      // keep the failing source for inspection
+      write_file_atomic(base + ".failed.cu", std::vector<char>(k.source.begin(), k.source.end()));
+      return fail(KX_ERR_COMPILE, "NVRTC failed on " + k.name + ": " + log.substr(0, 2000));
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    k.cubin.resize(n);
+    nvrtcGetCUBIN(prog, k.cubin.data());
+    nvrtcDestroyProgram(&prog);
+    parse_ptxas_info(log, k.registers, k.local_bytes);
+    mkdirs(h->cache_dir);
+    write_file_atomic(base + ".cubin", k.cubin);
+    write_file_atomic(base + ".log", std::vector<char>(log.begin(), log.end()));
+  }
+  k.compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (h->opt.verbose)
+    std::fprintf(stderr, "kx: %s: %.1f s, %d registers, %d spill bytes, %zu source bytes\n", k.name.c_str(),
+                 k.compile_seconds, k.registers, k.local_bytes, k.source.size());
+  return KX_OK;
+}
+
+kx_status load_kernel(Kernel& k) {
+  cudaError_t e = cudaLibraryLoadData(&k.lib, k.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryLoadData");
+  e = cudaLibraryGetKernel(&k.fn, k.lib, k.entry.c_str());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel");
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (k.smem > 0) {
+    e = cudaKernelSetAttributeForDevice(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaKernelSetAttributeForDevice");
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.fn, k.eopt.block, k.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  k.max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+  k.device = dev;
+  return KX_OK;
+}
+
+kx_status ensure_ready(kx_mech* h, Kernel& k) {
+  std::lock_guard<std::mutex> lock(k.mu);
+  if (k.ready) return KX_OK;
+  if (k.status != KX_OK) return fail(k.status, k.error);
+  kx_status s = KX_OK;
+  if (k.cubin.empty()) s = compile_kernel(h, k);
+  if (s == KX_OK && !h->opt.compile_only) s = load_kernel(k);
+  if (s != KX_OK) {
+    k.status = s;
+    k.error = g_last_error;
+    return s;
+  }
+  k.ready = !h->opt.compile_only;
+  return KX_OK;
+}
+
+Kernel* find_kernel(kx_mech* h, const std::string& name) {
+  for (auto& k : h->kernels)
+    if (k->name == name) return k.get();
+  return nullptr;
+}
+
+kx_status launch(kx_mech* h, const char* name, void** args, int64_t n, void* stream) {
+  Kernel* k = find_kernel(h, name);
+  if (!k) return fail(KX_ERR_UNSUPPORTED, std::string("no kernel ") + name);
+  if (h->opt.compile_only) return fail(KX_ERR_UNSUPPORTED, "handle was loaded with compile_only");
+  kx_status s = ensure_ready(h, *k);
+  if (s != KX_OK) return s;
+  const int64_t want = (n + k->eopt.block - 1) / k->eopt.block;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)k->max_blocks * 4);
+  cudaError_t e =
+      cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(k->eopt.block), args, k->smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
+  return KX_OK;
+}
+
+kx_status check_state(kx_mech* h, const double* T, const double* p, const double* Y, int64_t ld, int64_t n) {
+  if (!h) return fail(KX_ERR_ARG, "null handle");
+  if (n < 0) return fail(KX_ERR_ARG, "negative point count");
+  if (n > 0 && (!T || !p || !Y)) return fail(KX_ERR_ARG, "null state pointer");
+  if (ld < n) return fail(KX_ERR_ARG, "leading dimension smaller than the point count");
+  return KX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kx_status_string(kx_status s) {
+  switch (s) {
+    case KX_OK: return "ok";
+    case KX_ERR_IO: return "mechanism file cannot be read";
+    case KX_ERR_PARSE: return "malformed mechanism file";
+    case KX_ERR_UNBALANCED: return "reaction does not conserve atoms";
+    case KX_ERR_ARG: return "invalid argument";
+    case KX_ERR_OOM: return "out of memory";
+    case KX_ERR_COMPILE: return "kernel compilation failed";
+    case KX_ERR_CUDA: return "CUDA error";
+    case KX_ERR_TIMEOUT: return "timed out";
+    case KX_ERR_NONFINITE_INPUT: return "non-finite input";
+    case KX_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* kx_last_error(void) { return g_last_error.c_str(); }
+
+kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* out) {
+  if (!path || !out) return fail(KX_ERR_ARG, "null argument");
+  *out = nullptr;
+  std::unique_ptr<kx_mech> h(new (std::nothrow) kx_mech());
+  if (!h) return fail(KX_ERR_OOM, "host allocation failed");
+  if (opt) h->opt = *opt;
+  if (h->opt.block == 0) h->opt.block = 128;
+  if (h->opt.block < 32 || h->opt.block > 1024 || h->opt.block % 32) return fail(KX_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
+  if (h->opt.diff_mode < 0 || h->opt.diff_mode > 2) return fail(KX_ERR_ARG, "diff_mode must be 0, 1 or 2");
+  if (h->opt.kc_mode < 0 || h->opt.kc_mode > 1) return fail(KX_ERR_ARG, "kc_mode must be 0 or 1");
+  if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
+  h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
+  h->opt.cache_dir = nullptr;
+  std::string err;
+  kx_status s = kx::parse_mechanism(path, h->m, err);
+  if (s != KX_OK) return fail(s, err);
+
+  struct Spec { const char* name; kx::KernelKind kind; bool mixed; };
+  const Spec specs[] = {
+      {"wdot_fp64", kx::KernelKind::Wdot, false},       {"wdot_mixed", kx::KernelKind::Wdot, true},
+      {"rop_fp64", kx::KernelKind::Rop, false},         {"rop_mixed", kx::KernelKind::Rop, true},
+      {"thermo", kx::KernelKind::Thermo, false},        {"transport_fp64", kx::KernelKind::Transport, false},
+      {"transport_mixed", kx::KernelKind::Transport, true},
+  };
+  for (const Spec& sp : specs) {
+    std::unique_ptr<Kernel> k(new Kernel());
+    k->name = sp.name;
+    k->entry = std::string("kx_") + sp.name;
+    k->kind = sp.kind;
+    k->eopt.mixed = sp.mixed;
+    k->eopt.block = h->opt.block;
+    k->eopt.diff_mode = h->opt.diff_mode == 2 ? 2 : 1;
+    k->eopt.kc_mode = h->opt.kc_mode;
+    if (sp.kind == kx::KernelKind::Transport) {
+      // species vectors staged in shared memory: as many threads as fit in ~200 KB, a multiple of 32
+      const int per = kx::transport_smem_per_thread(h->m, sp.mixed);
+      int b = std::min(h->opt.block, (200 * 1024 / per) / 32 * 32);
+      if (b < 32) return fail(KX_ERR_UNSUPPORTED, "mechanism too large for the transport kernel");
+      k->eopt.block = b;
+      k->smem = per * b;
+    }
+    h->kernels.push_back(std::move(k));
+  }
+  if (!h->opt.lazy) {
+    // compile in parallel (NVRTC programs are independent), load serially
+    std::vector<std::thread> th;
+    std::vector<kx_status> st(h->kernels.size(), KX_OK);
+    std::vector<std::string> msg(h->kernels.size());
+    for (size_t i = 0; i < h->kernels.size(); ++i)
+      th.emplace_back([&, i] {
+        st[i] = compile_kernel(h.get(), *h->kernels[i]);
+        if (st[i] != KX_OK) msg[i] = g_last_error;
+      });
+    for (auto& t : th) t.join();
+    for (size_t i = 0; i < st.size(); ++i)
+      if (st[i] != KX_OK) return fail(st[i], msg[i]);
+    if (!h->opt.compile_only)
+      for (auto& k : h->kernels) {
+        s = ensure_ready(h.get(), *k);
+        if (s != KX_OK) return s;
+      }
+  }
+  *out = h.release();
+  return KX_OK;
+}
+
+kx_status kx_free_mechanism(kx_handle h) {
+  if (!h) return fail(KX_ERR_ARG, "null handle");
+  for (auto& k : h->kernels)
+    if (k->lib) cudaLibraryUnload(k->lib);
+  delete h;
+  return KX_OK;
+}
+
+kx_status kx_mechanism_info(kx_handle h, int* n_species, int* n_reactions, double* W) {
+  if (!h) return fail(KX_ERR_ARG, "null handle");
+  if (n_species) *n_species = h->m.ns;
+  if (n_reactions) *n_reactions = h->m.nr();
+  if (W) std::memcpy(W, h->m.W.data(), sizeof(double) * h->m.ns);
+  return KX_OK;
+}
+
+kx_status kx_production_rates(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                              double* wdot, int64_t n, kx_precision precision, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && !wdot) return fail(KX_ERR_ARG, "null output");
+  if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
+  return launch(h, precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed", args, n, stream);
+}
+
+kx_status kx_rates_of_progress(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* q,
+                               int64_t n, kx_precision precision, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && !q) return fail(KX_ERR_ARG, "null output");
+  if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &q, &nl};
+  return launch(h, precision == KX_FP64 ? "rop_fp64" : "rop_mixed", args, n, stream);
+}
+
+kx_status kx_thermo(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* cp,
+                    double* hmass, int64_t n, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && (!cp || !hmass)) return fail(KX_ERR_ARG, "null output");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &cp, &hmass, &nl};
+  return launch(h, "thermo", args, n, stream);
+}
+
+kx_status kx_transport(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* mu,
+                       double* lambda, double* Dk, int64_t n, kx_precision precision, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && (!mu || !lambda || !Dk)) return fail(KX_ERR_ARG, "null output");
+  if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &mu, &lambda, &Dk, &nl};
+  return launch(h, precision == KX_FP64 ? "transport_fp64" : "transport_mixed", args, n, stream);
+}
+
+kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                  const double* v, double* gT, double* gY, int64_t n, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && (!v || !gT || !gY)) return fail(KX_ERR_ARG, "null argument");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &v, &gT, &gY, &nl};
+  return launch(h, "vjp", args, n, stream);
+}
+
+kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes, double* compile_seconds,
+                         double* fp64_ops, double* fp32_ops, double* exps) {
+  if (!h || !kernel) return fail(KX_ERR_ARG, "null argument");
+  Kernel* k = find_kernel(h, kernel);
+  if (!k) return fail(KX_ERR_ARG, std::string("no kernel ") + kernel);
+  if (k->cubin.empty()) {
+    std::lock_guard<std::mutex> lock(k->mu);
+    if (k->cubin.empty()) {
+      kx_status s = compile_kernel(h, *k);
+      if (s != KX_OK) return s;
+    }
+  }
+  if (registers) *registers = k->registers;
+  if (local_bytes) *local_bytes = k->local_bytes;
+  if (compile_seconds) *compile_seconds = k->compile_seconds;
+  const kx::OpCounts& c = k->ops;
+  if (fp64_ops) *fp64_ops = c.fp64;
+  if (fp32_ops) *fp32_ops = c.fp32;
+  if (exps) *exps = c.exp64 + c.exp32;
+  return KX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,917 @@
+// CUDA source emitter: turns one mechanism into straight-line, fully
+// unrolled per-point kernels for sm_103a.
+//
+// Every constant of the mechanism (Arrhenius triples, stoichiometry,
+// efficiencies, Troe/SRI/PLOG parameters, NASA-7 and transport-fit
+// coefficients) is folded into the generated source, so a kernel is one
+// long dependence-light instruction stream per grid point (thread per
+// point, the paper's per-thread model, Sec. 2.4).  On GB300 the float64
+// pipe is the scarce unit (about 2 DFMA per clock per SM, against 128 FFMA),
+// so the emitter's job is to spend as few float64 operations as it can:
+//
+//  * one ln T and 1/T per point, shared by every Arrhenius term;
+//    k_f = exp(ln A + beta ln T - E/T) with the special cases of Eq. (k_f)
+//    (constant, integer power) and one shared exponential for reactions
+//    with equal (beta, E), emitted next to each other;
+//  * reverse rates in log space, k_r = exp(ln k_f - ln K_c), with
+//    ln K_c = -sum nu G/RT + (sum nu) ln(p_atm/(R T)) (Eq. K_p), or, as an
+//    option, the paper's per-species exp(-G/RT) products with one division;
+//  * float64 exp/log of our own (table-driven, Tang's method) whose
+//    polynomial tail runs on the float32 pipe;
+//  * the Wilke sum refactored into three products with a constant matrix,
+//    the Mathur and diffusion sums accumulated pairwise (symmetric D_kj).
+//
+// The mixed-precision variant evaluates the Arrhenius, third-body and
+// falloff arithmetic in float32, keeps ln K_c (through species chemical
+// potentials G_k/RT + ln C_k), the forward/reverse cancellation and the
+// accumulation of wdot in float64 (see emit_rates_mixed).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <set>
+#include <sstream>
+
+#include "kx_internal.h"
+
+namespace kx {
+
+const char* kTables =
+#include "kx_tables.inc"
+    ;
+
+const char* kDevicePrelude = R"KXPRE(
+#define KX_INF __longlong_as_double(0x7ff0000000000000LL)
+#define KX_NAN __longlong_as_double(0x7ff8000000000000LL)
+#define KX_INV_LN10 0.43429448190325182765
+#define KX_LN10 2.30258509299404568402
+#define KX_LOG2E_F 1.44269504f
+
+// float64 exp: x = k ln2/256 + r with k = rint(x 256/ln2) found in float32
+// and r by a two-constant Cody-Waite reduction in float64; e^r - 1 =
+// r + r^2 q(r) with the short tail q in float32 (|r^2 q| < 1.1e-6, so its
+// float32 rounding is below 1e-13 relative); 2^(j/256) from a shared table
+// and 2^(k>>8) by an exponent-field add.  |x| >= 700, inf and nan take the
+// library path.
+__device__ __forceinline__ double kx_exp(double x) {
+#ifdef KX_LIBMATH
+  return exp(x);
+#else
+  if (!(fabs(x) < 700.0)) return exp(x);
+  const int k = __float2int_rn(__double2float_rn(x) * KX_256_OVER_LN2F);
+  const double kd = (double)k;
+  double r = fma(kd, -KX_LN2_256_HI, x);
+  r = fma(kd, -KX_LN2_256_LO, r);
+  const float rf = __double2float_rn(r);
+  const float qf = fmaf(fmaf(fmaf(rf, 8.33333333e-3f, 4.16666667e-2f), rf, 0.166666667f), rf, 0.5f);
+  const double s = fma(r * r, (double)qf, r);
+  const double tj = kx_s_exp[k & 255];
+  const double v = fma(tj, s, tj);
+  return __hiloint2double(__double2hiint(v) + (int)((unsigned)(k >> 8) << 20), __double2loint(v));
+#endif
+}
+
+// float64 natural log: x = 2^e m, m in [1,2); c = 1 + (2j+1)/512 is the
+// centre of m's cell, r = (m - c)/c with 1/c from the table, and
+// log1p(r) = r - r^2 q(r) with the tail q in float32 (|r^2 q| < 2e-6).
+// Zero, negative, subnormal, inf and nan inputs take the library path.
+__device__ __forceinline__ double kx_log(double x) {
+#ifdef KX_LIBMATH
+  return log(x);
+#else
+  if (!(x >= 2.2250738585072014e-308 && x < KX_INF)) return log(x);
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) - 1023;
+  const int j = (hi >> 12) & 0xff;
+  const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));
+  const double u = m - fma((double)(2 * j + 1), 1.0 / 512.0, 1.0);
+  const double r = u * kx_s_log[3 * j];
+  const float rf = __double2float_rn(r);
+  const float qf = fmaf(fmaf(fmaf(rf, -0.2f, 0.25f), rf, -0.333333333f), rf, 0.5f);
+  const double t = fma(-(r * r), (double)qf, r);
+  const double ed = (double)e;
+  return fma(ed, KX_LN2_HI, kx_s_log[3 * j + 1]) + (fma(ed, KX_LN2_LO, kx_s_log[3 * j + 2]) + t);
+#endif
+}
+
+__device__ __forceinline__ void kx_load_tables() {
+#ifndef KX_LIBMATH
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
+  for (int t = threadIdx.x; t < 768; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
+  __syncthreads();
+#endif
+}
+
+// fac * 2^t as a float64 for |t| up to ~1100 and fac in [0, 1]: the
+// mantissa comes from float32 exp2 of the fractional part, the power of two
+// is added to the float64 exponent field (no float64 arithmetic).
+__device__ __forceinline__ double kx_pow2_scaled(float t, float fac) {
+  const float n = floorf(t);
+  const float m = exp2f(t - n) * fac;
+  if (!(m >= 0.0f)) return KX_NAN;
+  if (!(n < 4096.0f)) return m == 0.0f ? 0.0 : KX_INF;
+  if (!(n > -4096.0f)) return 0.0;
+  const double dm = (double)m;
+  const int ni = (int)n;
+  const int hi = __double2hiint(dm);
+  const int E = ((hi >> 20) & 0x7ff) + ni;
+  if (m == 0.0f || E <= 0) return 0.0;
+  if (E >= 0x7ff) return KX_INF;
+  return __hiloint2double(hi + (int)((unsigned)ni << 20), __double2loint(dm));
+}
+
+// Net rate of progress R_f - R_r from ln R_f (float32) and the float64
+// log-ratio ln(R_r/R_f): the larger of the two rates times
+// (1 - smaller/larger) = -expm1(-|ln ratio|), so the cancellation near
+// equilibrium is resolved from the float64 ratio, not by subtracting two
+// rounded rates.
+__device__ __forceinline__ double kx_net_rate(float lnRf, double lnrho) {
+  const float a = __double2float_rn(lnrho);
+  const float e = lnRf + fmaxf(a, 0.0f);
+  const float fac = -expm1f(-fabsf(a));
+  const double mag = kx_pow2_scaled(e * KX_LOG2E_F, fac);
+  return a > 0.0f ? -mag : mag;
+}
+
+// ln(Pr/(1+Pr)) and ln(1/(1+Pr)) from ln Pr without overflow (float32).
+__device__ __forceinline__ float kx_ln_pr_ratio(float lnPr) {
+  return lnPr < 0.0f ? lnPr - log1pf(__expf(lnPr)) : -log1pf(__expf(-lnPr));
+}
+__device__ __forceinline__ float kx_ln_inv_1p(float lnPr) {
+  return lnPr < 0.0f ? -log1pf(__expf(lnPr)) : -(lnPr + log1pf(__expf(-lnPr)));
+}
+)KXPRE";
+
+namespace {
+
+// ------------------------------------------------------------------ text helpers
+std::string fmt(const char* f, ...) {
+  va_list ap, ap2;
+  va_start(ap, f);
+  va_copy(ap2, ap);
+  const int n = vsnprintf(nullptr, 0, f, ap);
+  va_end(ap);
+  std::string out(n > 0 ? n : 0, '\0');
+  if (n > 0) vsnprintf(&out[0], n + 1, f, ap2);
+  va_end(ap2);
+  return out;
+}
+
+// float64 literal that reads back bit-exactly
+std::string D(double v) {
+  if (std::isnan(v)) return "KX_NAN";
+  if (std::isinf(v)) return v > 0 ? "KX_INF" : "(-KX_INF)";
+  std::string s = fmt("%.17g", v);
+  if (s.find_first_of(".en") == std::string::npos) s += ".0";
+  return s[0] == '-' ? "(" + s + ")" : s;
+}
+
+// float32 literal (value rounded to float first)
+std::string F(double v) {
+  float f = (float)v;
+  if (std::isinf(f)) return v > 0 ? "__int_as_float(0x7f800000)" : "(-__int_as_float(0x7f800000))";
+  std::string s = fmt("%.9g", (double)f);
+  if (s.find_first_of(".en") == std::string::npos) s += ".0";
+  s += "f";
+  return s[0] == '-' ? "(" + s + ")" : s;
+}
+
+struct Out {
+  std::ostringstream o;
+  int ind = 1;
+  void operator()(const std::string& s) { o << std::string(2 * ind, ' ') << s << "\n"; }
+};
+
+bool is_small_int(double b) { return b == std::floor(b) && std::fabs(b) <= 4.0; }
+
+// ln k expression (float64) of an Arrhenius triple, or "" when k is A alone.
+std::string ln_arrh64(const Arrh& a, OpCounts& c) {
+  std::string s = D(std::log(a.A));
+  if (a.E != 0.0) { s = fmt("fma(%s, iT, %s)", D(-a.E).c_str(), s.c_str()); c.fp64 += 1; }
+  if (a.beta != 0.0) { s = fmt("fma(%s, lnT, %s)", D(a.beta).c_str(), s.c_str()); c.fp64 += 1; }
+  return s;
+}
+
+std::string ln_arrh32(const Arrh& a, OpCounts& c) {
+  std::string s = F(std::log(a.A));
+  if (a.E != 0.0) { s = fmt("fmaf(%s, iTf, %s)", F(-a.E).c_str(), s.c_str()); c.fp32 += 1; }
+  if (a.beta != 0.0) { s = fmt("fmaf(%s, lnTf, %s)", F(a.beta).c_str(), s.c_str()); c.fp32 += 1; }
+  return s;
+}
+
+// Species that need G/RT: those of reversible reactions.
+std::vector<char> gibbs_needed(const Mechanism& m) {
+  std::vector<char> need(m.ns, 0);
+  for (auto& r : m.rx)
+    if (r.reversible) {
+      for (auto& e : r.reac) need[e.first] = 1;
+      for (auto& e : r.prod) need[e.first] = 1;
+    }
+  return need;
+}
+
+std::vector<char> species_used(const Mechanism& m) {
+  std::vector<char> used(m.ns, 0);
+  for (auto& r : m.rx) {
+    for (auto& e : r.reac) used[e.first] = 1;
+    for (auto& e : r.prod) used[e.first] = 1;
+    if (r.collider >= 0) used[r.collider] = 1;
+    for (auto& e : r.eff) used[e.first] = 1;
+  }
+  return used;
+}
+
+// Distinct NASA mid temperatures get one range flag each.
+std::map<double, int> tmid_flags(const Mechanism& m) {
+  std::map<double, int> f;
+  for (int k = 0; k < m.ns; ++k)
+    if (!f.count(m.Tmid[k])) { int id = (int)f.size(); f[m.Tmid[k]] = id; }
+  return f;
+}
+
+std::string sel(const std::string& flag, double lo, double hi) {
+  if (lo == hi) return D(lo);
+  return fmt("(%s ? %s : %s)", flag.c_str(), D(lo).c_str(), D(hi).c_str());
+}
+
+// G/RT of species k as float64 (Eq. (Ck)): a polynomial in T, a5/T, -a0 ln T.
+void emit_gibbs64(Out& o, const Mechanism& m, int k, const std::string& flag, OpCounts& c) {
+  const double* lo = &m.a_lo[7 * k];
+  const double* hi = &m.a_hi[7 * k];
+  auto co = [&](const double* a, int n) {
+    switch (n) {
+      case 0: return a[0] - a[6];
+      case 1: return -a[1] / 2.0;
+      case 2: return -a[2] / 6.0;
+      case 3: return -a[3] / 12.0;
+      default: return -a[4] / 20.0;
+    }
+  };
+  std::string h = sel(flag, co(lo, 4), co(hi, 4));
+  for (int n = 3; n >= 0; --n) h = fmt("fma(%s, T, %s)", h.c_str(), sel(flag, co(lo, n), co(hi, n)).c_str());
+  o(fmt("const double g_%d = fma(%s, lnT, fma(%s, iT, %s));", k, sel(flag, -lo[0], -hi[0]).c_str(),
+        sel(flag, lo[5], hi[5]).c_str(), h.c_str()));
+  c.fp64 += 6;
+}
+
+std::string nasa_flag(const Mechanism& m, int k, const std::map<double, int>& flags) {
+  return fmt("lo%d", flags.at(m.Tmid[k]));
+}
+
+// Concentrations C_k (float64) and [M]; y_k = Y_k/W_k.
+void emit_concentrations64(Out& o, const Mechanism& m, const std::vector<char>& used, OpCounts& c) {
+  o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
+  std::string sum;
+  for (int k = 0; k < m.ns; ++k) {
+    o(fmt("const double y_%d = Y_[(long long)%d * ld + i] * %s;", k, k, D(1.0 / m.W[k]).c_str()));
+    sum += (k ? " + y_" : "y_") + std::to_string(k);
+  }
+  o("const double sig = " + sum + ";");
+  o("const double fC = cM / sig;");
+  for (int k = 0; k < m.ns; ++k)
+    if (used[k]) o(fmt("const double C_%d = y_%d * fC;", k, k));
+  c.fp64 += 2 * m.ns + 3;
+  c.div64 += 1;
+}
+
+// Third-body concentration [X]_i (float64).
+std::string third_body64(const Reaction& r, OpCounts& c) {
+  if (r.collider >= 0) return fmt("C_%d", r.collider);
+  std::string s = r.default_eff == 1.0 ? std::string("cM") : fmt("%s * cM", D(r.default_eff).c_str());
+  for (auto& e : r.eff) {
+    double a = e.second - r.default_eff;
+    if (a == 0.0) continue;
+    s = fmt("fma(%s, C_%d, %s)", D(a).c_str(), e.first, s.c_str());
+    c.fp64 += 1;
+  }
+  return s;
+}
+
+std::string third_body32(const Reaction& r, OpCounts& c) {
+  if (r.collider >= 0) return fmt("Cf_%d", r.collider);
+  std::string s = r.default_eff == 1.0 ? std::string("cMf") : fmt("%s * cMf", F(r.default_eff).c_str());
+  for (auto& e : r.eff) {
+    double a = e.second - r.default_eff;
+    if (a == 0.0) continue;
+    s = fmt("fmaf(%s, Cf_%d, %s)", F(a).c_str(), e.first, s.c_str());
+    c.fp32 += 1;
+  }
+  return s;
+}
+
+std::string conc_product(const std::vector<std::pair<int, int>>& side, const std::string& pre) {
+  std::string s;
+  for (auto& e : side)
+    for (int n = 0; n < e.second; ++n) s += " * " + pre + std::to_string(e.first);
+  return s;
+}
+
+int sum_nu(const Reaction& r) {
+  int dn = 0;
+  for (auto& e : r.prod) dn += e.second;
+  for (auto& e : r.reac) dn -= e.second;
+  return dn;
+}
+
+// sum_k nu_k v_k over products minus reactants, as an fma chain on `var`.
+std::string nu_sum(const Reaction& r, const char* var, OpCounts& c) {
+  std::map<int, int> nu;
+  for (auto& e : r.prod) nu[e.first] += e.second;
+  for (auto& e : r.reac) nu[e.first] -= e.second;
+  std::string s;
+  for (auto& kv : nu) {
+    if (kv.second == 0) continue;
+    std::string term = fmt("%s_%d", var, kv.first);
+    if (s.empty()) {
+      s = kv.second == 1 ? term : kv.second == -1 ? "-" + term : fmt("%s * %s", D(kv.second).c_str(), term.c_str());
+    } else {
+      s = kv.second == 1 ? s + " + " + term : kv.second == -1 ? s + " - " + term
+                                                               : fmt("fma(%s, %s, %s)", D(kv.second).c_str(), term.c_str(), s.c_str());
+    }
+    c.fp64 += 1;
+  }
+  return s.empty() ? "0.0" : s;
+}
+
+// ------------------------------------------------------------------ rates, float64
+// Order of emission: reactions sharing a (beta, E) pair (and neither being
+// a special case) are emitted next to each other so that their common
+// exp(beta ln T - E/T) is computed once and dies at once (Sec. 2.3.1).
+std::vector<int> emission_order(const Mechanism& m, std::map<int, int>& share_group) {
+  std::map<std::pair<double, double>, std::vector<int>> groups;
+  for (int i = 0; i < m.nr(); ++i) {
+    const Reaction& r = m.rx[i];
+    if ((r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && !(r.k.beta == 0.0 && r.k.E == 0.0) &&
+        !(r.k.E == 0.0 && is_small_int(r.k.beta)))
+      groups[{r.k.beta, r.k.E}].push_back(i);
+  }
+  std::vector<int> order;
+  std::vector<char> done(m.nr(), 0);
+  int gid = 0;
+  for (int i = 0; i < m.nr(); ++i) {
+    if (done[i]) continue;
+    const Reaction& r = m.rx[i];
+    auto it = groups.find({r.k.beta, r.k.E});
+    if ((r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && it != groups.end() && it->second.size() > 1 &&
+        it->second[0] == i) {
+      for (int j : it->second) { order.push_back(j); done[j] = 1; share_group[j] = gid; }
+      ++gid;
+    } else if (!done[i]) {
+      order.push_back(i);
+      done[i] = 1;
+    }
+  }
+  return order;
+}
+
+void emit_rates64(Out& o, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
+  const auto used = species_used(m);
+  const auto need_g = gibbs_needed(m);
+  const auto flags = tmid_flags(m);
+  o("const double lnT = log(T);");
+  o("const double iT = 1.0 / T;");
+  c.log64 += 1; c.div64 += 1;
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  if (any_plog) { o("const double lnP = kx_log(P);"); c.log64 += 1; }
+  emit_concentrations64(o, m, used, c);
+  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
+  for (int k = 0; k < m.ns; ++k)
+    if (need_g[k]) emit_gibbs64(o, m, k, nasa_flag(m, k, flags), c);
+  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
+  c.fp64 += 1;
+  if (opt.kc_mode == 1) {
+    o("const double PRT = P_ATM_R * iT;");
+    for (int k = 0; k < m.ns; ++k)
+      if (need_g[k]) { o(fmt("const double eg_%d = kx_exp(-g_%d);", k, k)); c.exp64 += 1; }
+  }
+  if (!rop)
+    for (int k = 0; k < m.ns; ++k) o(fmt("double w_%d = 0.0;", k));
+
+  std::map<int, int> share;
+  std::vector<int> order = emission_order(m, share);
+  int open_group = -1;
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const int i = order[oi];
+    const Reaction& r = m.rx[i];
+    if (share.count(i) && share[i] != open_group) {
+      o(fmt("{  // shared exp(beta lnT - E/T), beta = %s, E/R = %s", D(r.k.beta).c_str(), D(r.k.E).c_str()));
+      ++o.ind;
+      Arrh a = r.k;
+      a.A = 1.0;
+      o(fmt("const double ex = kx_exp(%s);", ln_arrh64(a, c).c_str()));
+      c.exp64 += 1;
+      open_group = share[i];
+    }
+    o(fmt("{  // reaction %d", i));
+    ++o.ind;
+    bool kf_is_exp = false;   // kf = exp(lkf) with lkf available
+    if (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) {
+      if (share.count(i)) {
+        o(fmt("const double kf = %s * ex;", D(r.k.A).c_str()));
+        c.fp64 += 1;
+      } else if (r.k.beta == 0.0 && r.k.E == 0.0) {
+        o(fmt("const double kf = %s;", D(r.k.A).c_str()));
+        o(fmt("const double lkf = %s;", D(std::log(r.k.A)).c_str()));
+        kf_is_exp = true;
+      } else if (r.k.E == 0.0 && is_small_int(r.k.beta)) {
+        int b = (int)r.k.beta;
+        std::string s = D(r.k.A);
+        for (int n = 0; n < std::abs(b); ++n) s += b > 0 ? " * T" : " * iT";
+        o("const double kf = " + s + ";");
+        c.fp64 += std::abs(b);
+      } else {
+        o(fmt("const double lkf = %s;", ln_arrh64(r.k, c).c_str()));
+        o("const double kf = kx_exp(lkf);");
+        c.exp64 += 1;
+        kf_is_exp = true;
+      }
+    } else if (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) {
+      o(fmt("const double lk0 = %s;", ln_arrh64(r.k0, c).c_str()));
+      o(fmt("const double lki = %s;", ln_arrh64(r.k, c).c_str()));
+      o(fmt("const double X = %s;", third_body64(r, c).c_str()));
+      o("const double lnPr = fmax(lk0 - lki + kx_log(X), -690.77552789821368);");
+      o("const double Pr = kx_exp(lnPr);");
+      c.fp64 += 2; c.log64 += 1; c.exp64 += 1;
+      if (r.blend == Blend::Troe) {
+        const double al = r.troe[0];
+        std::string Fc;
+        if (1.0 - al != 0.0) { Fc = fmt("%s * kx_exp(T * %s)", D(1.0 - al).c_str(), D(-1.0 / r.troe[1]).c_str()); c.exp64 += 1; c.fp64 += 2; }
+        if (al != 0.0) { Fc += (Fc.empty() ? "" : " + ") + fmt("%s * kx_exp(T * %s)", D(al).c_str(), D(-1.0 / r.troe[2]).c_str()); c.exp64 += 1; c.fp64 += 2; }
+        Fc += (Fc.empty() ? "" : " + ") + fmt("kx_exp(%s * iT)", D(-r.troe[3]).c_str());
+        c.exp64 += 1; c.fp64 += 1;
+        o("const double lFc = kx_log(" + Fc + ") * KX_INV_LN10;");
+        o("const double xx = fma(lnPr, KX_INV_LN10, fma(-0.67, lFc, -0.4));");
+        o("const double ff = xx / (fma(-1.27, lFc, 0.75) - 0.14 * xx);");
+        o("const double F = kx_exp(KX_LN10 * lFc / fma(ff, ff, 1.0));");
+        c.log64 += 1; c.exp64 += 1; c.div64 += 2; c.fp64 += 8;
+      } else if (r.blend == Blend::Sri) {
+        o("const double lPr = lnPr * KX_INV_LN10;");
+        o(fmt("const double base = %s * kx_exp(%s * iT) + kx_exp(T * %s);", D(r.sri[0]).c_str(), D(-r.sri[1]).c_str(),
+              D(-1.0 / r.sri[2]).c_str()));
+        o(fmt("const double F = %s * kx_exp(fma(%s, lnT, kx_log(base) / fma(lPr, lPr, 1.0)));", D(r.sri[3]).c_str(),
+              D(r.sri[4]).c_str()));
+        c.exp64 += 3; c.log64 += 1; c.div64 += 1; c.fp64 += 8;
+      } else {
+        o("const double F = 1.0;");
+      }
+      if (r.kind == Kind::Falloff) {
+        o("const double kf = kx_exp(lki) * (Pr / (1.0 + Pr)) * F;");
+      } else {
+        o("const double kf = kx_exp(lk0) * (1.0 / (1.0 + Pr)) * F;");
+      }
+      c.exp64 += 1; c.div64 += 1; c.fp64 += 3;
+    } else {  // PLOG
+      const auto& t = r.plog;
+      auto lk = [&](size_t j) {
+        Arrh a{t[j][1], t[j][2], t[j][3]};
+        return ln_arrh64(a, c);
+      };
+      o("double lkf;");
+      o(fmt("if (P <= %s) lkf = %s;", D(t[0][0]).c_str(), lk(0).c_str()));
+      for (size_t j = 0; j + 1 < t.size(); ++j) {
+        double l1 = std::log(t[j][0]), l2 = std::log(t[j + 1][0]);
+        o(fmt("else if (P < %s) { const double l1 = %s; lkf = fma(%s - l1, (lnP - %s) * %s, l1); }", D(t[j + 1][0]).c_str(),
+              lk(j).c_str(), lk(j + 1).c_str(), D(l1).c_str(), D(1.0 / (l2 - l1)).c_str()));
+      }
+      o(fmt("else lkf = %s;", lk(t.size() - 1).c_str()));
+      o("const double kf = kx_exp(lkf);");
+      c.exp64 += 1; c.fp64 += 3;
+      kf_is_exp = true;
+    }
+    std::string q;
+    if (r.reversible) {
+      const int dn = sum_nu(r);
+      if (opt.kc_mode == 1) {
+        std::string num = "kf" + conc_product(r.reac, "eg_");
+        std::string den = conc_product(r.prod, "eg_").substr(3);
+        for (int n = 0; n < -dn; ++n) num += " * PRT";
+        for (int n = 0; n < dn; ++n) den += " * PRT";
+        o("const double kr = (" + num + ") / (" + den + ");");
+        c.div64 += 1; c.fp64 += 4;
+      } else {
+        std::string lnkc = nu_sum(r, "g", c);
+        // ln K_c = -sum nu g + dn lnPRT
+        std::string lk = dn == 0 ? "-(" + lnkc + ")" : fmt("fma(%s, lnPRT, -(%s))", D(dn).c_str(), lnkc.c_str());
+        if (dn != 0) c.fp64 += 1;
+        o("const double lnKc = " + lk + ";");
+        if (kf_is_exp) o("const double kr = kx_exp(lkf - lnKc);");
+        else o("const double kr = kf * kx_exp(-lnKc);");
+        c.exp64 += 1; c.fp64 += 1;
+      }
+      o("const double q = kf" + conc_product(r.reac, "C_") + " - kr" + conc_product(r.prod, "C_") + ";");
+    } else {
+      o("const double q = kf" + conc_product(r.reac, "C_") + ";");
+    }
+    for (auto& e : r.reac) c.fp64 += e.second;
+    for (auto& e : r.prod) c.fp64 += e.second;
+    c.fp64 += 1;
+    std::string qq = "q";
+    if (r.kind == Kind::ThreeBody) {
+      o(fmt("const double qX = q * (%s);", third_body64(r, c).c_str()));
+      qq = "qX";
+      c.fp64 += 1;
+    }
+    if (rop) {
+      o(fmt("out_[(long long)%d * ld + i] = %s;", i, qq.c_str()));
+    } else {
+      std::map<int, int> nu;
+      for (auto& e : r.prod) nu[e.first] += e.second;
+      for (auto& e : r.reac) nu[e.first] -= e.second;
+      for (auto& kv : nu) {
+        if (kv.second == 1) o(fmt("w_%d += %s;", kv.first, qq.c_str()));
+        else if (kv.second == -1) o(fmt("w_%d -= %s;", kv.first, qq.c_str()));
+        else if (kv.second != 0) o(fmt("w_%d = fma(%s, %s, w_%d);", kv.first, D(kv.second).c_str(), qq.c_str(), kv.first));
+        if (kv.second != 0) c.fp64 += 1;
+      }
+    }
+    --o.ind;
+    o("}");
+    const bool last_of_group = share.count(i) && (oi + 1 == order.size() || !share.count(order[oi + 1]) ||
+                                                  share[order[oi + 1]] != share[i]);
+    if (last_of_group) {
+      --o.ind;
+      o("}");
+      open_group = -1;
+    }
+  }
+  if (!rop)
+    for (int k = 0; k < m.ns; ++k) o(fmt("out_[(long long)%d * ld + i] = w_%d;", k, k));
+}
+
+// ------------------------------------------------------------------ rates, mixed
+// float32: ln k_f, third-body [X], falloff blending, ln R_f = ln(c_i k_f
+// prod C^nu').  float64: ln C_k, G_k/RT, mu_k = G_k/RT + ln C_k and
+// ln(R_r/R_f) = sum_k nu_k mu_k - (sum nu) ln(p_atm/(R T)), which is
+// -ln K_c + sum nu ln C (Eq. K_p); q = R_f - R_r from kx_net_rate; wdot
+// accumulated in float64.
+void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
+  const auto used = species_used(m);
+  const auto need_g = gibbs_needed(m);
+  const auto flags = tmid_flags(m);
+  o("const double lnT = log(T);");
+  o("const double iT = 1.0 / T;");
+  o("const float lnTf = (float)lnT, iTf = (float)iT;");
+  c.log64 += 1; c.div64 += 1;
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  if (any_plog) { o("const float lnPf = __logf((float)P);"); c.log32 += 1; }
+  o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
+  std::string sum;
+  for (int k = 0; k < m.ns; ++k) {
+    o(fmt("const double Yk_%d = Y_[(long long)%d * ld + i];", k, k));
+    o(fmt("const double y_%d = Yk_%d * %s;", k, k, D(1.0 / m.W[k]).c_str()));
+    sum += (k ? " + y_" : "y_") + std::to_string(k);
+  }
+  o("const double sig = " + sum + ";");
+  o("const double fC = cM / sig;");
+  o("const double lnfC = kx_log(fC);");
+  o("const float cMf = (float)cM, fCf = (float)fC;");
+  c.fp64 += 2 * m.ns + 2; c.div64 += 1; c.log64 += 1;
+  bool any_tb = false;
+  for (auto& r : m.rx) any_tb |= r.third_body();
+  for (int k = 0; k < m.ns; ++k) {
+    if (!used[k]) continue;
+    // ln C_k = ln Y_k - ln W_k + ln fC, floored at ln(1e-304) so that an absent species gives 0 rates, not nan
+    o(fmt("const double lnC_%d = fmax(kx_log(Yk_%d) + (lnfC - %s), -700.0);", k, k, D(std::log(m.W[k])).c_str()));
+    o(fmt("const float lnCf_%d = (float)lnC_%d;", k, k));
+    if (any_tb) o(fmt("const float Cf_%d = (float)y_%d * fCf;", k, k));
+    c.log64 += 1; c.fp64 += 2; c.fp32 += 1;
+  }
+  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
+  for (int k = 0; k < m.ns; ++k)
+    if (need_g[k]) {
+      emit_gibbs64(o, m, k, nasa_flag(m, k, flags), c);
+      o(fmt("const double mu_%d = g_%d + lnC_%d;", k, k, k));
+      c.fp64 += 1;
+    }
+  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
+  c.fp64 += 1;
+  if (!rop)
+    for (int k = 0; k < m.ns; ++k) o(fmt("double w_%d = 0.0;", k));
+  for (int i = 0; i < m.nr(); ++i) {
+    const Reaction& r = m.rx[i];
+    o(fmt("{  // reaction %d", i));
+    ++o.ind;
+    std::string lnRf;
+    if (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) {
+      lnRf = ln_arrh32(r.k, c);
+      if (r.kind == Kind::ThreeBody) {
+        o(fmt("const float lX = __logf(%s);", third_body32(r, c).c_str()));
+        c.log32 += 1;
+        lnRf += " + lX";
+      }
+    } else if (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) {
+      o(fmt("const float lk0 = %s;", ln_arrh32(r.k0, c).c_str()));
+      o(fmt("const float lki = %s;", ln_arrh32(r.k, c).c_str()));
+      o(fmt("const float lnPr = fmaxf(lk0 - lki + __logf(%s), -690.0f);", third_body32(r, c).c_str()));
+      c.log32 += 1; c.fp32 += 2;
+      std::string lnF = "0.0f";
+      if (r.blend == Blend::Troe) {
+        const double al = r.troe[0];
+        std::string Fc;
+        if (1.0 - al != 0.0) Fc = fmt("%s * __expf((float)T * %s)", F(1.0 - al).c_str(), F(-1.0 / r.troe[1]).c_str());
+        if (al != 0.0) Fc += (Fc.empty() ? "" : " + ") + fmt("%s * __expf((float)T * %s)", F(al).c_str(), F(-1.0 / r.troe[2]).c_str());
+        Fc += (Fc.empty() ? "" : " + ") + fmt("__expf(%s * iTf)", F(-r.troe[3]).c_str());
+        o("const float lFc = __log10f(" + Fc + ");");
+        o("const float xx = fmaf(lnPr, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
+        o("const float ff = __fdividef(xx, fmaf(-1.27f, lFc, 0.75f) - 0.14f * xx);");
+        o("const float lnF = __fdividef(2.30258509f * lFc, fmaf(ff, ff, 1.0f));");
+        c.exp32 += 3; c.log32 += 1; c.div32 += 2; c.fp32 += 14;
+        lnF = "lnF";
+      } else if (r.blend == Blend::Sri) {
+        o("const float lPr = lnPr * 0.434294482f;");
+        o(fmt("const float base = %s * __expf(%s * iTf) + __expf((float)T * %s);", F(r.sri[0]).c_str(), F(-r.sri[1]).c_str(),
+              F(-1.0 / r.sri[2]).c_str()));
+        o(fmt("const float lnF = %s + %s * lnTf + __fdividef(__logf(base), fmaf(lPr, lPr, 1.0f));", F(std::log(r.sri[3])).c_str(),
+              F(r.sri[4]).c_str()));
+        c.exp32 += 2; c.log32 += 1; c.div32 += 1; c.fp32 += 8;
+        lnF = "lnF";
+      }
+      if (r.kind == Kind::Falloff) lnRf = "lki + kx_ln_pr_ratio(lnPr) + " + lnF;
+      else lnRf = "lk0 + kx_ln_inv_1p(lnPr) + " + lnF;
+      c.exp32 += 1; c.log32 += 1; c.fp32 += 4;
+    } else {  // PLOG
+      const auto& t = r.plog;
+      auto lk = [&](size_t j) { return ln_arrh32(Arrh{t[j][1], t[j][2], t[j][3]}, c); };
+      o("float lkf;");
+      o(fmt("if (P <= %s) lkf = %s;", D(t[0][0]).c_str(), lk(0).c_str()));
+      for (size_t j = 0; j + 1 < t.size(); ++j) {
+        double l1 = std::log(t[j][0]), l2 = std::log(t[j + 1][0]);
+        o(fmt("else if (P < %s) { const float l1 = %s; lkf = fmaf(%s - l1, (lnPf - %s) * %s, l1); }", D(t[j + 1][0]).c_str(),
+              lk(j).c_str(), lk(j + 1).c_str(), F(l1).c_str(), F(1.0 / (l2 - l1)).c_str()));
+      }
+      o(fmt("else lkf = %s;", lk(t.size() - 1).c_str()));
+      lnRf = "lkf";
+      c.fp32 += 3;
+    }
+    for (auto& e : r.reac) {
+      lnRf += e.second == 1 ? fmt(" + lnCf_%d", e.first) : fmt(" + %d.0f * lnCf_%d", e.second, e.first);
+      c.fp32 += 1;
+    }
+    o("const float lnRf = " + lnRf + ";");
+    if (r.reversible) {
+      const int dn = sum_nu(r);
+      std::string s = nu_sum(r, "mu", c);
+      if (dn != 0) { s = fmt("fma(%s, lnPRT, %s)", D(-dn).c_str(), s.c_str()); c.fp64 += 1; }
+      o("const double q = kx_net_rate(lnRf, " + s + ");");
+      c.exp32 += 2; c.fp32 += 6;
+    } else {
+      o("const double q = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+      c.exp32 += 1; c.fp32 += 2;
+    }
+    if (rop) {
+      o(fmt("out_[(long long)%d * ld + i] = q;", i));
+    } else {
+      std::map<int, int> nu;
+      for (auto& e : r.prod) nu[e.first] += e.second;
+      for (auto& e : r.reac) nu[e.first] -= e.second;
+      for (auto& kv : nu) {
+        if (kv.second == 1) o(fmt("w_%d += q;", kv.first));
+        else if (kv.second == -1) o(fmt("w_%d -= q;", kv.first));
+        else if (kv.second != 0) o(fmt("w_%d = fma(%s, q, w_%d);", kv.first, D(kv.second).c_str(), kv.first));
+        if (kv.second != 0) c.fp64 += 1;
+      }
+    }
+    --o.ind;
+    o("}");
+  }
+  if (!rop)
+    for (int k = 0; k < m.ns; ++k) o(fmt("out_[(long long)%d * ld + i] = w_%d;", k, k));
+}
+
+// ------------------------------------------------------------------ thermo
+void emit_thermo(Out& o, const Mechanism& m, OpCounts& c) {
+  const auto flags = tmid_flags(m);
+  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
+  o("const double iT = 1.0 / T;");
+  o("double cp = 0.0, hs = 0.0;");
+  c.div64 += 1;
+  for (int k = 0; k < m.ns; ++k) {
+    const std::string fl = nasa_flag(m, k, flags);
+    const double* lo = &m.a_lo[7 * k];
+    const double* hi = &m.a_hi[7 * k];
+    // cp/R = a0 + a1 T + a2 T^2 + a3 T^3 + a4 T^4
+    std::string cp = sel(fl, lo[4], hi[4]);
+    for (int n = 3; n >= 0; --n) cp = fmt("fma(%s, T, %s)", cp.c_str(), sel(fl, lo[n], hi[n]).c_str());
+    // H/RT = a0 + a1/2 T + a2/3 T^2 + a3/4 T^3 + a4/5 T^4 + a5/T
+    std::string h = sel(fl, lo[4] / 5.0, hi[4] / 5.0);
+    for (int n = 3; n >= 0; --n) h = fmt("fma(%s, T, %s)", h.c_str(), sel(fl, lo[n] / (n + 1), hi[n] / (n + 1)).c_str());
+    h = fmt("fma(%s, iT, %s)", sel(fl, lo[5], hi[5]).c_str(), h.c_str());
+    o(fmt("{ const double yr = Y_[(long long)%d * ld + i] * %s;", k, D(R_U / m.W[k]).c_str()));
+    o(fmt("  cp = fma(yr, %s, cp);", cp.c_str()));
+    o(fmt("  hs = fma(yr, %s, hs); }", h.c_str()));
+    c.fp64 += 12;
+  }
+  o("out0_[i] = cp;");
+  o("out1_[i] = hs * T;");
+  c.fp64 += 1;
+}
+
+// ------------------------------------------------------------------ transport
+// Per-species work (X_k, eta_k, lambda_k) is unrolled; the O(N^2) pair sums
+// run as loops over coefficient tables in global memory (uniform addresses,
+// so every load is a broadcast) with each thread's species vectors staged in
+// its own column of shared memory, [species][thread].
+//
+// Wilke (the eta formula with phi_kj): with u_k = sqrt(eta_k) W_k^(-1/4) and
+// a_kj = (1 + W_k/W_j)^(-1/2)/sqrt(8),
+//   sum_j X_j phi_kj = S0_k + 2 u_k S1_k + u_k^2 S2_k,
+//   S0_k = sum_j a_kj X_j, S1_k = sum_j a_kj X_j/u_j, S2_k = sum_j a_kj X_j/u_j^2,
+// three products with a constant matrix; every term is positive.
+// Diffusion: S_k = sum_{j != k} X_j / D_kj(1 atm), each symmetric pair
+// evaluated once and added to both rows (Sec. 2.3.2), or the full matrix.
+double wilke_a(const Mechanism& m, int k, int j) { return 1.0 / std::sqrt(8.0 * (1.0 + m.W[k] / m.W[j])); }
+
+// p(L) = sum c_n L^n re-expanded about L0: d_m = sum_{n>=m} C(n,m) c_n L0^(n-m)
+void shift_poly(const double* cf, double L0, double scale, double out[5]) {
+  static const double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  for (int mm = 0; mm < 5; ++mm) {
+    long double d = 0;
+    for (int n = mm; n < 5; ++n) d += (long double)binom[n][mm] * cf[n] * std::pow((long double)L0, n - mm);
+    out[mm] = (double)(d * scale);
+  }
+}
+
+
+void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, OpCounts& c) {
+  const int ns = m.ns;
+  const bool mx = opt.mixed;
+  const char* TY = mx ? "float" : "double";
+  const char* FMA = mx ? "fmaf" : "fma";
+  const char* EXP = mx ? "exp2f" : "kx_exp";
+  const double L0 = mx ? 0.5 * (std::log(300.0) + std::log(3000.0)) : 0.0;
+  const double SC = mx ? 1.4426950408889634 : 1.0;      // exp2 form for float32
+  auto lit = [&](double v) { return mx ? F(v) : D(v); };
+  // coefficients of s * p(L) + add, in the kernel's variable (L, or L - L0 for float32)
+  auto coefs = [&](const double* cf, double s, double add, double out[5]) {
+    if (mx) shift_poly(cf, L0, s * SC, out);
+    else for (int n = 0; n < 5; ++n) out[n] = cf[n] * s;
+    out[0] += add * SC;
+  };
+  auto horner = [&](const double* cf, double s, double add) {
+    double d[5];
+    coefs(cf, s, add, d);
+    std::string r = lit(d[4]);
+    for (int n = 3; n >= 0; --n) r = fmt("%s(%s, L, %s)", FMA, r.c_str(), lit(d[n]).c_str());
+    return r;
+  };
+  auto cnt = [&](double n) { if (mx) c.fp32 += n; else c.fp64 += n; };
+  auto cexp = [&](double n) { if (mx) c.exp32 += n; else c.exp64 += n; };
+  // ---- module-scope tables
+  {
+    std::string a;
+    for (int k = 0; k < ns; ++k)
+      for (int j = 0; j < ns; ++j) a += lit(wilke_a(m, k, j)) + ((k == ns - 1 && j == ns - 1) ? "" : ",");
+    g(fmt("__device__ const %s kx_wa[%d] = {%s};", TY, ns * ns, a.c_str()));
+    std::string d;
+    int np = 0;
+    for (int k = 0; k < ns; ++k)
+      for (int j = (opt.diff_mode == 2 ? 0 : k + 1); j < ns; ++j) {
+        if (j == k) continue;
+        double cf[5];
+        coefs(&m.dif[5 * ((size_t)k * ns + j)], -1.0, 0.0, cf);
+        for (int n = 0; n < 5; ++n) d += lit(cf[n]) + ",";
+        ++np;
+      }
+    d += lit(0.0);
+    g(fmt("__device__ const %s kx_dc[%d] = {%s};", TY, 5 * np + 1, d.c_str()));
+  }
+  o(mx ? fmt("const float L = (float)(log(T) - %s);", D(L0).c_str()) : std::string("const double L = log(T);"));
+  c.log64 += 1;
+  o(fmt("%s* const sX = (%s*)kx_dyn;", TY, TY));
+  o(fmt("%s* const sZ1 = sX + %d;", TY, ns * opt.block));
+  o(fmt("%s* const sZ2 = sZ1 + %d;", TY, ns * opt.block));
+  o("const int t = threadIdx.x;");
+  std::string sy, sumY;
+  for (int k = 0; k < ns; ++k) {
+    o(fmt("const %s Yk_%d = (%s)Y_[(long long)%d * ld + i];", TY, k, TY, k));
+    o(fmt("const %s y_%d = Yk_%d * %s;", TY, k, k, lit(1.0 / m.W[k]).c_str()));
+    sy += (k ? " + y_" : "y_") + std::to_string(k);
+    sumY += (k ? " + Yk_" : "Yk_") + std::to_string(k);
+  }
+  o(fmt("const %s isig = %s / (%s);", TY, lit(1.0).c_str(), sy.c_str()));
+  o(fmt("const %s iWbar = %s / ((%s) * isig);", TY, lit(1.0).c_str(), sumY.c_str()));
+  cnt(3 * ns);
+  if (mx) c.div32 += 2; else c.div64 += 2;
+  // per species: X, u, z1 = X/u, z2 = X/u^2, and the Mathur sums
+  o(fmt("%s sl = 0, sil = 0;", TY));
+  for (int k = 0; k < ns; ++k) {
+    o(fmt("{ const %s X = y_%d * isig; sX[%d + t] = X;", TY, k, k * opt.block));
+    o(fmt("  const %s v = %s(%s);", TY, EXP, horner(&m.eta[5 * k], -0.5, 0.25 * std::log(m.W[k])).c_str()));
+    o(fmt("  const %s z1 = X * v; sZ1[%d + t] = z1; sZ2[%d + t] = z1 * v;", TY, k * opt.block, k * opt.block));
+    o(fmt("  const %s ll = %s;", TY, horner(&m.lam[5 * k], 1.0, 0.0).c_str()));
+    o(fmt("  sl = %s(X, %s(ll), sl); sil = %s(X, %s(-ll), sil); }", FMA, EXP, FMA, EXP));
+    cnt(16); cexp(3);
+  }
+  // Wilke rows
+  o(fmt("%s mu = 0;", TY));
+  for (int k = 0; k < ns; ++k) {
+    o(fmt("{ const %s u = %s(%s);", TY, EXP, horner(&m.eta[5 * k], 0.5, -0.25 * std::log(m.W[k])).c_str()));
+    o(fmt("  %s s0 = 0, s1 = 0, s2 = 0;", TY));
+    o(fmt("  const %s* a = kx_wa + %d;", TY, k * ns));
+    o("  #pragma unroll 4");
+    o(fmt("  for (int j = 0; j < %d; ++j) { const %s aj = a[j]; s0 = %s(aj, sX[j * %d + t], s0); s1 = %s(aj, sZ1[j * %d + t], s1); s2 = %s(aj, sZ2[j * %d + t], s2); }",
+          ns, TY, FMA, opt.block, FMA, opt.block, FMA, opt.block));
+    o(fmt("  mu += sX[%d + t] * (u * u * %s) / %s(u, %s(u, s2, %s * s1), s0); }", k * opt.block, lit(std::sqrt(m.W[k])).c_str(),
+          FMA, FMA, lit(2.0).c_str()));
+    cnt(3.0 * ns + 12); cexp(1);
+    if (mx) c.div32 += 1; else c.div64 += 1;
+  }
+  // diffusion: S in the sZ1 columns
+  o(fmt("%s* const sS = sZ1;", TY));
+  o(fmt("for (int k = 0; k < %d; ++k) sS[k * %d + t] = 0;", ns, opt.block));
+  int base = 0;
+  for (int k = 0; k < ns; ++k) {
+    if (opt.diff_mode == 2) {
+      o(fmt("{ %s Sk = 0; const %s* cf = kx_dc + %d;", TY, TY, 5 * base));
+      o("  #pragma unroll 2");
+      o(fmt("  for (int j = 0; j < %d; ++j) { if (j == %d) continue; const %s e = %s(%s(%s(%s(%s(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 5; Sk = %s(sX[j * %d + t], e, Sk); }",
+            ns, k, TY, EXP, FMA, FMA, FMA, FMA, FMA, opt.block));
+      o(fmt("  sS[%d + t] = Sk; }", k * opt.block));
+      base += ns - 1;
+      cnt(6.0 * (ns - 1)); cexp(ns - 1);
+    } else {
+      if (k == ns - 1) break;
+      o(fmt("{ %s Sk = sS[%d + t]; const %s Xk = sX[%d + t]; const %s* cf = kx_dc + %d;", TY, k * opt.block, TY, k * opt.block, TY,
+            5 * base));
+      o("  #pragma unroll 2");
+      o(fmt("  for (int j = %d; j < %d; ++j) { const %s e = %s(%s(%s(%s(%s(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 5; Sk = %s(sX[j * %d + t], e, Sk); sS[j * %d + t] = %s(Xk, e, sS[j * %d + t]); }",
+            k + 1, ns, TY, EXP, FMA, FMA, FMA, FMA, FMA, opt.block, opt.block, FMA, opt.block));
+      o(fmt("  sS[%d + t] = Sk; }", k * opt.block));
+      base += ns - 1 - k;
+      cnt(6.0 * (ns - 1 - k)); cexp(ns - 1 - k);
+    }
+  }
+  o(fmt("const double pr = %s / P;", D(P_ATM).c_str()));
+  o("out0_[i] = (double)mu;");
+  o(fmt("out1_[i] = (double)(%s * (sl + %s / sil));", lit(0.5).c_str(), lit(1.0).c_str()));
+  for (int k = 0; k < ns; ++k) {
+    // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
+    o(fmt("{ const %s Sk = sS[%d + t]; out2_[(long long)%d * ld + i] = (double)(Sk > 0 ? %s(-sX[%d + t], %s * iWbar, %s) / Sk : %s(%s)) * pr; }",
+          TY, k * opt.block, k, FMA, k * opt.block, lit(m.W[k]).c_str(), lit(1.0).c_str(), EXP,
+          horner(&m.dif[5 * ((size_t)k * ns + k)], 1.0, 0.0).c_str()));
+    cnt(3);
+    c.fp64 += 1;
+    if (mx) c.div32 += 1; else c.div64 += 1;
+  }
+}
+
+}  // namespace
+
+// Shared memory per thread of the transport kernels, in bytes.
+int transport_smem_per_thread(const Mechanism& m, bool mixed) { return 3 * m.ns * (mixed ? 4 : 8); }
+
+// ------------------------------------------------------------------ kernels
+std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
+                        OpCounts* counts) {
+  OpCounts c;
+  Out body, globals;
+  body.ind = 2;
+  globals.ind = 0;
+  std::string outs, nan_fill;
+  switch (kind) {
+    case KernelKind::Wdot:
+    case KernelKind::Rop: {
+      const bool rop = kind == KernelKind::Rop;
+      outs = "double* __restrict__ out_";
+      nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);
+      if (opt.mixed) emit_rates_mixed(body, m, rop, c);
+      else emit_rates64(body, m, opt, rop, c);
+      break;
+    }
+    case KernelKind::Thermo:
+      outs = "double* __restrict__ out0_, double* __restrict__ out1_";
+      nan_fill = "out0_[i] = KX_NAN; out1_[i] = KX_NAN;";
+      emit_thermo(body, m, c);
+      break;
+    case KernelKind::Transport:
+      outs = "double* __restrict__ out0_, double* __restrict__ out1_, double* __restrict__ out2_";
+      nan_fill = fmt("out0_[i] = KX_NAN; out1_[i] = KX_NAN; for (int k = 0; k < %d; ++k) out2_[(long long)k * ld + i] = KX_NAN;", m.ns);
+      emit_transport(body, globals, m, opt, c);
+      break;
+    case KernelKind::Vjp:
+      return "";
+  }
+  std::ostringstream s;
+  s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
+  s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
+  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[768];\n";
+  s << kTables << "\n" << kDevicePrelude << "\n";
+  s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
+  s << globals.o.str();
+  s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ") " << entry
+    << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
+    << outs << ", long long n)\n{\n";
+  s << "  kx_load_tables();\n";
+  s << "  for (long long i = (long long)blockIdx.x * " << opt.block << " + threadIdx.x; i < n; i += (long long)gridDim.x * "
+    << opt.block << ") {\n";
+  s << "    const double T = T_[i], P = P_[i];\n";
+  s << "    if (!(T > 0.0 && P > 0.0 && T < KX_INF && P < KX_INF)) { " << nan_fill << " continue; }\n";
+  s << body.o.str();
+  s << "  }\n}\n";
+  if (counts) *counts = c;
+  return s.str();
+}
+
+}  // namespace kx

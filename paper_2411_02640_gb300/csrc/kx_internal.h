@@ -1,0 +1,86 @@
+// Internal declarations of the kx library: the mechanism model read from a
+// KXMECH file, the CUDA source emitter and its per-point operation counts.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/kx.h"
+
+namespace kx {
+
+constexpr double R_U = 8314.46261815324;   // J/(kmol K)
+constexpr double P_ATM = 101325.0;         // Pa
+
+struct Arrh {
+  double A = 0.0, beta = 0.0, E = 0.0;      // k = A T^beta exp(-E/T), E in K
+};
+
+enum class Kind { Elementary, ThreeBody, Falloff, ChemAct, Plog };
+enum class Blend { Lindemann, Troe, Sri };
+
+struct Reaction {
+  Kind kind = Kind::Elementary;
+  bool reversible = true;
+  std::vector<std::pair<int, int>> reac, prod;   // (species, stoichiometric coefficient)
+  Arrh k;                                        // k_f, k_inf (falloff) or k_inf (chem. activated)
+  Arrh k0;                                       // k_0 of falloff / chemically activated reactions
+  bool has_k0 = false;
+  double default_eff = 1.0;
+  std::vector<std::pair<int, double>> eff;       // third-body efficiencies that differ from default
+  int collider = -1;                             // single-species third body, or -1
+  Blend blend = Blend::Lindemann;
+  double troe[4] = {0, 0, 0, 0};                 // alpha, T***, T*, T**
+  double sri[5] = {0, 0, 0, 1, 0};               // a, b, c, d, e
+  std::vector<std::array<double, 4>> plog;       // (p [Pa], A, beta, E), ascending p
+  bool third_body() const { return kind == Kind::ThreeBody || kind == Kind::Falloff || kind == Kind::ChemAct; }
+};
+
+struct Mechanism {
+  std::string name;
+  std::vector<std::string> elements;
+  int ns = 0;
+  std::vector<std::string> species;
+  std::vector<double> W;                 // kg/kmol
+  std::vector<int> comp;                 // [ns][n_elements]
+  std::vector<char> inert;
+  std::vector<double> Tlow, Tmid, Thigh;
+  std::vector<double> a_lo, a_hi;        // [ns][7] NASA-7
+  std::vector<double> eta, lam;          // [ns][5]: ln eta, ln lambda as polynomials in ln T
+  std::vector<double> dif;               // [ns][ns][5]: ln D_jk at p_atm
+  std::vector<Reaction> rx;
+  int nr() const { return (int)rx.size(); }
+};
+
+// Parse and validate a KXMECH 1 file.  Returns KX_OK or an error code with a message.
+kx_status parse_mechanism(const std::string& path, Mechanism& m, std::string& err);
+
+enum class KernelKind { Wdot, Rop, Thermo, Transport, Vjp };
+
+struct EmitOptions {
+  bool mixed = false;       // float32 bulk arithmetic
+  int diff_mode = 1;        // 1 symmetric pairs, 2 full matrix
+  int kc_mode = 0;          // 0 log space, 1 per-species exponential products
+  int block = 128;
+};
+
+// Operation counts per point, tallied while emitting (library calls such as
+// exp and log counted once each, in their own columns).
+struct OpCounts {
+  double fp64 = 0, fp32 = 0, exp64 = 0, log64 = 0, div64 = 0, exp32 = 0, log32 = 0, div32 = 0;
+};
+
+// CUDA C++ source of one kernel, entry point named `entry`.
+std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
+                        OpCounts* counts);
+
+// Dynamic shared memory per thread that a kernel of this kind needs.
+int transport_smem_per_thread(const Mechanism& m, bool mixed);
+
+// Device-side helper functions prepended to every generated kernel.
+extern const char* kDevicePrelude;
+
+}  // namespace kx

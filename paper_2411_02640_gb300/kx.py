@@ -1,0 +1,191 @@
+"""Python binding of libkx (ctypes): argument marshalling only.
+
+Every computation happens in the library's CUDA kernels.  Tensors are
+torch CUDA float64 tensors in the library's layout (T[n], p[n],
+Y[N_s, ld], outputs likewise); the work is enqueued on the current torch
+stream (or the stream given).  There is no CPU fallback: if libkx.so is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+from . import build as _build
+
+_lib: Optional[ctypes.CDLL] = None
+
+FP64, MIXED = 0, 1
+_PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+
+KERNELS = ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "transport_fp64", "transport_mixed", "vjp")
+
+
+class KxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"kx error {status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("diff_mode", ctypes.c_int), ("kc_mode", ctypes.c_int), ("maxrreg", ctypes.c_int),
+                ("block", ctypes.c_int), ("lazy", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("libmath", ctypes.c_int), ("compile_only", ctypes.c_int), ("cache_dir", ctypes.c_char_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libkx.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libkx.so not found at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+        L.kx_load_mechanism.argtypes = [ctypes.c_char_p, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+        L.kx_free_mechanism.argtypes = [vp]
+        L.kx_mechanism_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.kx_production_rates.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
+        L.kx_rates_of_progress.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
+        L.kx_thermo.argtypes = [vp, dp, dp, dp, i64, dp, dp, i64, vp]
+        L.kx_transport.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, ctypes.c_int, vp]
+        L.kx_production_rates_vjp.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, vp]
+        L.kx_kernel_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.kx_status_string.argtypes = [ctypes.c_int]
+        L.kx_status_string.restype = ctypes.c_char_p
+        L.kx_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        L = lib()
+        raise KxError(status, (L.kx_last_error() or b"").decode() or L.kx_status_string(status).decode())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Mechanism:
+    """A mechanism compiled into GPU kernels.
+
+    ``Mechanism(path, diff_mode=..., kc_mode=..., block=..., libmath=...,
+    lazy=..., verbose=..., compile_only=..., cache_dir=...)``."""
+
+    def __init__(self, path: str, **opts):
+        L = lib()
+        o = Options()
+        for k, v in opts.items():
+            if k == "cache_dir":
+                o.cache_dir = v.encode() if v else None
+            else:
+                setattr(o, k, int(v))
+        self._opts = o
+        h = ctypes.c_void_p()
+        _check(L.kx_load_mechanism(path.encode(), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        ns, nr = ctypes.c_int(), ctypes.c_int()
+        _check(L.kx_mechanism_info(h, ctypes.byref(ns), ctypes.byref(nr), None))
+        self.n_species, self.n_reactions = ns.value, nr.value
+        W = (ctypes.c_double * ns.value)()
+        _check(L.kx_mechanism_info(h, None, None, W))
+        self.W = list(W)
+        self.path = path
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().kx_free_mechanism(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- helpers
+    def _state(self, T, p, Y):
+        import torch
+        for t in (T, p, Y):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+                raise TypeError("T, p and Y must be CUDA float64 tensors")
+        n = T.shape[0]
+        if p.shape[0] != n or Y.dim() != 2 or Y.shape[0] != self.n_species or Y.shape[1] < n:
+            raise ValueError("expected T[n], p[n], Y[N_s, >= n]")
+        if not (T.is_contiguous() and p.is_contiguous() and Y.stride(1) == 1):
+            raise ValueError("T and p must be contiguous and Y point-contiguous")
+        return n, Y.stride(0)
+
+    def _alloc(self, rows, n, ld, like):
+        import torch
+        if rows is None:
+            return torch.empty(n, dtype=torch.float64, device=like.device)
+        return torch.empty((rows, ld), dtype=torch.float64, device=like.device)
+
+    # -------------------------------------------------------------- calls
+    def production_rates(self, T, p, Y, out=None, precision="fp64", stream=None):
+        n, ld = self._state(T, p, Y)
+        out = out if out is not None else self._alloc(self.n_species, n, ld, T)
+        assert out.stride(0) == ld and out.shape[0] == self.n_species
+        _check(lib().kx_production_rates(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _PREC[precision],
+                                          _stream(stream)))
+        return out
+
+    def rates_of_progress(self, T, p, Y, out=None, precision="fp64", stream=None):
+        n, ld = self._state(T, p, Y)
+        out = out if out is not None else self._alloc(self.n_reactions, n, ld, T)
+        assert out.stride(0) == ld and out.shape[0] == self.n_reactions
+        _check(lib().kx_rates_of_progress(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _PREC[precision],
+                                           _stream(stream)))
+        return out
+
+    def thermo(self, T, p, Y, out: Optional[Tuple] = None, stream=None):
+        n, ld = self._state(T, p, Y)
+        cp, h = out if out is not None else (self._alloc(None, n, ld, T), self._alloc(None, n, ld, T))
+        _check(lib().kx_thermo(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(cp), _ptr(h), n, _stream(stream)))
+        return cp, h
+
+    def transport(self, T, p, Y, out: Optional[Tuple] = None, precision="fp64", stream=None):
+        n, ld = self._state(T, p, Y)
+        if out is None:
+            out = (self._alloc(None, n, ld, T), self._alloc(None, n, ld, T), self._alloc(self.n_species, n, ld, T))
+        mu, lam, D = out
+        assert D.stride(0) == ld
+        _check(lib().kx_transport(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(mu), _ptr(lam), _ptr(D), n,
+                                  _PREC[precision], _stream(stream)))
+        return mu, lam, D
+
+    def production_rates_vjp(self, T, p, Y, v, out: Optional[Tuple] = None, stream=None):
+        n, ld = self._state(T, p, Y)
+        assert v.shape[0] == self.n_species and v.stride(0) == ld and v.dtype == Y.dtype
+        if out is None:
+            out = (self._alloc(None, n, ld, T), self._alloc(self.n_species, n, ld, T))
+        gT, gY = out
+        _check(lib().kx_production_rates_vjp(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(v), _ptr(gT), _ptr(gY), n,
+                                             _stream(stream)))
+        return gT, gY
+
+    def kernel_info(self, name: str) -> dict:
+        r, lb = ctypes.c_int(), ctypes.c_int()
+        cs, f64, f32, ex = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().kx_kernel_info(self.h, name.encode(), ctypes.byref(r), ctypes.byref(lb), ctypes.byref(cs),
+                                    ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(ex)))
+        return dict(registers=r.value, spill_bytes=lb.value, compile_seconds=cs.value, fp64_ops=f64.value,
+                    fp32_ops=f32.value, exps=ex.value)

@@ -1,0 +1,90 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol the header
+declares, rejects bad input with the documented codes, and the emitter's
+kernels compile with NVRTC for sm_103a (no GPU needed for either)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2411_02640_gb300 import kx, synth
+from tests import toys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "kx.h")).read()
+    return sorted(set(re.findall(r"\b(kx_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = kx.lib()
+    names = declared_symbols()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_status_strings():
+    L = kx.lib()
+    for s in range(11):
+        assert L.kx_status_string(s)
+
+
+def _load(path, **opts):
+    o = kx.Options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    st = kx.lib().kx_load_mechanism(path.encode(), ctypes.byref(o), ctypes.byref(h))
+    return st, h
+
+
+def test_error_codes(tmp_path):
+    assert _load(str(tmp_path / "missing.kxmech"))[0] == 1            # KX_ERR_IO
+    bad = tmp_path / "bad.kxmech"
+    bad.write_text("KXMECH 1\nspecies x\n")
+    assert _load(str(bad))[0] == 2                                    # KX_ERR_PARSE
+    m, path = toys.toy("unb", [toys.recomb("elementary")], str(tmp_path))
+    text = open(path).read().replace("products 1 2 1", "products 1 0 1")
+    unb = tmp_path / "unbalanced.kxmech"
+    unb.write_text(text)
+    assert _load(str(unb))[0] == 3                                    # KX_ERR_UNBALANCED
+    assert _load(path, block=100)[0] == 4                             # KX_ERR_ARG
+    assert b"multiple of 32" in kx.lib().kx_last_error()
+    assert _load(path, kc_mode=7)[0] == 4
+
+
+@pytest.mark.parametrize("name", ["h2o2_9_21"])
+def test_emitted_kernels_compile_for_sm103a(name, tmp_path):
+    path = synth.mechanism_file(name, str(tmp_path))
+    m = kx.Mechanism(path, compile_only=1, cache_dir=str(tmp_path / "cache"))
+    for k in ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "transport_fp64", "transport_mixed"):
+        info = m.kernel_info(k)
+        assert 0 < info["registers"] <= 255, (k, info)
+    # a compile-only handle refuses launches
+    L = kx.lib()
+    st = L.kx_production_rates(m.h, 1, 1, 1, 4, 1, 4, 0, None)
+    assert st == 10                                                   # KX_ERR_UNSUPPORTED
+    assert L.kx_production_rates(m.h, 1, 1, 1, 2, 1, 4, 0, None) == 4  # ld < n
+
+
+def test_toy_mechanisms_compile(tmp_path):
+    """Every reaction kind the file format has (three-body with a collider,
+    Lindemann/Troe/SRI falloff, chemically activated, PLOG, irreversible)
+    goes through the emitter and NVRTC."""
+    from paper_2411_02640_gb300.synth import P_ATM, Reaction
+    rx = [toys.recomb("elementary"), toys.recomb("three_body", efficiencies={3: 2.0}),
+          toys.recomb("three_body", collider=3), toys.recomb("falloff", rate_low=(1e12, 0.1, 100.0)),
+          toys.recomb("falloff", rate_low=(1e12, 0.1, 100.0), troe=(0.5, 100.0, 2000.0, 3000.0)),
+          toys.recomb("falloff", rate_low=(1e12, 0.1, 100.0), sri=(0.5, 200.0, 1000.0, 1.2, 0.1)),
+          toys.recomb("chem_act", rate_low=(1e12, 0.1, 100.0), troe=(0.5, 100.0, 2000.0, 3000.0)),
+          Reaction(kind="plog", reversible=True, reactants=[(0, 1), (1, 1)], products=[(2, 1)], rate=(0, 0, 0),
+                   plog=[(0.1 * P_ATM, 1e9, 0.2, 300.0), (10 * P_ATM, 1e11, -0.3, 900.0)]),
+          Reaction(kind="elementary", reversible=False, reactants=[(2, 1)], products=[(0, 1), (1, 1)],
+                   rate=(1e13, 0.0, 2e4))]
+    _, path = toys.toy("allkinds", rx, str(tmp_path))
+    m = kx.Mechanism(path, compile_only=1, cache_dir=str(tmp_path / "cache"))
+    for k in ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed"):
+        assert m.kernel_info(k)["registers"] > 0
