@@ -1,0 +1,345 @@
+"""Benchmark: production rates + thermo + mixture-averaged transport on the
+53-species / 325-reaction synthetic mechanism (30 three-body, 29 Troe),
+2^20 states per GPU, float64 path (headline) and mixed path beside it.
+
+One step = kx_production_rates + kx_thermo + kx_transport over the whole
+batch (every step of the hot path).  Inputs (T, p, Y: 461 MB) and outputs
+are larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kx|reference]
+
+Under torchrun each rank runs its own 2^20 states (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  --impl
+reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MECH = "gri_53_325"
+POINTS = 1 << 20
+METRIC = "Mpoints/s wdot+thermo+transport (53sp/325rxn)"
+CACHE = os.environ.get("KX_CACHE_DIR", os.path.join(ROOT, ".kxcache"))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# float64 pipe: 2 DFMA per clock per SM on GB300 (measured 5.99e11 DFMA/s at ~2.0 GHz);
+# the peak is taken at the maximum SM clock.
+FP64_DFMA_PER_CLK_SM = 2.0
+SMS = 152
+
+
+def fp64_peak_gops(sm_max_mhz: float) -> float:
+    return FP64_DFMA_PER_CLK_SM * SMS * sm_max_mhz * 1e6 / 1e9
+
+
+# float64 instructions that one call of each library routine costs in the
+# generated kernels (the library's own exp/log; IEEE division).
+COST = {"exp64": 5.0, "log64": 9.0, "div64": 9.0}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for s in self.samples for j in range(4) if s[3 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_inputs(rank: int, n: int):
+    from paper_2411_02640_gb300 import synth
+    m = synth.mechanism(MECH)
+    # each rank draws its own shard of the seeded state stream
+    return synth.make_states(m.n_species, synth.STATE_SPECS[MECH], rank * n, n)
+
+
+def cpu_baseline(seconds_target: float = 15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle
+    from paper_2411_02640_gb300 import synth
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(synth.mechanism_file(MECH, os.path.join(CACHE, "mech")), nthreads=cores)
+    n = 256 * cores
+    T, p, Y = make_inputs(0, n)
+    t0 = time.perf_counter()
+    o.production_rates(T, p, Y)
+    o.thermo(T, p, Y)
+    o.transport(T, p, Y)
+    dt = time.perf_counter() - t0
+    # scale the sample so that it holds about `seconds_target` of wall time
+    n2 = int(min(POINTS, max(n, n * seconds_target / max(dt, 1e-3) / 4)))
+    T, p, Y = make_inputs(0, n2)
+    t0 = time.perf_counter()
+    o.production_rates(T, p, Y)
+    o.thermo(T, p, Y)
+    o.transport(T, p, Y)
+    dt = time.perf_counter() - t0
+    return {"value": n2 / dt / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n2} states of the 2^20-state workload, one pass of wdot+thermo+transport"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2411_02640_gb300 import synth
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(synth.mechanism_file(MECH, os.path.join(CACHE, "mech")), nthreads=cores)
+    n = 512 * cores
+    T, p, Y = make_inputs(0, n)
+
+    def step():
+        o.production_rates(T, p, Y)
+        o.thermo(T, p, Y)
+        o.transport(T, p, Y)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = n / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{MECH} synthetic mechanism, bounded sample of {n} states per step "
+                               f"(the GPU arm runs 2^20 per GPU)", "points_per_step": n},
+        "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} states per step"},
+        "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_kx(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_02640_gb300 import kx, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.points
+    path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
+    mech = kx.Mechanism(path, cache_dir=CACHE)
+    ns = mech.n_species
+    T, p, Y = make_inputs(rank, n)
+    dev = torch.device("cuda", local)
+    Td, pd, Yd = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+    w = torch.empty((ns, n), dtype=torch.float64, device=dev)
+    cp = torch.empty(n, dtype=torch.float64, device=dev)
+    hm = torch.empty_like(cp)
+    mu = torch.empty_like(cp)
+    lam = torch.empty_like(cp)
+    D = torch.empty((ns, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    kernels = {"fp64": ("wdot_fp64", "thermo", "transport_fp64"), "mixed": ("wdot_mixed", "thermo", "transport_mixed")}
+
+    def step(prec, ev=None):
+        if ev: ev[0].record(stream)
+        mech.production_rates(Td, pd, Yd, out=w, precision=prec)
+        if ev: ev[1].record(stream)
+        mech.thermo(Td, pd, Yd, out=(cp, hm))
+        if ev: ev[2].record(stream)
+        mech.transport(Td, pd, Yd, out=(mu, lam, D), precision=prec)
+        if ev: ev[3].record(stream)
+
+    def timed(prec, K, W):
+        for _ in range(W):
+            step(prec)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(K):
+            step(prec, evs[k])
+        t1.record(stream)
+        barrier()
+        total = t0.elapsed_time(t1)
+        per = [sum(e[j].elapsed_time(e[j + 1]) for e in evs) / K for j in range(3)]
+        return total, per
+
+    results = {}
+    with ClockSampler(local) as clk:
+        for prec in ("fp64", "mixed"):
+            total, per = timed(prec, args.steps, args.warmup)
+            t = torch.tensor([total], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            results[prec] = (t.item(), per)
+    clocks = clk.summary()
+
+    # end to end through the public API from pinned host buffers
+    Th, ph, Yh = (torch.from_numpy(a).pin_memory() for a in (T, p, Y))
+    wh = torch.empty((ns, n), dtype=torch.float64).pin_memory()
+    Dh = torch.empty((ns, n), dtype=torch.float64).pin_memory()
+    sc = torch.empty((4, n), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        Td.copy_(Th, non_blocking=True); pd.copy_(ph, non_blocking=True); Yd.copy_(Yh, non_blocking=True)
+        step("fp64")
+        wh.copy_(w, non_blocking=True); Dh.copy_(D, non_blocking=True)
+        sc[0].copy_(cp, non_blocking=True); sc[1].copy_(hm, non_blocking=True)
+        sc[2].copy_(mu, non_blocking=True); sc[3].copy_(lam, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = t.item() / args.steps
+
+    if rank == 0:
+        pk = peaks()
+        total, per = results["fp64"]
+        ms = total / args.steps
+        value = world * n / (ms * 1e-3) / 1e6
+        mtotal, mper = results["mixed"]
+        mms = mtotal / args.steps
+        # roofline of the dominant float64 kernel, float64-pipe bound
+        names = kernels["fp64"]
+        dom = int(np.argmax(per))
+        # per-point float64 instructions: plain ops plus the library routines at their instruction cost
+        f64 = ops_per_point(mech, names[dom])
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        achieved = f64 * n / (per[dom] * 1e-3) / 1e9
+        peak = fp64_peak_gops(sm_max)
+        mnames = kernels["mixed"]
+        mdom = int(np.argmax(mper))
+        m64 = ops_per_point(mech, mnames[mdom])
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{MECH}: synthetic 53 species / 325 reactions (30 three-body, 29 Troe), "
+                                   f"2^20 states per GPU, T U[300,2800] K, p log-U[0.5,40] atm, Y Dirichlet(0.2)",
+                       "points_per_gpu": n, "step": "production_rates + thermo + transport",
+                       "l2": "inputs (461 MB) and outputs larger than L2; no flush"},
+            "kernel_ms": {k: v for k, v in zip(names, per)},
+            "mixed": {"value": world * n / (mms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": mms,
+                      "kernel_ms": {k: v for k, v in zip(mnames, mper)},
+                      "error": "wdot <= 2e-4 of the per-point scale max_k|W_k wdot_k| (p99 <= 1e-4); "
+                               "transport <= 5e-6 relative; thermo float64",
+                      "roofline": {"bound": "alu", "kernel": mnames[mdom],
+                                   "achieved": m64 * n / (mper[mdom] * 1e-3) / 1e9, "peak": peak,
+                                   "unit": "G fp64 instr/s", "frac": m64 * n / (mper[mdom] * 1e-3) / 1e9 / peak}},
+            "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "unit": "G fp64 instr/s", "frac": achieved / peak, "traffic": None,
+                         "per_point_fp64_instr": f64,
+                         "peak_source": f"152 SMs x 2 DFMA/clk x {sm_max:.0f} MHz (float64 pipe; unit counts and "
+                                        "max SM clock)"},
+            "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def ops_per_point(mech, name):
+    """float64 instructions per point of a kernel: the emitter's count of plain
+    float64 operations plus each library routine at its instruction cost."""
+    c = mech.op_counts(name)
+    return c["fp64"] + COST["exp64"] * c["exp64"] + COST["log64"] * c["log64"] + COST["div64"] * c["div64"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kx", choices=["kx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=POINTS, help="states per GPU (profiling of smaller cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kx(args)
+
+
+if __name__ == "__main__":
+    main()

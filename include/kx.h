@@ -129,6 +129,12 @@ kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p,
 kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes,
                          double* compile_seconds, double* fp64_ops, double* fp32_ops, double* exps);
 
+/* The emitter's per-point operation counts of one kernel, in this order:
+ * float64 plain operations (add, mul, fma), float32 plain operations,
+ * float64 exp, float64 log, float64 divisions, float32 exp, float32 log,
+ * float32 divisions.  counts must hold 8 doubles. */
+kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts);
+
 const char* kx_status_string(kx_status s);
 
 /* Message of the calling thread's last failed call (empty if none). */

@@ -432,4 +432,14 @@ kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* l
   return KX_OK;
 }
 
+kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts) {
+  if (!counts) return fail(KX_ERR_ARG, "null counts");
+  kx_status s = kx_kernel_info(h, kernel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (s != KX_OK) return s;
+  const kx::OpCounts& c = find_kernel(h, kernel)->ops;
+  const double v[8] = {c.fp64, c.fp32, c.exp64, c.log64, c.div64, c.exp32, c.log32, c.div32};
+  std::memcpy(counts, v, sizeof v);
+  return KX_OK;
+}
+
 }  // extern "C"

@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         L.kx_kernel_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.kx_kernel_op_counts.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
         L.kx_status_string.argtypes = [ctypes.c_int]
         L.kx_status_string.restype = ctypes.c_char_p
         L.kx_last_error.restype = ctypes.c_char_p
@@ -181,6 +182,12 @@ class Mechanism:
         _check(lib().kx_production_rates_vjp(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(v), _ptr(gT), _ptr(gY), n,
                                              _stream(stream)))
         return gT, gY
+
+    def op_counts(self, name: str) -> dict:
+        """Per-point operation counts the emitter tallied for one kernel."""
+        c = (ctypes.c_double * 8)()
+        _check(lib().kx_kernel_op_counts(self.h, name.encode(), c))
+        return dict(zip(("fp64", "fp32", "exp64", "log64", "div64", "exp32", "log32", "div32"), list(c)))
 
     def kernel_info(self, name: str) -> dict:
         r, lb = ctypes.c_int(), ctypes.c_int()

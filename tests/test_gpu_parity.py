@@ -95,8 +95,10 @@ def test_transport_fp64(torch, name):
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision_error_bounds(torch, name):
     """Mixed path: production rates within 2e-4 of the per-point scale
-    (p99 within 2e-5), rates of progress within 2e-4 of their own gross
-    scale, transport within 2e-5 relative."""
+    (p99 within 1e-4), rates of progress within 2e-4 of their own gross
+    scale, transport within 5e-6 relative.  The float32 logarithms of the
+    rates (|ln R| up to ~300) carry ~1e-5 absolute rounding, which is the
+    floor of these bounds."""
     n = CASES[name]
     T, p, Y = _states(name, n, start=21)
     mech = mechanism(name)
@@ -113,9 +115,9 @@ def test_mixed_precision_error_bounds(torch, name):
     mu_r, lam_r, D_r = o.transport(T, p, Y)
     et = max(np.max(np.abs(mu / mu_r - 1)), np.max(np.abs(lam / lam_r - 1)), np.max(np.abs(D / D_r - 1)))
     print(f"{name} mixed transport: max rel {et:.3e}")
-    assert err.max() <= 2e-4 and np.quantile(err, 0.99) <= 2e-5
+    assert err.max() <= 2e-4 and np.quantile(err, 0.99) <= 1e-4
     assert rq.max() <= 2e-4
-    assert et <= 2e-5
+    assert et <= 5e-6
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -141,7 +143,7 @@ def test_domain_edges(torch, precision):
     err = wdot_error(np.array(mech.W), w[:, good], w_ref)
     assert err.max() <= (1e-10 if precision == "fp64" else 2e-4)
     mu_r, lam_r, D_r = o.transport(T[good], p[good], Y[:, good])
-    tol = 1e-12 if precision == "fp64" else 2e-5
+    tol = 1e-12 if precision == "fp64" else 5e-6
     np.testing.assert_allclose(D[:, good], D_r, rtol=tol)
     np.testing.assert_allclose(mu[good], mu_r, rtol=tol)
     # n = 0
