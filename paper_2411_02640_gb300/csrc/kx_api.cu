@@ -292,7 +292,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
       {"wdot_fp64", kx::KernelKind::Wdot, false},       {"wdot_mixed", kx::KernelKind::Wdot, true},
       {"rop_fp64", kx::KernelKind::Rop, false},         {"rop_mixed", kx::KernelKind::Rop, true},
       {"thermo", kx::KernelKind::Thermo, false},        {"transport_fp64", kx::KernelKind::Transport, false},
-      {"transport_mixed", kx::KernelKind::Transport, true},
+      {"transport_mixed", kx::KernelKind::Transport, true}, {"vjp", kx::KernelKind::Vjp, false},
   };
   for (const Spec& sp : specs) {
     std::unique_ptr<Kernel> k(new Kernel());

@@ -46,6 +46,31 @@ const char* kDevicePrelude = R"KXPRE(
 #define KX_INV_LN10 0.43429448190325182765
 #define KX_LN10 2.30258509299404568402
 #define KX_LOG2E_F 1.44269504f
+#define KX_RND_F 12582912.0f          /* 1.5 * 2^23: adding it rounds a float to an integer */
+
+// Conversions between float64 and float32 by integer operations: on this
+// GPU the F2F/I2F conversions issue on the float64 pipe, which is the
+// bottleneck, while integer ops go to the ALU pipe.
+// Round-to-nearest float of a double within float's normal range; |x| below
+// it gives 0, above it (and nan) gives +-inf.
+__device__ __forceinline__ float kx_d2f(double x) {
+  const long long b = __double_as_longlong(x) + (1LL << 28);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  const unsigned sgn = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sgn);
+  if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+  return __uint_as_float(sgn | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | ((unsigned)b >> 29));
+}
+// Exact double of a normal float (zero and subnormals give 0).
+__device__ __forceinline__ double kx_f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+// Nearest integer of a float with |t| < 2^22, without the XU pipe.
+__device__ __forceinline__ int kx_rint(float t) { return __float_as_int(t + KX_RND_F) - 0x4b400000; }
 
 // float64 exp: x = k ln2/256 + r with k = rint(x 256/ln2) found in float32
 // and r by a two-constant Cody-Waite reduction in float64; e^r - 1 =
@@ -58,13 +83,13 @@ __device__ __forceinline__ double kx_exp(double x) {
   return exp(x);
 #else
   if (!(fabs(x) < 700.0)) return exp(x);
-  const int k = __float2int_rn(__double2float_rn(x) * KX_256_OVER_LN2F);
+  const int k = kx_rint(kx_d2f(x) * KX_256_OVER_LN2F);
   const double kd = (double)k;
   double r = fma(kd, -KX_LN2_256_HI, x);
   r = fma(kd, -KX_LN2_256_LO, r);
-  const float rf = __double2float_rn(r);
+  const float rf = kx_d2f(r);
   const float qf = fmaf(fmaf(fmaf(rf, 8.33333333e-3f, 4.16666667e-2f), rf, 0.166666667f), rf, 0.5f);
-  const double s = fma(r * r, (double)qf, r);
+  const double s = fma(r * r, kx_f2d(qf), r);
   const double tj = kx_s_exp[k & 255];
   const double v = fma(tj, s, tj);
   return __hiloint2double(__double2hiint(v) + (int)((unsigned)(k >> 8) << 20), __double2loint(v));
@@ -84,40 +109,41 @@ __device__ __forceinline__ double kx_log(double x) {
   const int e = (hi >> 20) - 1023;
   const int j = (hi >> 12) & 0xff;
   const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));
-  const double u = m - fma((double)(2 * j + 1), 1.0 / 512.0, 1.0);
-  const double r = u * kx_s_log[3 * j];
-  const float rf = __double2float_rn(r);
+  const double r = (m - kx_s_log[4 * j]) * kx_s_log[4 * j + 1];
+  const float rf = kx_d2f(r);
   const float qf = fmaf(fmaf(fmaf(rf, -0.2f, 0.25f), rf, -0.333333333f), rf, 0.5f);
-  const double t = fma(-(r * r), (double)qf, r);
+  const double t = fma(-(r * r), kx_f2d(qf), r);
   const double ed = (double)e;
-  return fma(ed, KX_LN2_HI, kx_s_log[3 * j + 1]) + (fma(ed, KX_LN2_LO, kx_s_log[3 * j + 2]) + t);
+  return fma(ed, KX_LN2_HI, kx_s_log[4 * j + 2]) + (fma(ed, KX_LN2_LO, kx_s_log[4 * j + 3]) + t);
 #endif
 }
 
 __device__ __forceinline__ void kx_load_tables() {
 #ifndef KX_LIBMATH
   for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
-  for (int t = threadIdx.x; t < 768; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
   __syncthreads();
 #endif
 }
 
 // fac * 2^t as a float64 for |t| up to ~1100 and fac in [0, 1]: the
-// mantissa comes from float32 exp2 of the fractional part, the power of two
-// is added to the float64 exponent field (no float64 arithmetic).
+// mantissa comes from float32 exp2 of t minus its nearest integer n, the
+// power 2^n is added to the float64 exponent field (no float64 arithmetic).
 __device__ __forceinline__ double kx_pow2_scaled(float t, float fac) {
-  const float n = floorf(t);
-  const float m = exp2f(t - n) * fac;
+  if (!(t > -4000.0f && t < 4000.0f)) {
+    if (t != t || fac != fac) return KX_NAN;
+    return (t > 0.0f && fac > 0.0f) ? KX_INF : 0.0;
+  }
+  const float tr = t + KX_RND_F;
+  const int n = __float_as_int(tr) - 0x4b400000;
+  const float m = exp2f(t - (tr - KX_RND_F)) * fac;
   if (!(m >= 0.0f)) return KX_NAN;
-  if (!(n < 4096.0f)) return m == 0.0f ? 0.0 : KX_INF;
-  if (!(n > -4096.0f)) return 0.0;
-  const double dm = (double)m;
-  const int ni = (int)n;
+  const double dm = kx_f2d(m);
   const int hi = __double2hiint(dm);
-  const int E = ((hi >> 20) & 0x7ff) + ni;
+  const int E = ((hi >> 20) & 0x7ff) + n;
   if (m == 0.0f || E <= 0) return 0.0;
   if (E >= 0x7ff) return KX_INF;
-  return __hiloint2double(hi + (int)((unsigned)ni << 20), __double2loint(dm));
+  return __hiloint2double(hi + (int)((unsigned)n << 20), __double2loint(dm));
 }
 
 // Net rate of progress R_f - R_r from ln R_f (float32) and the float64
@@ -126,7 +152,7 @@ __device__ __forceinline__ double kx_pow2_scaled(float t, float fac) {
 // equilibrium is resolved from the float64 ratio, not by subtracting two
 // rounded rates.
 __device__ __forceinline__ double kx_net_rate(float lnRf, double lnrho) {
-  const float a = __double2float_rn(lnrho);
+  const float a = kx_d2f(lnrho);
   const float e = lnRf + fmaxf(a, 0.0f);
   const float fac = -expm1f(-fabsf(a));
   const double mag = kx_pow2_scaled(e * KX_LOG2E_F, fac);
@@ -267,6 +293,7 @@ void emit_concentrations64(Out& o, const Mechanism& m, const std::vector<char>& 
     sum += (k ? " + y_" : "y_") + std::to_string(k);
   }
   o("const double sig = " + sum + ";");
+  o("if (!(sig > 0.0 && sig < KX_INF)) KX_BAD_POINT");
   o("const double fC = cM / sig;");
   for (int k = 0; k < m.ns; ++k)
     if (used[k]) o(fmt("const double C_%d = y_%d * fC;", k, k));
@@ -551,11 +578,11 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
   const auto flags = tmid_flags(m);
   o("const double lnT = log(T);");
   o("const double iT = 1.0 / T;");
-  o("const float lnTf = (float)lnT, iTf = (float)iT;");
+  o("const float lnTf = kx_d2f(lnT), iTf = kx_d2f(iT), Tf = kx_d2f(T);");
   c.log64 += 1; c.div64 += 1;
   bool any_plog = false;
   for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
-  if (any_plog) { o("const float lnPf = __logf((float)P);"); c.log32 += 1; }
+  if (any_plog) { o("const float lnPf = __logf(kx_d2f(P));"); c.log32 += 1; }
   o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
   std::string sum;
   for (int k = 0; k < m.ns; ++k) {
@@ -564,9 +591,10 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
     sum += (k ? " + y_" : "y_") + std::to_string(k);
   }
   o("const double sig = " + sum + ";");
+  o("if (!(sig > 0.0 && sig < KX_INF)) KX_BAD_POINT");
   o("const double fC = cM / sig;");
   o("const double lnfC = kx_log(fC);");
-  o("const float cMf = (float)cM, fCf = (float)fC;");
+  o("const float cMf = kx_d2f(cM), fCf = kx_d2f(fC);");
   c.fp64 += 2 * m.ns + 2; c.div64 += 1; c.log64 += 1;
   bool any_tb = false;
   for (auto& r : m.rx) any_tb |= r.third_body();
@@ -574,8 +602,8 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
     if (!used[k]) continue;
     // ln C_k = ln Y_k - ln W_k + ln fC, floored at ln(1e-304) so that an absent species gives 0 rates, not nan
     o(fmt("const double lnC_%d = fmax(kx_log(Yk_%d) + (lnfC - %s), -700.0);", k, k, D(std::log(m.W[k])).c_str()));
-    o(fmt("const float lnCf_%d = (float)lnC_%d;", k, k));
-    if (any_tb) o(fmt("const float Cf_%d = (float)y_%d * fCf;", k, k));
+    o(fmt("const float lnCf_%d = kx_d2f(lnC_%d);", k, k));
+    if (any_tb) o(fmt("const float Cf_%d = kx_d2f(y_%d) * fCf;", k, k));
     c.log64 += 1; c.fp64 += 2; c.fp32 += 1;
   }
   for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
@@ -610,8 +638,8 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
       if (r.blend == Blend::Troe) {
         const double al = r.troe[0];
         std::string Fc;
-        if (1.0 - al != 0.0) Fc = fmt("%s * __expf((float)T * %s)", F(1.0 - al).c_str(), F(-1.0 / r.troe[1]).c_str());
-        if (al != 0.0) Fc += (Fc.empty() ? "" : " + ") + fmt("%s * __expf((float)T * %s)", F(al).c_str(), F(-1.0 / r.troe[2]).c_str());
+        if (1.0 - al != 0.0) Fc = fmt("%s * __expf(Tf * %s)", F(1.0 - al).c_str(), F(-1.0 / r.troe[1]).c_str());
+        if (al != 0.0) Fc += (Fc.empty() ? "" : " + ") + fmt("%s * __expf(Tf * %s)", F(al).c_str(), F(-1.0 / r.troe[2]).c_str());
         Fc += (Fc.empty() ? "" : " + ") + fmt("__expf(%s * iTf)", F(-r.troe[3]).c_str());
         o("const float lFc = __log10f(" + Fc + ");");
         o("const float xx = fmaf(lnPr, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
@@ -621,7 +649,7 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
         lnF = "lnF";
       } else if (r.blend == Blend::Sri) {
         o("const float lPr = lnPr * 0.434294482f;");
-        o(fmt("const float base = %s * __expf(%s * iTf) + __expf((float)T * %s);", F(r.sri[0]).c_str(), F(-r.sri[1]).c_str(),
+        o(fmt("const float base = %s * __expf(%s * iTf) + __expf(Tf * %s);", F(r.sri[0]).c_str(), F(-r.sri[1]).c_str(),
               F(-1.0 / r.sri[2]).c_str()));
         o(fmt("const float lnF = %s + %s * lnTf + __fdividef(__logf(base), fmaf(lPr, lPr, 1.0f));", F(std::log(r.sri[3])).c_str(),
               F(r.sri[4]).c_str()));
@@ -678,6 +706,207 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
   }
   if (!rop)
     for (int k = 0; k < m.ns; ++k) o(fmt("out_[(long long)%d * ld + i] = w_%d;", k, k));
+}
+
+// ------------------------------------------------------------------ adjoint
+// Vector-Jacobian product of the production rates at fixed p.  With
+// a_i = sum_k nu_ki v_k, v^T wdot = sum_i a_i q_i, so each reaction adds
+// a_i dq_i to the adjoints of its own inputs (T, C_k, G_k/RT, [M]) in one
+// forward sweep; nothing is stored per reaction.  The chain to (T, Y) is
+// closed per point at the end: dG_k/RT/dT = -H_k/(R T^2) (Gibbs-Helmholtz),
+// C_k = [M] y_k / sigma with [M] = p/(R T), y_k = Y_k/W_k, sigma = sum y.
+// For q = c (R_f - R_r), R_f = k_f prod C^nu', R_r = k_r prod C^nu'',
+// ln k_r = ln k_f + sum nu G/RT - dn ln(p_atm/(R T)):
+//   dq/dT|_C,G = c ((R_f - R_r) dln k_f/dT - R_r dn/T),
+//   dq/dG_k = -c R_r nu_k,  dq/dC_k = c (nu'_k R_f - nu''_k R_r)/C_k.
+std::string dln_arrh(const Arrh& a) {
+  if (a.E == 0.0) return a.beta == 0.0 ? std::string("0.0") : fmt("%s * iT", D(a.beta).c_str());
+  return fmt("fma(%s, iT, %s) * iT", D(a.E).c_str(), D(a.beta).c_str());
+}
+
+// product of the concentrations of `side` with one factor of species k removed
+std::string conc_product_without(const std::vector<std::pair<int, int>>& side, int k) {
+  std::string s;
+  bool removed = false;
+  for (auto& e : side)
+    for (int n = 0; n < e.second; ++n) {
+      if (e.first == k && !removed) { removed = true; continue; }
+      s += " * C_" + std::to_string(e.first);
+    }
+  return s;
+}
+
+void emit_vjp64(Out& o, const Mechanism& m, OpCounts& c) {
+  const auto used = species_used(m);
+  const auto need_g = gibbs_needed(m);
+  const auto flags = tmid_flags(m);
+  o("const double lnT = log(T);");
+  o("const double iT = 1.0 / T;");
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  if (any_plog) o("const double lnP = kx_log(P);");
+  emit_concentrations64(o, m, used, c);
+  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
+  for (int k = 0; k < m.ns; ++k)
+    if (need_g[k]) emit_gibbs64(o, m, k, nasa_flag(m, k, flags), c);
+  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
+  for (int k = 0; k < m.ns; ++k) o(fmt("const double v_%d = V_[(long long)%d * ld + i];", k, k));
+  for (int k = 0; k < m.ns; ++k) o(fmt("double gC_%d = 0.0;", k));
+  for (int k = 0; k < m.ns; ++k)
+    if (need_g[k]) o(fmt("double gg_%d = 0.0;", k));
+  o("double gT = 0.0, gM = 0.0;");
+  for (int i = 0; i < m.nr(); ++i) {
+    const Reaction& r = m.rx[i];
+    o(fmt("{  // reaction %d", i));
+    ++o.ind;
+    std::map<int, int> nu;
+    for (auto& e : r.prod) nu[e.first] += e.second;
+    for (auto& e : r.reac) nu[e.first] -= e.second;
+    std::string a;
+    for (auto& kv : nu) {
+      if (kv.second == 0) continue;
+      std::string t = fmt("v_%d", kv.first);
+      if (a.empty()) a = kv.second == 1 ? t : kv.second == -1 ? "-" + t : fmt("%s * %s", D(kv.second).c_str(), t.c_str());
+      else a = kv.second == 1 ? a + " + " + t : kv.second == -1 ? a + " - " + t : fmt("fma(%s, %s, %s)", D(kv.second).c_str(), t.c_str(), a.c_str());
+    }
+    o("const double a = " + (a.empty() ? std::string("0.0") : a) + ";");
+    bool has_dX = false;
+    if (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) {
+      o(fmt("const double lkf = %s;", ln_arrh64(r.k, c).c_str()));
+      o("const double kf = kx_exp(lkf);");
+      o("const double dT = " + dln_arrh(r.k) + ";");
+    } else if (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) {
+      o(fmt("const double lk0 = %s, dk0 = %s;", ln_arrh64(r.k0, c).c_str(), dln_arrh(r.k0).c_str()));
+      o(fmt("const double lki = %s, dki = %s;", ln_arrh64(r.k, c).c_str(), dln_arrh(r.k).c_str()));
+      o(fmt("const double X = %s;", third_body64(r, c).c_str()));
+      o("const double lnPr = fmax(lk0 - lki + kx_log(X), -690.77552789821368);");
+      o("const double Pr = kx_exp(lnPr);");
+      o("const double ipr = 1.0 / (1.0 + Pr);");
+      if (r.blend == Blend::Troe) {
+        const double al = r.troe[0];
+        o(fmt("const double e3 = %s * kx_exp(T * %s), e1 = %s * kx_exp(T * %s), e2 = kx_exp(%s * iT);", D(1.0 - al).c_str(),
+              D(-1.0 / r.troe[1]).c_str(), D(al).c_str(), D(-1.0 / r.troe[2]).c_str(), D(-r.troe[3]).c_str()));
+        o(fmt("const double Fc = e3 + e1 + e2, dFc = e3 * %s + e1 * %s + e2 * %s * iT * iT;", D(-1.0 / r.troe[1]).c_str(),
+              D(-1.0 / r.troe[2]).c_str(), D(r.troe[3]).c_str()));
+        o("const double lFc = kx_log(Fc) * KX_INV_LN10;");
+        o("const double xx = fma(lnPr, KX_INV_LN10, fma(-0.67, lFc, -0.4));");
+        o("const double nn = fma(-1.27, lFc, 0.75);");
+        o("const double den = nn - 0.14 * xx, iden = 1.0 / den;");
+        o("const double ff = xx * iden, g1 = 1.0 / fma(ff, ff, 1.0);");
+        o("const double F = kx_exp(KX_LN10 * lFc * g1);");
+        o("const double h2 = -2.0 * ff * g1 * g1 * lFc;");
+        o("const double dF_lnPr = h2 * nn * iden * iden;");
+        o("const double dF_T = fma(h2, fma(-0.67, den, 1.1762 * xx) * iden * iden, g1) * dFc / Fc;");
+      } else if (r.blend == Blend::Sri) {
+        o("const double lPr = lnPr * KX_INV_LN10, Xs = 1.0 / fma(lPr, lPr, 1.0);");
+        o(fmt("const double ea = %s * kx_exp(%s * iT), eb = kx_exp(T * %s);", D(r.sri[0]).c_str(), D(-r.sri[1]).c_str(),
+              D(-1.0 / r.sri[2]).c_str()));
+        o("const double base = ea + eb, lnb = kx_log(base);");
+        o(fmt("const double F = %s * kx_exp(fma(%s, lnT, Xs * lnb));", D(r.sri[3]).c_str(), D(r.sri[4]).c_str()));
+        o("const double dF_lnPr = -2.0 * lPr * Xs * Xs * lnb * KX_INV_LN10;");
+        o(fmt("const double dF_T = %s * iT + Xs * (ea * %s * iT * iT + eb * %s) / base;", D(r.sri[4]).c_str(),
+              D(r.sri[1]).c_str(), D(-1.0 / r.sri[2]).c_str()));
+      } else {
+        o("const double F = 1.0, dF_lnPr = 0.0, dF_T = 0.0;");
+      }
+      if (r.kind == Kind::Falloff) {
+        o("const double kf = kx_exp(lki) * (Pr * ipr) * F;");
+        o("const double dP = ipr + dF_lnPr;");
+        o("const double dT = fma(dk0 - dki, dP, dki) + dF_T;");
+      } else {
+        o("const double kf = kx_exp(lk0) * ipr * F;");
+        o("const double dP = dF_lnPr - Pr * ipr;");
+        o("const double dT = fma(dk0 - dki, dP, dk0) + dF_T;");
+      }
+      o("const double dX = dP / X;");
+      has_dX = true;
+    } else {  // PLOG
+      const auto& t = r.plog;
+      auto lk = [&](size_t j) { return ln_arrh64(Arrh{t[j][1], t[j][2], t[j][3]}, c); };
+      auto dk = [&](size_t j) { return dln_arrh(Arrh{t[j][1], t[j][2], t[j][3]}); };
+      o("double lkf, dT;");
+      o(fmt("if (P <= %s) { lkf = %s; dT = %s; }", D(t[0][0]).c_str(), lk(0).c_str(), dk(0).c_str()));
+      for (size_t j = 0; j + 1 < t.size(); ++j) {
+        double l1 = std::log(t[j][0]), l2 = std::log(t[j + 1][0]);
+        o(fmt("else if (P < %s) { const double w = (lnP - %s) * %s; const double l1 = %s, d1 = %s; lkf = fma(%s - l1, w, l1); dT = fma(%s - d1, w, d1); }",
+              D(t[j + 1][0]).c_str(), D(l1).c_str(), D(1.0 / (l2 - l1)).c_str(), lk(j).c_str(), dk(j).c_str(), lk(j + 1).c_str(),
+              dk(j + 1).c_str()));
+      }
+      o(fmt("else { lkf = %s; dT = %s; }", lk(t.size() - 1).c_str(), dk(t.size() - 1).c_str()));
+      o("const double kf = kx_exp(lkf);");
+    }
+    const int dn = sum_nu(r);
+    o("const double Rf = kf" + conc_product(r.reac, "C_") + ";");
+    if (r.reversible) {
+      std::string lnkc = nu_sum(r, "g", c);
+      std::string lk = dn == 0 ? "-(" + lnkc + ")" : fmt("fma(%s, lnPRT, -(%s))", D(dn).c_str(), lnkc.c_str());
+      o("const double kr = kf * kx_exp(-(" + lk + "));");
+      o("const double Rr = kr" + conc_product(r.prod, "C_") + ";");
+    } else {
+      o("const double kr = 0.0, Rr = 0.0;");
+    }
+    std::string cm = "1.0";
+    if (r.kind == Kind::ThreeBody) {
+      o(fmt("const double X = %s;", third_body64(r, c).c_str()));
+      cm = "X";
+    }
+    o("const double aq = a * " + cm + ";");
+    o(dn != 0 ? fmt("gT = fma(aq, fma(Rf - Rr, dT, %s * Rr * iT), gT);", D(-dn).c_str())
+              : std::string("gT = fma(aq, (Rf - Rr) * dT, gT);"));
+    if (r.reversible)
+      for (auto& kv : nu)
+        if (kv.second != 0) o(fmt("gg_%d = fma(%s, aq * Rr, gg_%d);", kv.first, D(-kv.second).c_str(), kv.first));
+    // concentration adjoints from the mass-action products
+    std::map<int, int> f_nu, r_nu;
+    for (auto& e : r.reac) f_nu[e.first] += e.second;
+    for (auto& e : r.prod) r_nu[e.first] += e.second;
+    for (auto& kv : f_nu)
+      o(fmt("gC_%d = fma(aq, %s * kf%s, gC_%d);", kv.first, D(kv.second).c_str(), conc_product_without(r.reac, kv.first).c_str(),
+            kv.first));
+    if (r.reversible)
+      for (auto& kv : r_nu)
+        o(fmt("gC_%d = fma(aq, %s * kr%s, gC_%d);", kv.first, D(-kv.second).c_str(), conc_product_without(r.prod, kv.first).c_str(),
+              kv.first));
+    // third-body adjoint gX, distributed over [M] and the listed species
+    std::string gX;
+    if (r.kind == Kind::ThreeBody) gX = "a * (Rf - Rr)";
+    else if (has_dX) gX = "a * (Rf - Rr) * dX";
+    if (!gX.empty()) {
+      o("const double gX = " + gX + ";");
+      if (r.collider >= 0) {
+        o(fmt("gC_%d += gX;", r.collider));
+      } else {
+        o(r.default_eff == 1.0 ? std::string("gM += gX;") : fmt("gM = fma(%s, gX, gM);", D(r.default_eff).c_str()));
+        for (auto& e : r.eff) {
+          const double d = e.second - r.default_eff;
+          if (d != 0.0) o(fmt("gC_%d = fma(%s, gX, gC_%d);", e.first, D(d).c_str(), e.first));
+        }
+      }
+    }
+    --o.ind;
+    o("}");
+  }
+  // close the chain: G_k/RT(T), C_k([M], y), [M](T)
+  for (int k = 0; k < m.ns; ++k) {
+    if (!need_g[k]) continue;
+    const std::string fl = nasa_flag(m, k, flags);
+    const double* lo = &m.a_lo[7 * k];
+    const double* hi = &m.a_hi[7 * k];
+    std::string h = sel(fl, lo[4] / 5.0, hi[4] / 5.0);
+    for (int n = 3; n >= 0; --n) h = fmt("fma(%s, T, %s)", h.c_str(), sel(fl, lo[n] / (n + 1), hi[n] / (n + 1)).c_str());
+    h = fmt("fma(%s, iT, %s)", sel(fl, lo[5], hi[5]).c_str(), h.c_str());
+    o(fmt("gT = fma(-gg_%d * iT, %s, gT);", k, h.c_str()));
+  }
+  std::string sx = "0.0";
+  for (int k = 0; k < m.ns; ++k)
+    if (used[k]) sx = fmt("fma(gC_%d, C_%d, %s)", k, k, sx.c_str());
+  o("const double gCX = " + sx + ";");            // sum_k gC_k C_k
+  o("gM += gCX / cM;");
+  o("gT_[i] = fma(-gM * cM, iT, gT);");
+  // dC_k/dy_j = fC (delta_kj - X_k), X_k = C_k/[M]
+  o("const double gavg = gCX / cM;");
+  for (int k = 0; k < m.ns; ++k)
+    o(fmt("gY_[(long long)%d * ld + i] = fC * (%s - gavg) * %s;", k, used[k] ? fmt("gC_%d", k).c_str() : "0.0", D(1.0 / m.W[k]).c_str()));
 }
 
 // ------------------------------------------------------------------ thermo
@@ -777,7 +1006,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     d += lit(0.0);
     g(fmt("__device__ const %s kx_dc[%d] = {%s};", TY, 5 * np + 1, d.c_str()));
   }
-  o(mx ? fmt("const float L = (float)(log(T) - %s);", D(L0).c_str()) : std::string("const double L = log(T);"));
+  o(mx ? fmt("const float L = kx_d2f(log(T) - %s);", D(L0).c_str()) : std::string("const double L = log(T);"));
   c.log64 += 1;
   o(fmt("%s* const sX = (%s*)kx_dyn;", TY, TY));
   o(fmt("%s* const sZ1 = sX + %d;", TY, ns * opt.block));
@@ -785,12 +1014,14 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("const int t = threadIdx.x;");
   std::string sy, sumY;
   for (int k = 0; k < ns; ++k) {
-    o(fmt("const %s Yk_%d = (%s)Y_[(long long)%d * ld + i];", TY, k, TY, k));
+    o(mx ? fmt("const float Yk_%d = kx_d2f(Y_[(long long)%d * ld + i]);", k, k)
+         : fmt("const double Yk_%d = Y_[(long long)%d * ld + i];", k, k));
     o(fmt("const %s y_%d = Yk_%d * %s;", TY, k, k, lit(1.0 / m.W[k]).c_str()));
     sy += (k ? " + y_" : "y_") + std::to_string(k);
     sumY += (k ? " + Yk_" : "Yk_") + std::to_string(k);
   }
   o(fmt("const %s isig = %s / (%s);", TY, lit(1.0).c_str(), sy.c_str()));
+  o("if (!(isig > 0 && isig < KX_INF)) KX_BAD_POINT");
   o(fmt("const %s iWbar = %s / ((%s) * isig);", TY, lit(1.0).c_str(), sumY.c_str()));
   cnt(3 * ns);
   if (mx) c.div32 += 2; else c.div64 += 2;
@@ -844,12 +1075,13 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     }
   }
   o(fmt("const double pr = %s / P;", D(P_ATM).c_str()));
-  o("out0_[i] = (double)mu;");
-  o(fmt("out1_[i] = (double)(%s * (sl + %s / sil));", lit(0.5).c_str(), lit(1.0).c_str()));
+  const char* CV = mx ? "kx_f2d" : "";
+  o(fmt("out0_[i] = %s(mu);", CV));
+  o(fmt("out1_[i] = %s(%s * (sl + %s / sil));", CV, lit(0.5).c_str(), lit(1.0).c_str()));
   for (int k = 0; k < ns; ++k) {
     // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
-    o(fmt("{ const %s Sk = sS[%d + t]; out2_[(long long)%d * ld + i] = (double)(Sk > 0 ? %s(-sX[%d + t], %s * iWbar, %s) / Sk : %s(%s)) * pr; }",
-          TY, k * opt.block, k, FMA, k * opt.block, lit(m.W[k]).c_str(), lit(1.0).c_str(), EXP,
+    o(fmt("{ const %s Sk = sS[%d + t]; out2_[(long long)%d * ld + i] = %s(Sk > 0 ? %s(-sX[%d + t], %s * iWbar, %s) / Sk : %s(%s)) * pr; }",
+          TY, k * opt.block, k, CV, FMA, k * opt.block, lit(m.W[k]).c_str(), lit(1.0).c_str(), EXP,
           horner(&m.dif[5 * ((size_t)k * ns + k)], 1.0, 0.0).c_str()));
     cnt(3);
     c.fp64 += 1;
@@ -891,15 +1123,19 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       emit_transport(body, globals, m, opt, c);
       break;
     case KernelKind::Vjp:
-      return "";
+      outs = "const double* __restrict__ V_, double* __restrict__ gT_, double* __restrict__ gY_";
+      nan_fill = fmt("gT_[i] = KX_NAN; for (int k = 0; k < %d; ++k) gY_[(long long)k * ld + i] = KX_NAN;", m.ns);
+      emit_vjp64(body, m, c);
+      break;
   }
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[768];\n";
+  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[1024];\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
+  s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ") " << entry
     << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
     << outs << ", long long n)\n{\n";

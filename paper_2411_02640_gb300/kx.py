@@ -130,6 +130,8 @@ class Mechanism:
         n = T.shape[0]
         if p.shape[0] != n or Y.dim() != 2 or Y.shape[0] != self.n_species or Y.shape[1] < n:
             raise ValueError("expected T[n], p[n], Y[N_s, >= n]")
+        if n == 0:
+            return 0, 0
         if not (T.is_contiguous() and p.is_contiguous() and Y.stride(1) == 1):
             raise ValueError("T and p must be contiguous and Y point-contiguous")
         return n, Y.stride(0)
@@ -138,13 +140,13 @@ class Mechanism:
         import torch
         if rows is None:
             return torch.empty(n, dtype=torch.float64, device=like.device)
-        return torch.empty((rows, ld), dtype=torch.float64, device=like.device)
+        return torch.empty((rows, ld if n > 0 else 0), dtype=torch.float64, device=like.device)
 
     # -------------------------------------------------------------- calls
     def production_rates(self, T, p, Y, out=None, precision="fp64", stream=None):
         n, ld = self._state(T, p, Y)
         out = out if out is not None else self._alloc(self.n_species, n, ld, T)
-        assert out.stride(0) == ld and out.shape[0] == self.n_species
+        assert out.shape[0] == self.n_species and (n == 0 or out.stride(0) == ld)
         _check(lib().kx_production_rates(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _PREC[precision],
                                           _stream(stream)))
         return out
@@ -152,7 +154,7 @@ class Mechanism:
     def rates_of_progress(self, T, p, Y, out=None, precision="fp64", stream=None):
         n, ld = self._state(T, p, Y)
         out = out if out is not None else self._alloc(self.n_reactions, n, ld, T)
-        assert out.stride(0) == ld and out.shape[0] == self.n_reactions
+        assert out.shape[0] == self.n_reactions and (n == 0 or out.stride(0) == ld)
         _check(lib().kx_rates_of_progress(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _PREC[precision],
                                            _stream(stream)))
         return out
@@ -168,17 +170,19 @@ class Mechanism:
         if out is None:
             out = (self._alloc(None, n, ld, T), self._alloc(None, n, ld, T), self._alloc(self.n_species, n, ld, T))
         mu, lam, D = out
-        assert D.stride(0) == ld
+        assert n == 0 or D.stride(0) == ld
         _check(lib().kx_transport(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(mu), _ptr(lam), _ptr(D), n,
                                   _PREC[precision], _stream(stream)))
         return mu, lam, D
 
     def production_rates_vjp(self, T, p, Y, v, out: Optional[Tuple] = None, stream=None):
+        """gT[n] = sum_k v_k d wdot_k/dT, gY[N_s, ld] = sum_k v_k d wdot_k/dY_j (p fixed)."""
         n, ld = self._state(T, p, Y)
-        assert v.shape[0] == self.n_species and v.stride(0) == ld and v.dtype == Y.dtype
+        assert v.shape[0] == self.n_species and v.dtype == Y.dtype and (n == 0 or v.stride(0) == ld)
         if out is None:
             out = (self._alloc(None, n, ld, T), self._alloc(self.n_species, n, ld, T))
         gT, gY = out
+        assert n == 0 or gY.stride(0) == ld
         _check(lib().kx_production_rates_vjp(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(v), _ptr(gT), _ptr(gY), n,
                                              _stream(stream)))
         return gT, gY
