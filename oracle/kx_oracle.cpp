@@ -59,7 +59,7 @@ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
 inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
 inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
 inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual operator/(Dual a, Dual b) { double q = a.v / b.v; return Dual(q, (a.d - q * b.d) / b.v); }
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, e * a.d); }
 inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }

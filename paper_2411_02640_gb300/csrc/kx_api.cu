@@ -174,6 +174,8 @@ kx_status compile_kernel(kx_mech* h, Kernel& k) {
     nvrtcDestroyProgram(&prog);
     parse_ptxas_info(log, k.registers, k.local_bytes);
     mkdirs(h->cache_dir);
+    if (std::getenv("KX_DUMP_SOURCE"))
+      write_file_atomic(base + ".cu", std::vector<char>(k.source.begin(), k.source.end()));
     write_file_atomic(base + ".cubin", k.cubin);
     write_file_atomic(base + ".log", std::vector<char>(log.begin(), log.end()));
   }
