@@ -67,6 +67,8 @@ typedef struct {
   int diff_mode;      /* 0 default (symmetric), 1 symmetric D_kj pairs, 2 full matrix */
   int kc_mode;        /* 0 default (log space: k_r = exp(ln k_f - ln K_c)),
                          1 per-species exp(-G_k/RT) products, one division per reaction */
+  int tr_mode;        /* float64 transport: 0 (default) double-float arithmetic on the float32
+                         pipe (float64 accuracy, ~2^-47 per operation), 1 native float64 */
   int maxrreg;        /* register cap per thread for the generated kernels; 0 = compiler choice */
   int block;          /* threads per block; 0 = 128 */
   int lazy;           /* 0: compile every kernel at load (in parallel); 1: on first use */

@@ -282,6 +282,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.block < 32 || h->opt.block > 1024 || h->opt.block % 32) return fail(KX_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (h->opt.diff_mode < 0 || h->opt.diff_mode > 2) return fail(KX_ERR_ARG, "diff_mode must be 0, 1 or 2");
   if (h->opt.kc_mode < 0 || h->opt.kc_mode > 1) return fail(KX_ERR_ARG, "kc_mode must be 0 or 1");
+  if (h->opt.tr_mode < 0 || h->opt.tr_mode > 1) return fail(KX_ERR_ARG, "tr_mode must be 0 or 1");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
   h->opt.cache_dir = nullptr;
@@ -305,10 +306,12 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.block = h->opt.block;
     k->eopt.diff_mode = h->opt.diff_mode == 2 ? 2 : 1;
     k->eopt.kc_mode = h->opt.kc_mode;
+    k->eopt.tr_mode = h->opt.tr_mode;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~200 KB, a multiple of 32
       const int per = kx::transport_smem_per_thread(h->m, sp.mixed);
-      int b = std::min(h->opt.block, (200 * 1024 / per) / 32 * 32);
+      int b = std::min(std::max(h->opt.block, 256), (200 * 1024 / per) / 32 * 32);
+      if (b >= 128) b = b / 128 * 128;   // whole warps on every SM sub-partition
       if (b < 32) return fail(KX_ERR_UNSUPPORTED, "mechanism too large for the transport kernel");
       k->eopt.block = b;
       k->smem = per * b;

@@ -122,8 +122,9 @@ __device__ __forceinline__ void kx_load_tables() {
 #ifndef KX_LIBMATH
   for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
   for (int t = threadIdx.x; t < 1024; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
-  __syncthreads();
 #endif
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_dexp[t] = kx_dexp2_tab[t];
+  __syncthreads();
 }
 
 // fac * 2^t as a float64 for |t| up to ~1100 and fac in [0, 1]: the
@@ -165,6 +166,61 @@ __device__ __forceinline__ float kx_ln_pr_ratio(float lnPr) {
 }
 __device__ __forceinline__ float kx_ln_inv_1p(float lnPr) {
   return lnPr < 0.0f ? -log1pf(__expf(lnPr)) : -(lnPr + log1pf(__expf(-lnPr)));
+}
+
+// ---- double-float (float32 pair) arithmetic for float64-accurate work on
+// the float32 pipe.  Error-free transformations after Knuth (two-sum),
+// Dekker (fast two-sum) and the FMA two-product; the __f*_rn intrinsics keep
+// the compiler from contracting or reassociating them.
+struct kx_df { float hi, lo; };
+__device__ __forceinline__ kx_df kx_mk(float h, float l) { kx_df r; r.hi = h; r.lo = l; return r; }
+__device__ __forceinline__ kx_df kx_qts(float a, float b) {      // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return kx_mk(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ kx_df kx_ts(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return kx_mk(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// a*b + c
+__device__ __forceinline__ kx_df kx_df_fma(kx_df a, kx_df b, kx_df c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  const kx_df s = kx_ts(p, c.hi);
+  return kx_qts(s.hi, __fadd_rn(s.lo, __fadd_rn(pe, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, c.lo)))));
+}
+__device__ __forceinline__ kx_df kx_df_mul(kx_df a, kx_df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return kx_qts(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))));
+}
+__device__ __forceinline__ double kx_df2d(kx_df a) { return kx_f2d(a.hi) + kx_f2d(a.lo); }
+__device__ __forceinline__ kx_df kx_d2df(double x) {
+  const float h = kx_d2f(x);
+  return kx_mk(h, kx_d2f(x - kx_f2d(h)));
+}
+// e^x of a double-float x: x = k ln2/256 + r (k from the high part in
+// float32, ln2/256 split in three floats, the first short enough that k C1
+// is exact), e^r = 1 + r + r^2 q(r) with the tail in float32, times
+// 2^(j/256) from a float-pair table and 2^(k>>8) as an exact float scale.
+// Relative error about 1e-13; |x| >= 80 (and nan) go through float64.
+__device__ __forceinline__ kx_df kx_df_exp(kx_df x) {
+  if (!(fabsf(x.hi) < 80.0f)) return kx_d2df(exp(kx_df2d(x)));
+  const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_C1F, x.hi);
+  const float p = __fmul_rn(kf, KX_C2F);
+  const float pe = __fmaf_rn(kf, KX_C2F, -p);
+  kx_df r = kx_ts(t1, -p);
+  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_C3F))));
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const float sc = __int_as_float(((k >> 8) + 127) << 23);
+  return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
 )KXPRE";
 
@@ -938,10 +994,12 @@ void emit_thermo(Out& o, const Mechanism& m, OpCounts& c) {
 }
 
 // ------------------------------------------------------------------ transport
-// Per-species work (X_k, eta_k, lambda_k) is unrolled; the O(N^2) pair sums
-// run as loops over coefficient tables in global memory (uniform addresses,
-// so every load is a broadcast) with each thread's species vectors staged in
-// its own column of shared memory, [species][thread].
+// The O(N_s) and O(N_s^2) sums of the mixing rules run as loops over
+// coefficient tables in global memory (the addresses are the same for every
+// thread of a warp, so each load is a broadcast), with each thread's species
+// vectors staged in its own column of shared memory, [species][thread].
+// Compile time and instruction-cache footprint stay O(1) in the mechanism
+// size, where fully unrolled pair sums grow as N_s^2.
 //
 // Wilke (the eta formula with phi_kj): with u_k = sqrt(eta_k) W_k^(-1/4) and
 // a_kj = (1 + W_k/W_j)^(-1/2)/sqrt(8),
@@ -950,6 +1008,15 @@ void emit_thermo(Out& o, const Mechanism& m, OpCounts& c) {
 // three products with a constant matrix; every term is positive.
 // Diffusion: S_k = sum_{j != k} X_j / D_kj(1 atm), each symmetric pair
 // evaluated once and added to both rows (Sec. 2.3.2), or the full matrix.
+//
+// Three arithmetics share the loop structure:
+//   f64: native float64, polynomials in ln T as fitted;
+//   df:  double-float (float32 pairs, ~2^-47 relative per operation) on the
+//        float32 pipe, polynomials re-expanded about L0 = ln sqrt(300*3000)
+//        so every Horner step is well conditioned -- float64 accuracy
+//        without the float64 pipe, which is the scarce unit on this GPU;
+//   f32: float32 (the mixed precision), polynomials re-expanded about L0 and
+//        scaled by log2(e) so each property is one exp2.
 double wilke_a(const Mechanism& m, int k, int j) { return 1.0 / std::sqrt(8.0 * (1.0 + m.W[k] / m.W[j])); }
 
 // p(L) = sum c_n L^n re-expanded about L0: d_m = sum_{n>=m} C(n,m) c_n L0^(n-m)
@@ -962,131 +1029,214 @@ void shift_poly(const double* cf, double L0, double scale, double out[5]) {
   }
 }
 
+struct TrMode {
+  enum { F64, DF, F32 } kind;
+  const char* ty;     // arithmetic type
+  const char* st;     // shared / table element type
+};
 
 void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, OpCounts& c) {
   const int ns = m.ns;
-  const bool mx = opt.mixed;
-  const char* TY = mx ? "float" : "double";
-  const char* FMA = mx ? "fmaf" : "fma";
-  const char* EXP = mx ? "exp2f" : "kx_exp";
-  const double L0 = mx ? 0.5 * (std::log(300.0) + std::log(3000.0)) : 0.0;
-  const double SC = mx ? 1.4426950408889634 : 1.0;      // exp2 form for float32
-  auto lit = [&](double v) { return mx ? F(v) : D(v); };
-  // coefficients of s * p(L) + add, in the kernel's variable (L, or L - L0 for float32)
-  auto coefs = [&](const double* cf, double s, double add, double out[5]) {
-    if (mx) shift_poly(cf, L0, s * SC, out);
-    else for (int n = 0; n < 5; ++n) out[n] = cf[n] * s;
-    out[0] += add * SC;
+  TrMode md;
+  if (opt.mixed) md = {TrMode::F32, "float", "float"};
+  else if (opt.tr_mode == 0) md = {TrMode::DF, "kx_df", "float2"};
+  else md = {TrMode::F64, "double", "double"};
+  const double L0 = md.kind == TrMode::F64 ? 0.0 : 0.5 * (std::log(300.0) + std::log(3000.0));
+  const double SC = md.kind == TrMode::F32 ? 1.4426950408889634 : 1.0;   // exp2 form for float32
+  const int B = opt.block;
+  // ---- element literal, load, store and arithmetic spelled per mode
+  auto lit = [&](double v) -> std::string {
+    if (md.kind == TrMode::F64) return D(v);
+    if (md.kind == TrMode::F32) return F(v);
+    const float h = (float)v;
+    return fmt("{%s, %s}", F(h).c_str(), F((float)(v - (double)h)).c_str());
   };
-  auto horner = [&](const double* cf, double s, double add) {
-    double d[5];
-    coefs(cf, s, add, d);
-    std::string r = lit(d[4]);
-    for (int n = 3; n >= 0; --n) r = fmt("%s(%s, L, %s)", FMA, r.c_str(), lit(d[n]).c_str());
+  auto ld = [&](const std::string& e) { return md.kind == TrMode::DF ? fmt("kx_mk((%s).x, (%s).y)", e.c_str(), e.c_str()) : e; };
+  auto st = [&](const std::string& dst, const std::string& v) {
+    return md.kind == TrMode::DF ? fmt("%s = make_float2((%s).hi, (%s).lo);", dst.c_str(), v.c_str(), v.c_str())
+                                 : fmt("%s = %s;", dst.c_str(), v.c_str());
+  };
+  auto FMA = [&](const std::string& a, const std::string& b, const std::string& cc) {
+    return fmt("%s(%s, %s, %s)", md.kind == TrMode::DF ? "kx_df_fma" : md.kind == TrMode::F32 ? "fmaf" : "fma", a.c_str(), b.c_str(),
+               cc.c_str());
+  };
+  auto MUL = [&](const std::string& a, const std::string& b) {
+    return md.kind == TrMode::DF ? fmt("kx_df_mul(%s, %s)", a.c_str(), b.c_str()) : fmt("(%s) * (%s)", a.c_str(), b.c_str());
+  };
+  auto EXP = [&](const std::string& a) {
+    return fmt("%s(%s)", md.kind == TrMode::DF ? "kx_df_exp" : md.kind == TrMode::F32 ? "exp2f" : "kx_exp", a.c_str());
+  };
+  auto NEG = [&](const std::string& a) {
+    return md.kind == TrMode::DF ? fmt("kx_mk(-(%s).hi, -(%s).lo)", a.c_str(), a.c_str()) : fmt("(-(%s))", a.c_str());
+  };
+  auto TOD = [&](const std::string& a) {
+    return md.kind == TrMode::DF ? fmt("kx_df2d(%s)", a.c_str()) : md.kind == TrMode::F32 ? fmt("kx_f2d(%s)", a.c_str()) : a;
+  };
+  auto FROMD = [&](const std::string& a) {
+    return md.kind == TrMode::DF ? fmt("kx_d2df(%s)", a.c_str()) : md.kind == TrMode::F32 ? fmt("kx_d2f(%s)", a.c_str()) : a;
+  };
+  const std::string ZERO = md.kind == TrMode::DF ? "kx_mk(0.f, 0.f)" : md.kind == TrMode::F32 ? "0.0f" : "0.0";
+  auto horner = [&](const std::string& tab) {   // polynomial with coefficients tab[0..4]
+    std::string r = ld(tab + "[4]");
+    for (int n = 3; n >= 0; --n) r = FMA(r, "L", ld(fmt("%s[%d]", tab.c_str(), n)));
     return r;
   };
-  auto cnt = [&](double n) { if (mx) c.fp32 += n; else c.fp64 += n; };
-  auto cexp = [&](double n) { if (mx) c.exp32 += n; else c.exp64 += n; };
+  auto coefs = [&](const double* cf, double s, double add, double out[5]) {
+    if (md.kind == TrMode::F64) for (int n = 0; n < 5; ++n) out[n] = cf[n] * s;
+    else shift_poly(cf, L0, s * SC, out);
+    out[0] += add * SC;
+  };
+  // per-op costs, for the manifest
+  const double cf_fma = md.kind == TrMode::DF ? 14 : 1, cf_exp = md.kind == TrMode::DF ? 45 : 1;
+  auto count_fma = [&](double n) {
+    if (md.kind == TrMode::F64) c.fp64 += n; else c.fp32 += n * cf_fma;
+  };
+  auto count_exp = [&](double n) {
+    if (md.kind == TrMode::F64) c.exp64 += n; else if (md.kind == TrMode::F32) c.exp32 += n; else c.fp32 += n * cf_exp;
+  };
   // ---- module-scope tables
   {
-    std::string a;
-    for (int k = 0; k < ns; ++k)
-      for (int j = 0; j < ns; ++j) a += lit(wilke_a(m, k, j)) + ((k == ns - 1 && j == ns - 1) ? "" : ",");
-    g(fmt("__device__ const %s kx_wa[%d] = {%s};", TY, ns * ns, a.c_str()));
-    std::string d;
+    std::string pv, pl, wa, dself, w, iw, sqw;
+    for (int k = 0; k < ns; ++k) {
+      double d[5];
+      coefs(&m.eta[5 * k], -0.5, 0.25 * std::log(m.W[k]), d);      // ln v_k = -(ln eta_k / 2 - ln W_k / 4)
+      for (int n = 0; n < 5; ++n) pv += lit(d[n]) + ",";
+      coefs(&m.lam[5 * k], 1.0, 0.0, d);
+      for (int n = 0; n < 5; ++n) pl += lit(d[n]) + ",";
+      for (int n = 0; n < 5; ++n) dself += D(m.dif[5 * ((size_t)k * ns + k) + n]) + ",";
+      w += D(m.W[k]) + ",";
+      iw += D(1.0 / m.W[k]) + ",";
+      sqw += D(std::sqrt(m.W[k])) + ",";
+      for (int j = 0; j < ns; ++j) wa += lit(wilke_a(m, k, j)) + ",";
+    }
+    std::string dc;
     int np = 0;
     for (int k = 0; k < ns; ++k)
       for (int j = (opt.diff_mode == 2 ? 0 : k + 1); j < ns; ++j) {
         if (j == k) continue;
-        double cf[5];
-        coefs(&m.dif[5 * ((size_t)k * ns + j)], -1.0, 0.0, cf);
-        for (int n = 0; n < 5; ++n) d += lit(cf[n]) + ",";
+        double d[5];
+        coefs(&m.dif[5 * ((size_t)k * ns + j)], -1.0, 0.0, d);
+        for (int n = 0; n < 5; ++n) dc += lit(d[n]) + ",";
+        dc += lit(0.0) + ",";                 // each pair padded to 6 entries for vector loads
         ++np;
       }
-    d += lit(0.0);
-    g(fmt("__device__ const %s kx_dc[%d] = {%s};", TY, 5 * np + 1, d.c_str()));
+    const char* T = md.st;
+    g(fmt("__device__ const %s kx_pv[%d] = {%s};", T, 5 * ns, pv.c_str()));
+    g(fmt("__device__ const %s kx_pl[%d] = {%s};", T, 5 * ns, pl.c_str()));
+    g(fmt("__device__ const %s kx_wa[%d] = {%s};", T, ns * ns, wa.c_str()));
+    g(fmt("__device__ const %s kx_dc[%d] __attribute__((aligned(16))) = {%s%s};", T, 6 * np + 2, dc.c_str(),
+          (lit(0.0) + "," + lit(0.0)).c_str()));
+    g(fmt("__device__ const double kx_dself[%d] = {%s};", 5 * ns, dself.c_str()));
+    g(fmt("__device__ const double kx_w[%d] = {%s};", ns, w.c_str()));
+    g(fmt("__device__ const double kx_iw[%d] = {%s};", ns, iw.c_str()));
+    g(fmt("__device__ const double kx_sqw[%d] = {%s};", ns, sqw.c_str()));
   }
-  o(mx ? fmt("const float L = kx_d2f(log(T) - %s);", D(L0).c_str()) : std::string("const double L = log(T);"));
+  o("const double lnT = log(T);");
   c.log64 += 1;
-  o(fmt("%s* const sX = (%s*)kx_dyn;", TY, TY));
-  o(fmt("%s* const sZ1 = sX + %d;", TY, ns * opt.block));
-  o(fmt("%s* const sZ2 = sZ1 + %d;", TY, ns * opt.block));
+  if (md.kind == TrMode::F64) o("const double L = lnT;");
+  else o(fmt("const %s L = %s;", md.ty, FROMD(fmt("lnT - %s", D(L0).c_str())).c_str()));
+  o(fmt("%s* const sX = (%s*)kx_dyn;", md.st, md.st));
+  o(fmt("%s* const sZ1 = sX + %d;", md.st, ns * B));
+  o(fmt("%s* const sZ2 = sZ1 + %d;", md.st, ns * B));
   o("const int t = threadIdx.x;");
-  std::string sy, sumY;
-  for (int k = 0; k < ns; ++k) {
-    o(mx ? fmt("const float Yk_%d = kx_d2f(Y_[(long long)%d * ld + i]);", k, k)
-         : fmt("const double Yk_%d = Y_[(long long)%d * ld + i];", k, k));
-    o(fmt("const %s y_%d = Yk_%d * %s;", TY, k, k, lit(1.0 / m.W[k]).c_str()));
-    sy += (k ? " + y_" : "y_") + std::to_string(k);
-    sumY += (k ? " + Yk_" : "Yk_") + std::to_string(k);
-  }
-  o(fmt("const %s isig = %s / (%s);", TY, lit(1.0).c_str(), sy.c_str()));
+  o("double sy = 0.0, sY = 0.0;");
+  o(fmt("for (int k = 0; k < %d; ++k) { const double Yk = Y_[(long long)k * ld + i]; sY += Yk; sy = fma(Yk, kx_iw[k], sy); }", ns));
+  o("const double isig = 1.0 / sy;");
   o("if (!(isig > 0 && isig < KX_INF)) KX_BAD_POINT");
-  o(fmt("const %s iWbar = %s / ((%s) * isig);", TY, lit(1.0).c_str(), sumY.c_str()));
-  cnt(3 * ns);
-  if (mx) c.div32 += 2; else c.div64 += 2;
-  // per species: X, u, z1 = X/u, z2 = X/u^2, and the Mathur sums
-  o(fmt("%s sl = 0, sil = 0;", TY));
-  for (int k = 0; k < ns; ++k) {
-    o(fmt("{ const %s X = y_%d * isig; sX[%d + t] = X;", TY, k, k * opt.block));
-    o(fmt("  const %s v = %s(%s);", TY, EXP, horner(&m.eta[5 * k], -0.5, 0.25 * std::log(m.W[k])).c_str()));
-    o(fmt("  const %s z1 = X * v; sZ1[%d + t] = z1; sZ2[%d + t] = z1 * v;", TY, k * opt.block, k * opt.block));
-    o(fmt("  const %s ll = %s;", TY, horner(&m.lam[5 * k], 1.0, 0.0).c_str()));
-    o(fmt("  sl = %s(X, %s(ll), sl); sil = %s(X, %s(-ll), sil); }", FMA, EXP, FMA, EXP));
-    cnt(16); cexp(3);
-  }
+  o("const double iWbar = 1.0 / (sY * isig);");
+  c.fp64 += 2 * ns + 1; c.div64 += 2;
+  // per species: X, v = 1/u, z1 = X v, z2 = X v^2, Mathur sums
+  o(fmt("%s sl = %s, sil = %s;", md.ty, ZERO.c_str(), ZERO.c_str()));
+  o("#pragma unroll 1");
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o(fmt("  const %s X = %s;", md.ty, FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig").c_str()));
+  o("  " + st(fmt("sX[k * %d + t]", B), "X"));
+  o(fmt("  const %s* pv = kx_pv + 5 * k; const %s* pl = kx_pl + 5 * k;", md.st, md.st));
+  o(fmt("  const %s v = %s;", md.ty, EXP(horner("pv")).c_str()));
+  o(fmt("  const %s z1 = %s;", md.ty, MUL("X", "v").c_str()));
+  o("  " + st(fmt("sZ1[k * %d + t]", B), "z1"));
+  o("  " + st(fmt("sZ2[k * %d + t]", B), MUL("z1", "v")));
+  o(fmt("  const %s ll = %s;", md.ty, horner("pl").c_str()));
+  o("  sl = " + FMA("X", EXP("ll"), "sl") + ";");
+  o("  sil = " + FMA("X", EXP(NEG("ll")), "sil") + ";");
+  o("}");
+  count_fma(ns * 14.0); count_exp(ns * 3.0);
+  c.fp64 += 2 * ns;
   // Wilke rows
-  o(fmt("%s mu = 0;", TY));
-  for (int k = 0; k < ns; ++k) {
-    o(fmt("{ const %s u = %s(%s);", TY, EXP, horner(&m.eta[5 * k], 0.5, -0.25 * std::log(m.W[k])).c_str()));
-    o(fmt("  %s s0 = 0, s1 = 0, s2 = 0;", TY));
-    o(fmt("  const %s* a = kx_wa + %d;", TY, k * ns));
-    o("  #pragma unroll 4");
-    o(fmt("  for (int j = 0; j < %d; ++j) { const %s aj = a[j]; s0 = %s(aj, sX[j * %d + t], s0); s1 = %s(aj, sZ1[j * %d + t], s1); s2 = %s(aj, sZ2[j * %d + t], s2); }",
-          ns, TY, FMA, opt.block, FMA, opt.block, FMA, opt.block));
-    o(fmt("  mu += sX[%d + t] * (u * u * %s) / %s(u, %s(u, s2, %s * s1), s0); }", k * opt.block, lit(std::sqrt(m.W[k])).c_str(),
-          FMA, FMA, lit(2.0).c_str()));
-    cnt(3.0 * ns + 12); cexp(1);
-    if (mx) c.div32 += 1; else c.div64 += 1;
-  }
-  // diffusion: S in the sZ1 columns
-  o(fmt("%s* const sS = sZ1;", TY));
-  o(fmt("for (int k = 0; k < %d; ++k) sS[k * %d + t] = 0;", ns, opt.block));
-  int base = 0;
-  for (int k = 0; k < ns; ++k) {
-    if (opt.diff_mode == 2) {
-      o(fmt("{ %s Sk = 0; const %s* cf = kx_dc + %d;", TY, TY, 5 * base));
-      o("  #pragma unroll 2");
-      o(fmt("  for (int j = 0; j < %d; ++j) { if (j == %d) continue; const %s e = %s(%s(%s(%s(%s(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 5; Sk = %s(sX[j * %d + t], e, Sk); }",
-            ns, k, TY, EXP, FMA, FMA, FMA, FMA, FMA, opt.block));
-      o(fmt("  sS[%d + t] = Sk; }", k * opt.block));
-      base += ns - 1;
-      cnt(6.0 * (ns - 1)); cexp(ns - 1);
-    } else {
-      if (k == ns - 1) break;
-      o(fmt("{ %s Sk = sS[%d + t]; const %s Xk = sX[%d + t]; const %s* cf = kx_dc + %d;", TY, k * opt.block, TY, k * opt.block, TY,
-            5 * base));
-      o("  #pragma unroll 2");
-      o(fmt("  for (int j = %d; j < %d; ++j) { const %s e = %s(%s(%s(%s(%s(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 5; Sk = %s(sX[j * %d + t], e, Sk); sS[j * %d + t] = %s(Xk, e, sS[j * %d + t]); }",
-            k + 1, ns, TY, EXP, FMA, FMA, FMA, FMA, FMA, opt.block, opt.block, FMA, opt.block));
-      o(fmt("  sS[%d + t] = Sk; }", k * opt.block));
-      base += ns - 1 - k;
-      cnt(6.0 * (ns - 1 - k)); cexp(ns - 1 - k);
-    }
+  o("double mu = 0.0;");
+  o("#pragma unroll 1");
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
+  o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
+  o(fmt("  %s s0 = %s, s1 = %s, s2 = %s;", md.ty, ZERO.c_str(), ZERO.c_str(), ZERO.c_str()));
+  o(fmt("  const %s* a = kx_wa + %d * k;", md.st, ns));
+  o("  #pragma unroll 4");
+  o(fmt("  for (int j = 0; j < %d; ++j) {", ns));
+  o(fmt("    const %s A = %s;", md.ty, ld("a[j]").c_str()));
+  o(fmt("    s0 = %s; s1 = %s; s2 = %s;", FMA("A", ld(fmt("sX[j * %d + t]", B)), "s0").c_str(),
+        FMA("A", ld(fmt("sZ1[j * %d + t]", B)), "s1").c_str(), FMA("A", ld(fmt("sZ2[j * %d + t]", B)), "s2").c_str()));
+  o("  }");
+  const std::string two_s1 = md.kind == TrMode::DF ? "kx_mk(2.f * s1.hi, 2.f * s1.lo)" : md.kind == TrMode::F32 ? "2.0f * s1" : "2.0 * s1";
+  o(fmt("  const %s den = %s;", md.ty, FMA("u", FMA("u", "s2", two_s1), "s0").c_str()));
+  o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD(ld(fmt("sX[k * %d + t]", B))).c_str(), TOD(MUL("u", "u")).c_str(),
+        TOD("den").c_str()));
+  o("}");
+  count_fma(ns * (3.0 * ns + 8)); count_exp(ns);
+  c.fp64 += 4 * ns; c.div64 += ns;
+  // mixture-averaged diffusion, S in the sZ1 columns
+  o(fmt("%s* const sS = sZ1;", md.st));
+  o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(fmt("sS[k * %d + t]", B), ZERO).c_str()));
+  o(fmt("const %s* cf = kx_dc;", md.st));
+  std::string pair_exp;
+  if (md.kind == TrMode::DF)
+    pair_exp = "const float4 c01 = *(const float4*)(cf), c23 = *(const float4*)(cf + 2), c45 = *(const float4*)(cf + 4); cf += 6;\n"
+               "      const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma(kx_df_fma(kx_df_fma(kx_mk(c45.x, c45.y), L, kx_mk(c23.z, c23.w)), L, "
+               "kx_mk(c23.x, c23.y)), L, kx_mk(c01.z, c01.w)), L, kx_mk(c01.x, c01.y)));";
+  else if (md.kind == TrMode::F64)
+    pair_exp = "const double2 c01 = *(const double2*)(cf), c23 = *(const double2*)(cf + 2), c45 = *(const double2*)(cf + 4); cf += 6;\n"
+               "      const double e = kx_exp(fma(fma(fma(fma(c45.x, L, c23.y), L, c23.x), L, c01.y), L, c01.x));";
+  else
+    pair_exp = "const float e = exp2f(fmaf(fmaf(fmaf(fmaf(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 6;";
+  if (opt.diff_mode == 2) {
+    o("#pragma unroll 1");
+    o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+    o(fmt("  %s Sk = %s;", md.ty, ZERO.c_str()));
+    o("  #pragma unroll 2");
+    o(fmt("  for (int j = 0; j < %d; ++j) {", ns));
+    o("    if (j == k) continue;");
+    o("    " + pair_exp);
+    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
+    o("  }");
+    o("  " + st(fmt("sS[k * %d + t]", B), "Sk"));
+    o("}");
+    count_fma(ns * (ns - 1) * 5.0); count_exp(ns * (ns - 1.0));
+  } else {
+    o("#pragma unroll 1");
+    o(fmt("for (int k = 0; k < %d; ++k) {", ns - 1));
+    o(fmt("  %s Sk = %s;", md.ty, ld(fmt("sS[k * %d + t]", B)).c_str()));
+    o(fmt("  const %s Xk = %s;", md.ty, ld(fmt("sX[k * %d + t]", B)).c_str()));
+    o("  #pragma unroll 2");
+    o(fmt("  for (int j = k + 1; j < %d; ++j) {", ns));
+    o("    " + pair_exp);
+    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
+    o(fmt("    const %s Sj = %s;", md.ty, FMA("Xk", "e", ld(fmt("sS[j * %d + t]", B))).c_str()));
+    o("    " + st(fmt("sS[j * %d + t]", B), "Sj"));
+    o("  }");
+    o("  " + st(fmt("sS[k * %d + t]", B), "Sk"));
+    o("}");
+    count_fma(ns * (ns - 1) / 2.0 * 6); count_exp(ns * (ns - 1) / 2.0);
   }
   o(fmt("const double pr = %s / P;", D(P_ATM).c_str()));
-  const char* CV = mx ? "kx_f2d" : "";
-  o(fmt("out0_[i] = %s(mu);", CV));
-  o(fmt("out1_[i] = %s(%s * (sl + %s / sil));", CV, lit(0.5).c_str(), lit(1.0).c_str()));
-  for (int k = 0; k < ns; ++k) {
-    // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
-    o(fmt("{ const %s Sk = sS[%d + t]; out2_[(long long)%d * ld + i] = %s(Sk > 0 ? %s(-sX[%d + t], %s * iWbar, %s) / Sk : %s(%s)) * pr; }",
-          TY, k * opt.block, k, CV, FMA, k * opt.block, lit(m.W[k]).c_str(), lit(1.0).c_str(), EXP,
-          horner(&m.dif[5 * ((size_t)k * ns + k)], 1.0, 0.0).c_str()));
-    cnt(3);
-    c.fp64 += 1;
-    if (mx) c.div32 += 1; else c.div64 += 1;
-  }
+  o("out0_[i] = mu;");
+  o(fmt("out1_[i] = 0.5 * (%s + 1.0 / %s);", TOD("sl").c_str(), TOD("sil").c_str()));
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o(fmt("  const double Sk = %s, Xk = %s;", TOD(ld(fmt("sS[k * %d + t]", B))).c_str(), TOD(ld(fmt("sX[k * %d + t]", B))).c_str()));
+  o("  const double* ds = kx_dself + 5 * k;");
+  // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
+  o("  out2_[(long long)k * ld + i] = Sk > 0.0 ? fma(-Xk, kx_w[k] * iWbar, 1.0) * pr / Sk"
+    " : kx_exp(fma(fma(fma(fma(ds[4], lnT, ds[3]), lnT, ds[2]), lnT, ds[1]), lnT, ds[0])) * pr;");
+  o("}");
+  c.fp64 += 5 * ns + 4; c.div64 += ns + 2;
 }
 
 }  // namespace
@@ -1131,7 +1281,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[1024];\n";
+  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[1024];\n__shared__ float2 kx_s_dexp[256];\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();

@@ -64,6 +64,7 @@ struct EmitOptions {
   bool mixed = false;       // float32 bulk arithmetic
   int diff_mode = 1;        // 1 symmetric pairs, 2 full matrix
   int kc_mode = 0;          // 0 log space, 1 per-species exponential products
+  int tr_mode = 0;          // float64 transport: 0 double-float on the float32 pipe, 1 native float64
   int block = 128;
 };
 
