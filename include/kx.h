@@ -117,6 +117,14 @@ kx_status kx_thermo(kx_handle h, const double* T, const double* p, const double*
 kx_status kx_transport(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                        double* mu, double* lambda, double* Dk, int64_t n, kx_precision precision, void* stream);
 
+/* The two halves of kx_transport, for callers that need only one of them:
+ * Wilke viscosity mu[n] and Mathur conductivity lambda[n]; and the
+ * mixture-averaged diffusion coefficients Dk[N_s][ld] (Eq. (mix_diff)). */
+kx_status kx_viscosity_conductivity(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                    double* mu, double* lambda, int64_t n, kx_precision precision, void* stream);
+kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* Dk,
+                       int64_t n, kx_precision precision, void* stream);
+
 /* Vector-Jacobian product of the production rates at fixed p: for each
  * point, gT = sum_k v_k d wdot_k/dT and gY[j] = sum_k v_k d wdot_k/dY_j,
  * with v[N_s][ld] and gY[N_s][ld].  The paper lists the analytical
@@ -126,7 +134,7 @@ kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p,
 
 /* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
  * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
- * "transport_fp64", "transport_mixed", "vjp".  Any output pointer may be
+ * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp".  Any output pointer may be
  * NULL.  fp64_ops/fp32_ops/exps: the emitter's per-point operation counts. */
 kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes,
                          double* compile_seconds, double* fp64_ops, double* fp32_ops, double* exps);

@@ -290,12 +290,13 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   kx_status s = kx::parse_mechanism(path, h->m, err);
   if (s != KX_OK) return fail(s, err);
 
-  struct Spec { const char* name; kx::KernelKind kind; bool mixed; };
+  struct Spec { const char* name; kx::KernelKind kind; bool mixed; int part; };
   const Spec specs[] = {
-      {"wdot_fp64", kx::KernelKind::Wdot, false},       {"wdot_mixed", kx::KernelKind::Wdot, true},
-      {"rop_fp64", kx::KernelKind::Rop, false},         {"rop_mixed", kx::KernelKind::Rop, true},
-      {"thermo", kx::KernelKind::Thermo, false},        {"transport_fp64", kx::KernelKind::Transport, false},
-      {"transport_mixed", kx::KernelKind::Transport, true}, {"vjp", kx::KernelKind::Vjp, false},
+      {"wdot_fp64", kx::KernelKind::Wdot, false, 0},      {"wdot_mixed", kx::KernelKind::Wdot, true, 0},
+      {"rop_fp64", kx::KernelKind::Rop, false, 0},        {"rop_mixed", kx::KernelKind::Rop, true, 0},
+      {"thermo", kx::KernelKind::Thermo, false, 0},       {"visc_fp64", kx::KernelKind::Transport, false, 1},
+      {"diff_fp64", kx::KernelKind::Transport, false, 2}, {"visc_mixed", kx::KernelKind::Transport, true, 1},
+      {"diff_mixed", kx::KernelKind::Transport, true, 2}, {"vjp", kx::KernelKind::Vjp, false, 0},
   };
   for (const Spec& sp : specs) {
     std::unique_ptr<Kernel> k(new Kernel());
@@ -307,10 +308,11 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.diff_mode = h->opt.diff_mode == 2 ? 2 : 1;
     k->eopt.kc_mode = h->opt.kc_mode;
     k->eopt.tr_mode = h->opt.tr_mode;
+    k->eopt.part = sp.part;
     if (sp.kind == kx::KernelKind::Transport) {
-      // species vectors staged in shared memory: as many threads as fit in ~200 KB, a multiple of 32
-      const int per = kx::transport_smem_per_thread(h->m, sp.mixed);
-      int b = std::min(std::max(h->opt.block, 256), (200 * 1024 / per) / 32 * 32);
+      // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
+      const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);
+      int b = std::min(std::max(h->opt.block, 256), (216 * 1024 / per) / 32 * 32);
       if (b >= 128) b = b / 128 * 128;   // whole warps on every SM sub-partition
       if (b < 32) return fail(KX_ERR_UNSUPPORTED, "mechanism too large for the transport kernel");
       k->eopt.block = b;
@@ -394,14 +396,35 @@ kx_status kx_thermo(kx_handle h, const double* T, const double* p, const double*
 
 kx_status kx_transport(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* mu,
                        double* lambda, double* Dk, int64_t n, kx_precision precision, void* stream) {
+  kx_status s = kx_viscosity_conductivity(h, T, p, Y, ld, mu, lambda, n, precision, stream);
+  if (s != KX_OK) return s;
+  return kx_diffusion(h, T, p, Y, ld, Dk, n, precision, stream);
+}
+
+kx_status kx_viscosity_conductivity(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                    double* mu, double* lambda, int64_t n, kx_precision precision, void* stream) {
   kx_status s = check_state(h, T, p, Y, ld, n);
   if (s != KX_OK) return s;
-  if (n > 0 && (!mu || !lambda || !Dk)) return fail(KX_ERR_ARG, "null output");
+  if (n > 0 && (!mu || !lambda)) return fail(KX_ERR_ARG, "null output");
   if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
   if (n == 0) return KX_OK;
   long long ldl = ld, nl = n;
-  void* args[] = {&T, &p, &Y, &ldl, &mu, &lambda, &Dk, &nl};
-  return launch(h, precision == KX_FP64 ? "transport_fp64" : "transport_mixed", args, n, stream);
+  double* none = nullptr;
+  void* args[] = {&T, &p, &Y, &ldl, &mu, &lambda, &none, &nl};
+  return launch(h, precision == KX_FP64 ? "visc_fp64" : "visc_mixed", args, n, stream);
+}
+
+kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* Dk,
+                       int64_t n, kx_precision precision, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && !Dk) return fail(KX_ERR_ARG, "null output");
+  if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  double* none = nullptr;
+  void* args[] = {&T, &p, &Y, &ldl, &none, &none, &Dk, &nl};
+  return launch(h, precision == KX_FP64 ? "diff_fp64" : "diff_mixed", args, n, stream);
 }
 
 kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,

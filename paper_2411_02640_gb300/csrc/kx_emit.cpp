@@ -72,6 +72,9 @@ __device__ __forceinline__ double kx_f2d(float f) {
 // Nearest integer of a float with |t| < 2^22, without the XU pipe.
 __device__ __forceinline__ int kx_rint(float t) { return __float_as_int(t + KX_RND_F) - 0x4b400000; }
 
+#if KX_T64
+__shared__ double kx_s_exp[256];
+__shared__ double kx_s_log[1024];
 // float64 exp: x = k ln2/256 + r with k = rint(x 256/ln2) found in float32
 // and r by a two-constant Cody-Waite reduction in float64; e^r - 1 =
 // r + r^2 q(r) with the short tail q in float32 (|r^2 q| < 1.1e-6, so its
@@ -118,14 +121,7 @@ __device__ __forceinline__ double kx_log(double x) {
 #endif
 }
 
-__device__ __forceinline__ void kx_load_tables() {
-#ifndef KX_LIBMATH
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
-  for (int t = threadIdx.x; t < 1024; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
-#endif
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_dexp[t] = kx_dexp2_tab[t];
-  __syncthreads();
-}
+#endif  // KX_T64
 
 // fac * 2^t as a float64 for |t| up to ~1100 and fac in [0, 1]: the
 // mantissa comes from float32 exp2 of t minus its nearest integer n, the
@@ -168,6 +164,20 @@ __device__ __forceinline__ float kx_ln_inv_1p(float lnPr) {
   return lnPr < 0.0f ? -log1pf(__expf(lnPr)) : -(lnPr + log1pf(__expf(-lnPr)));
 }
 
+#if KX_TDF
+__shared__ float2 kx_s_dexp[256];
+#endif
+__device__ __forceinline__ void kx_load_tables() {
+#if KX_T64 && !defined(KX_LIBMATH)
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) kx_s_log[t] = kx_log_tab[t];
+#endif
+#if KX_TDF
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_dexp[t] = kx_dexp2_tab[t];
+#endif
+  __syncthreads();
+}
+
 // ---- double-float (float32 pair) arithmetic for float64-accurate work on
 // the float32 pipe.  Error-free transformations after Knuth (two-sum),
 // Dekker (fast two-sum) and the FMA two-product; the __f*_rn intrinsics keep
@@ -199,6 +209,7 @@ __device__ __forceinline__ kx_df kx_d2df(double x) {
   const float h = kx_d2f(x);
   return kx_mk(h, kx_d2f(x - kx_f2d(h)));
 }
+#if KX_TDF
 // e^x of a double-float x: x = k ln2/256 + r (k from the high part in
 // float32, ln2/256 split in three floats, the first short enough that k C1
 // is exact), e^r = 1 + r + r^2 q(r) with the tail in float32, times
@@ -222,6 +233,7 @@ __device__ __forceinline__ kx_df kx_df_exp(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+#endif  // KX_TDF
 )KXPRE";
 
 namespace {
@@ -1124,8 +1136,9 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     g(fmt("__device__ const %s kx_pv[%d] = {%s};", T, 5 * ns, pv.c_str()));
     g(fmt("__device__ const %s kx_pl[%d] = {%s};", T, 5 * ns, pl.c_str()));
     g(fmt("__device__ const %s kx_wa[%d] = {%s};", T, ns * ns, wa.c_str()));
-    g(fmt("__device__ const %s kx_dc[%d] __attribute__((aligned(16))) = {%s%s};", T, 6 * np + 2, dc.c_str(),
-          (lit(0.0) + "," + lit(0.0)).c_str()));
+    std::string pad;
+    for (int n = 0; n < 6; ++n) pad += lit(0.0) + (n < 5 ? "," : "");
+    g(fmt("__device__ const %s kx_dc[%d] __attribute__((aligned(16))) = {%s%s};", T, 6 * np + 6, dc.c_str(), pad.c_str()));
     g(fmt("__device__ const double kx_dself[%d] = {%s};", 5 * ns, dself.c_str()));
     g(fmt("__device__ const double kx_w[%d] = {%s};", ns, w.c_str()));
     g(fmt("__device__ const double kx_iw[%d] = {%s};", ns, iw.c_str()));
@@ -1145,6 +1158,13 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("if (!(isig > 0 && isig < KX_INF)) KX_BAD_POINT");
   o("const double iWbar = 1.0 / (sY * isig);");
   c.fp64 += 2 * ns + 1; c.div64 += 2;
+  const bool p1 = opt.part != 2, p2 = opt.part != 1;
+  if (!p1) {
+    o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(fmt("sX[k * %d + t]", B),
+                                                    FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig")).c_str()));
+    c.fp64 += ns;
+  }
+  if (p1) {
   // per species: X, v = 1/u, z1 = X v, z2 = X v^2, Mathur sums
   o(fmt("%s sl = %s, sil = %s;", md.ty, ZERO.c_str(), ZERO.c_str()));
   o("#pragma unroll 1");
@@ -1183,20 +1203,34 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("}");
   count_fma(ns * (3.0 * ns + 8)); count_exp(ns);
   c.fp64 += 4 * ns; c.div64 += ns;
+  o("out0_[i] = mu;");
+  o(fmt("out1_[i] = 0.5 * (%s + 1.0 / %s);", TOD("sl").c_str(), TOD("sil").c_str()));
+  c.fp64 += 4; c.div64 += 1;
+  }  // part 1
+  if (!p2) return;
   // mixture-averaged diffusion, S in the sZ1 columns
   o(fmt("%s* const sS = sZ1;", md.st));
   o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(fmt("sS[k * %d + t]", B), ZERO).c_str()));
   o(fmt("const %s* cf = kx_dc;", md.st));
-  std::string pair_exp;
-  if (md.kind == TrMode::DF)
-    pair_exp = "const float4 c01 = *(const float4*)(cf), c23 = *(const float4*)(cf + 2), c45 = *(const float4*)(cf + 4); cf += 6;\n"
-               "      const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma(kx_df_fma(kx_df_fma(kx_mk(c45.x, c45.y), L, kx_mk(c23.z, c23.w)), L, "
-               "kx_mk(c23.x, c23.y)), L, kx_mk(c01.z, c01.w)), L, kx_mk(c01.x, c01.y)));";
-  else if (md.kind == TrMode::F64)
-    pair_exp = "const double2 c01 = *(const double2*)(cf), c23 = *(const double2*)(cf + 2), c45 = *(const double2*)(cf + 4); cf += 6;\n"
-               "      const double e = kx_exp(fma(fma(fma(fma(c45.x, L, c23.y), L, c23.x), L, c01.y), L, c01.x));";
-  else
-    pair_exp = "const float e = exp2f(fmaf(fmaf(fmaf(fmaf(cf[4], L, cf[3]), L, cf[2]), L, cf[1]), L, cf[0])); cf += 6;";
+  // the next pair's coefficients are loaded one iteration ahead (the table
+  // carries one zero pair of padding), so their latency hides behind the
+  // current pair's arithmetic
+  std::string vec, pre, take, pair_exp;
+  if (md.kind == TrMode::DF) {
+    vec = "float4";
+    pair_exp = "const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma(kx_df_fma(kx_df_fma(kx_mk(c2.x, c2.y), L, kx_mk(c1.z, c1.w)), L, "
+               "kx_mk(c1.x, c1.y)), L, kx_mk(c0.z, c0.w)), L, kx_mk(c0.x, c0.y)));";
+  } else if (md.kind == TrMode::F64) {
+    vec = "double2";
+    pair_exp = "const double e = kx_exp(fma(fma(fma(fma(c2.x, L, c1.y), L, c1.x), L, c0.y), L, c0.x));";
+  } else {
+    vec = "float2";
+    pair_exp = "const float e = exp2f(fmaf(fmaf(fmaf(fmaf(c2.x, L, c1.y), L, c1.x), L, c0.y), L, c0.x));";
+  }
+  o(fmt("const %s* cq = (const %s*)kx_dc;", vec.c_str(), vec.c_str()));
+  o(fmt("%s n0 = cq[0], n1 = cq[1], n2 = cq[2];", vec.c_str()));
+  take = fmt("const %s c0 = n0, c1 = n1, c2 = n2; cq += 3; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];", vec.c_str());
+  pair_exp = take + "\n      " + pair_exp;
   if (opt.diff_mode == 2) {
     o("#pragma unroll 1");
     o(fmt("for (int k = 0; k < %d; ++k) {", ns));
@@ -1227,14 +1261,12 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     count_fma(ns * (ns - 1) / 2.0 * 6); count_exp(ns * (ns - 1) / 2.0);
   }
   o(fmt("const double pr = %s / P;", D(P_ATM).c_str()));
-  o("out0_[i] = mu;");
-  o(fmt("out1_[i] = 0.5 * (%s + 1.0 / %s);", TOD("sl").c_str(), TOD("sil").c_str()));
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const double Sk = %s, Xk = %s;", TOD(ld(fmt("sS[k * %d + t]", B))).c_str(), TOD(ld(fmt("sX[k * %d + t]", B))).c_str()));
   o("  const double* ds = kx_dself + 5 * k;");
   // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
   o("  out2_[(long long)k * ld + i] = Sk > 0.0 ? fma(-Xk, kx_w[k] * iWbar, 1.0) * pr / Sk"
-    " : kx_exp(fma(fma(fma(fma(ds[4], lnT, ds[3]), lnT, ds[2]), lnT, ds[1]), lnT, ds[0])) * pr;");
+    " : exp(fma(fma(fma(fma(ds[4], lnT, ds[3]), lnT, ds[2]), lnT, ds[1]), lnT, ds[0])) * pr;");
   o("}");
   c.fp64 += 5 * ns + 4; c.div64 += ns + 2;
 }
@@ -1242,7 +1274,9 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
 }  // namespace
 
 // Shared memory per thread of the transport kernels, in bytes.
-int transport_smem_per_thread(const Mechanism& m, bool mixed) { return 3 * m.ns * (mixed ? 4 : 8); }
+int transport_smem_per_thread(const Mechanism& m, bool mixed, int part) {
+  return (part == 2 ? 2 : 3) * m.ns * (mixed ? 4 : 8);
+}
 
 // ------------------------------------------------------------------ kernels
 std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
@@ -1281,7 +1315,10 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  s << "__shared__ double kx_s_exp[256];\n__shared__ double kx_s_log[1024];\n__shared__ float2 kx_s_dexp[256];\n";
+  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport;
+  const bool tdf = kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0;
+  s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
+  s << "#define KX_TDF " << tdf << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();

@@ -66,6 +66,7 @@ struct EmitOptions {
   int kc_mode = 0;          // 0 log space, 1 per-species exponential products
   int tr_mode = 0;          // float64 transport: 0 double-float on the float32 pipe, 1 native float64
   int block = 128;
+  int part = 0;             // transport: 0 all outputs, 1 viscosity and conductivity, 2 diffusion
 };
 
 // Operation counts per point, tallied while emitting (library calls such as
@@ -79,7 +80,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
                         OpCounts* counts);
 
 // Dynamic shared memory per thread that a kernel of this kind needs.
-int transport_smem_per_thread(const Mechanism& m, bool mixed);
+int transport_smem_per_thread(const Mechanism& m, bool mixed, int part);
 
 // Device-side helper functions prepended to every generated kernel.
 extern const char* kDevicePrelude;

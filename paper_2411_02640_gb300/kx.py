@@ -19,7 +19,8 @@ _lib: Optional[ctypes.CDLL] = None
 FP64, MIXED = 0, 1
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
-KERNELS = ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "transport_fp64", "transport_mixed", "vjp")
+KERNELS = ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "visc_fp64", "visc_mixed", "diff_fp64",
+           "diff_mixed", "vjp")
 
 
 class KxError(RuntimeError):
@@ -55,6 +56,8 @@ def lib() -> ctypes.CDLL:
         L.kx_rates_of_progress.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_thermo.argtypes = [vp, dp, dp, dp, i64, dp, dp, i64, vp]
         L.kx_transport.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, ctypes.c_int, vp]
+        L.kx_viscosity_conductivity.argtypes = [vp, dp, dp, dp, i64, dp, dp, i64, ctypes.c_int, vp]
+        L.kx_diffusion.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_production_rates_vjp.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, vp]
         L.kx_kernel_info.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -174,6 +177,20 @@ class Mechanism:
         _check(lib().kx_transport(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(mu), _ptr(lam), _ptr(D), n,
                                   _PREC[precision], _stream(stream)))
         return mu, lam, D
+
+    def viscosity_conductivity(self, T, p, Y, out: Optional[Tuple] = None, precision="fp64", stream=None):
+        n, ld = self._state(T, p, Y)
+        mu, lam = out if out is not None else (self._alloc(None, n, ld, T), self._alloc(None, n, ld, T))
+        _check(lib().kx_viscosity_conductivity(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(mu), _ptr(lam), n,
+                                               _PREC[precision], _stream(stream)))
+        return mu, lam
+
+    def diffusion(self, T, p, Y, out=None, precision="fp64", stream=None):
+        n, ld = self._state(T, p, Y)
+        D = out if out is not None else self._alloc(self.n_species, n, ld, T)
+        assert n == 0 or D.stride(0) == ld
+        _check(lib().kx_diffusion(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(D), n, _PREC[precision], _stream(stream)))
+        return D
 
     def production_rates_vjp(self, T, p, Y, v, out: Optional[Tuple] = None, stream=None):
         """gT[n] = sum_k v_k d wdot_k/dT, gY[N_s, ld] = sum_k v_k d wdot_k/dY_j (p fixed)."""

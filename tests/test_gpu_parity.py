@@ -79,11 +79,13 @@ def test_thermo(torch, name):
     assert np.max(np.abs(h - h_ref) / (np.abs(h_ref) + 1e-3 * np.abs(h_ref).max())) < 1e-9
 
 
+@pytest.mark.parametrize("tr_mode", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_transport_fp64(torch, name):
+def test_transport_fp64(torch, name, tr_mode):
+    """tr_mode 0: double-float arithmetic on the float32 pipe; 1: native float64."""
     n = CASES[name]
     T, p, Y = _states(name, n, start=3)
-    mech = mechanism(name)
+    mech = mechanism(name, tr_mode=tr_mode)
     Td, pd, Yd = to_device(torch, T, p, Y, ld=n + LD_PAD)
     mu, lam, D = (t.cpu().numpy() for t in mech.transport(Td, pd, Yd))
     mu_r, lam_r, D_r = oracle(name).transport(T, p, Y)
