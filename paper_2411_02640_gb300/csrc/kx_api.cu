@@ -134,7 +134,7 @@ kx_status compile_kernel(kx_mech* h, Kernel& k) {
   if (k.source.empty()) return fail(KX_ERR_UNSUPPORTED, "kernel " + k.name + " is not available");
   std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
   if (h->opt.libmath) opts.push_back("-DKX_LIBMATH");
-  if (h->opt.maxrreg > 0) opts.push_back("--maxrregcount=" + std::to_string(h->opt.maxrreg));
+
   std::string key = std::string(KX_VERSION) + "\n";
   for (auto& o : opts) key += o + "\n";
   int ver_major = 0, ver_minor = 0;
@@ -309,6 +309,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.kc_mode = h->opt.kc_mode;
     k->eopt.tr_mode = h->opt.tr_mode;
     k->eopt.part = sp.part;
+    k->eopt.maxrreg = h->opt.maxrreg;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
       const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);

@@ -1303,7 +1303,10 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       break;
     case KernelKind::Transport:
       outs = "double* __restrict__ out0_, double* __restrict__ out1_, double* __restrict__ out2_";
-      nan_fill = fmt("out0_[i] = KX_NAN; out1_[i] = KX_NAN; for (int k = 0; k < %d; ++k) out2_[(long long)k * ld + i] = KX_NAN;", m.ns);
+      // each half writes only its own outputs (the other pointers are null)
+      if (opt.part == 1) nan_fill = "out0_[i] = KX_NAN; out1_[i] = KX_NAN;";
+      else if (opt.part == 2) nan_fill = fmt("for (int k = 0; k < %d; ++k) out2_[(long long)k * ld + i] = KX_NAN;", m.ns);
+      else nan_fill = fmt("out0_[i] = KX_NAN; out1_[i] = KX_NAN; for (int k = 0; k < %d; ++k) out2_[(long long)k * ld + i] = KX_NAN;", m.ns);
       emit_transport(body, globals, m, opt, c);
       break;
     case KernelKind::Vjp:
@@ -1323,7 +1326,12 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
-  s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ") " << entry
+  // a register cap is expressed as a minimum number of resident blocks (ptxas
+  // ignores --maxrregcount for kernels that carry launch bounds)
+  const int min_blocks = opt.maxrreg > 0 ? std::max(1, 65536 / (opt.maxrreg * opt.block)) : 0;
+  s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
+  if (min_blocks > 0) s << ", " << min_blocks;
+  s << ") " << entry
     << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
     << outs << ", long long n)\n{\n";
   s << "  kx_load_tables();\n";

@@ -67,6 +67,7 @@ struct EmitOptions {
   int tr_mode = 0;          // float64 transport: 0 double-float on the float32 pipe, 1 native float64
   int block = 128;
   int part = 0;             // transport: 0 all outputs, 1 viscosity and conductivity, 2 diffusion
+  int maxrreg = 0;          // register cap per thread (0: compiler choice)
 };
 
 // Operation counts per point, tallied while emitting (library calls such as
