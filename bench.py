@@ -318,9 +318,90 @@ def run_kx(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        if world == 1 and not args.no_serve:
+            srv = run_serve_suite(args, sweep=False)
+            line["serving"] = {"p50_ms": srv["batching"][0]["p50_ms"], "p99_ms": srv["batching"][0]["p99_ms"],
+                               "mpoints_s": srv["batching"][0]["mpoints_s"], "rate_req_s": srv["batching"][0]["rate_req_s"],
+                               "requests": srv["batching"][0]["requests"],
+                               "one_at_a_time": {k: srv["one_at_a_time"][0][k] for k in ("p50_ms", "p99_ms", "mpoints_s")},
+                               "workload": "Poisson arrivals, 1e3-2e6 states per request, mechanisms 9/21, 53/325, "
+                                           "160/900; 70% mixed, 20% with transport; host (pinned) in and out"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+SERVE_MECHS = ("h2o2_9_21", "gri_53_325", "large_160_900")
+
+
+def serve_pools(points: int):
+    """Per mechanism a pool of seeded states (2^20 drawn, tiled to 2x) that
+    requests slice; pinned host memory, as CFD ranks would hand over."""
+    import torch
+    from paper_2411_02640_gb300 import synth
+    pools = {}
+    for name in SERVE_MECHS:
+        m = synth.mechanism(name)
+        T, p, Y = synth.make_states(m.n_species, synth.STATE_SPECS[name], 0, points)
+        pools[name] = tuple(np.concatenate([a, a], axis=-1) for a in (T, p, Y))
+    return pools
+
+
+def serve_run(mechs, pools, rate: float, count: int, seed: int, coalesce: bool, streams: int, budget: int):
+    """Poisson arrivals at `rate` requests/s; sizes log-uniform 1e3..2e6 states;
+    mechanism uniform over the three; 70 % mixed / 30 % float64; 20 % also
+    transport.  Returns throughput and latency statistics."""
+    from paper_2411_02640_gb300.serve import Server
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(count):
+        name = SERVE_MECHS[rng.integers(len(SERVE_MECHS))]
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(2e6))))
+        off = int(rng.integers(0, pools[name][0].shape[0] - n))
+        reqs.append((name, off, n, "mixed" if rng.random() < 0.7 else "fp64", bool(rng.random() < 0.2)))
+    gaps = rng.exponential(1.0 / rate, count)
+    srv = Server(mechs, hbm_budget=budget, streams=streams, coalesce=coalesce).start()
+    futs = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for (name, off, n, prec, tr), gap in zip(reqs, gaps):
+        t_next += gap
+        d = t_next - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        T, p, Y = pools[name]
+        futs.append(srv.submit(name, T[off:off + n], p[off:off + n], Y[:, off:off + n], precision=prec, transport=tr))
+    for f in futs:
+        f.result(timeout=600)
+    t1 = time.perf_counter()
+    srv.stop()
+    st = srv.stats()
+    pts = sum(r[2] for r in reqs)
+    return {"rate_req_s": rate, "requests": count, "mpoints_s": pts / (t1 - t0) / 1e6, "p50_ms": st["p50_ms"],
+            "p99_ms": st["p99_ms"], "launches": st["launches"], "coalesce": coalesce, "streams": streams}
+
+
+def run_serve_suite(args, sweep=True):
+    import torch
+    from paper_2411_02640_gb300 import kx, synth
+    torch.cuda.set_device(0)
+    mechs = {n: kx.Mechanism(synth.mechanism_file(n, os.path.join(CACHE, "mech")), cache_dir=CACHE)
+             for n in SERVE_MECHS}
+    pools = serve_pools(1 << 20)
+    budget = 48 << 30
+    # warm every kernel once
+    for name, m in mechs.items():
+        T, p, Y = (torch.from_numpy(a[..., :4096].copy()).cuda() for a in pools[name])
+        for prec in ("fp64", "mixed"):
+            m.production_rates(T, p, Y, precision=prec)
+            m.transport(T, p, Y, precision=prec)
+    torch.cuda.synchronize()
+    rates = [2.0, 4.0, 8.0, 16.0] if sweep else [4.0]
+    out = {"budget_bytes": budget, "mechanisms": list(SERVE_MECHS), "batching": [], "one_at_a_time": []}
+    for r in rates:
+        out["batching"].append(serve_run(mechs, pools, r, args.serve_requests, 105, True, 4, budget))
+        out["one_at_a_time"].append(serve_run(mechs, pools, r, args.serve_requests, 105, False, 1, budget))
+    return out
 
 
 def ops_per_point(mech, name):
@@ -339,9 +420,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=POINTS, help="states per GPU (profiling of smaller cases)")
     ap.add_argument("--maxrreg", type=int, default=0, help="register cap for the generated kernels (0: compiler)")
+    ap.add_argument("--serve", action="store_true", help="serving sweep (rates x batching vs one at a time) only")
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sample in the default line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        print(json.dumps({"metric": "serving", "serving": run_serve_suite(args, sweep=True)}), flush=True)
     else:
         run_kx(args)
 

@@ -69,9 +69,13 @@ typedef struct {
                          1 per-species exp(-G_k/RT) products, one division per reaction */
   int tr_mode;        /* float64 transport: 0 (default) double-float arithmetic on the float32
                          pipe (float64 accuracy, ~2^-47 per operation), 1 native float64 */
+  int rates_mode;     /* production-rate kernels: 0 (default) automatic -- fully unrolled up to 64
+                         species and 400 reactions, table driven beyond; 1 unrolled; 2 table driven */
   int maxrreg;        /* register cap per thread for the generated kernels; 0 = compiler choice */
   int block;          /* threads per block; 0 = 128 */
-  int lazy;           /* 0: compile every kernel at load (in parallel); 1: on first use */
+  int lazy;           /* 0: compile the production-rate, thermo and transport kernels at load
+                         (in parallel), the rates-of-progress and adjoint kernels on first
+                         use; 1: every kernel on first use */
   int verbose;        /* 1: print compile times and register/spill counts to stderr */
   int libmath;        /* 1: CUDA's exp/log in the float64 kernels instead of the library's own */
   int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);

@@ -283,6 +283,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.diff_mode < 0 || h->opt.diff_mode > 2) return fail(KX_ERR_ARG, "diff_mode must be 0, 1 or 2");
   if (h->opt.kc_mode < 0 || h->opt.kc_mode > 1) return fail(KX_ERR_ARG, "kc_mode must be 0 or 1");
   if (h->opt.tr_mode < 0 || h->opt.tr_mode > 1) return fail(KX_ERR_ARG, "tr_mode must be 0 or 1");
+  if (h->opt.rates_mode < 0 || h->opt.rates_mode > 2) return fail(KX_ERR_ARG, "rates_mode must be 0, 1 or 2");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
   h->opt.cache_dir = nullptr;
@@ -310,6 +311,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.tr_mode = h->opt.tr_mode;
     k->eopt.part = sp.part;
     k->eopt.maxrreg = h->opt.maxrreg;
+    k->eopt.rates_mode = h->opt.rates_mode;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
       const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);
@@ -322,20 +324,25 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     h->kernels.push_back(std::move(k));
   }
   if (!h->opt.lazy) {
-    // compile in parallel (NVRTC programs are independent), load serially
+    // compile the kernels of the production-rate, thermo and transport calls
+    // in parallel (NVRTC programs are independent) and load them; the
+    // rates-of-progress and adjoint kernels compile on first use
+    std::vector<Kernel*> eager;
+    for (auto& k : h->kernels)
+      if (k->kind != kx::KernelKind::Rop && k->kind != kx::KernelKind::Vjp) eager.push_back(k.get());
     std::vector<std::thread> th;
-    std::vector<kx_status> st(h->kernels.size(), KX_OK);
-    std::vector<std::string> msg(h->kernels.size());
-    for (size_t i = 0; i < h->kernels.size(); ++i)
+    std::vector<kx_status> st(eager.size(), KX_OK);
+    std::vector<std::string> msg(eager.size());
+    for (size_t i = 0; i < eager.size(); ++i)
       th.emplace_back([&, i] {
-        st[i] = compile_kernel(h.get(), *h->kernels[i]);
+        st[i] = compile_kernel(h.get(), *eager[i]);
         if (st[i] != KX_OK) msg[i] = g_last_error;
       });
     for (auto& t : th) t.join();
     for (size_t i = 0; i < st.size(); ++i)
       if (st[i] != KX_OK) return fail(st[i], msg[i]);
     if (!h->opt.compile_only)
-      for (auto& k : h->kernels) {
+      for (Kernel* k : eager) {
         s = ensure_ready(h.get(), *k);
         if (s != KX_OK) return s;
       }

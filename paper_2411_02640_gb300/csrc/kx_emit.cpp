@@ -776,6 +776,251 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
     for (int k = 0; k < m.ns; ++k) o(fmt("out_[(long long)%d * ld + i] = w_%d;", k, k));
 }
 
+// ------------------------------------------------------------------ rates, table driven
+// For large mechanisms the fully unrolled kernels spill heavily and take
+// minutes to compile.  This variant keeps thread-per-point but walks a
+// reaction table in a loop: every thread of a warp handles the same
+// reaction at the same time, so the control flow and the table loads are
+// uniform (broadcasts), and the species state (C_k, G_k/RT, wdot_k) lives
+// in per-thread local-memory arrays indexed by the table's species numbers
+// (interleaved across threads, so each access is one coalesced line).
+// Same arithmetic, in the same order per reaction, as the unrolled kernels.
+//
+// Reaction record: ints  {kind, reversible, n_reac, n_prod, dn, eff_offset,
+//                         n_eff, blend, plog_offset, n_plog, const_kf, pad,
+//                         species[6], nu[6]}
+//                  doubles {ln A, beta, -E, ln A0, beta0, -E0, default_eff,
+//                           blend parameters[5], pad...}
+constexpr int RI = 24, RD = 16;
+
+void emit_rate_tables(Out& g, const Mechanism& m, bool mixed) {
+  std::string ri, rd, eff, plog, nasa, tm;
+  int eo = 0, po = 0;
+  for (const Reaction& r : m.rx) {
+    int kind = r.kind == Kind::Elementary ? 0 : r.kind == Kind::ThreeBody ? 1 : r.kind == Kind::Falloff ? 2
+             : r.kind == Kind::ChemAct ? 3 : 4;
+    int blend = r.blend == Blend::Lindemann ? 0 : r.blend == Blend::Troe ? 1 : 2;
+    int ne = 0;
+    std::string e;
+    if (r.third_body()) {
+      if (r.collider >= 0) { e += fmt("%d,", r.collider); ne = -1; }   // collider marker
+      else for (auto& x : r.eff) if (x.second != r.default_eff) { e += fmt("%d,", x.first); ++ne; }
+    }
+    const bool constk = (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && r.k.beta == 0.0 && r.k.E == 0.0;
+    int v[RI] = {kind, r.reversible ? 1 : 0, (int)r.reac.size(), (int)r.prod.size(), sum_nu(r), eo, ne, blend, po,
+                 (int)r.plog.size(), constk ? 1 : 0, 0};
+    for (size_t j = 0; j < r.reac.size(); ++j) { v[12 + j] = r.reac[j].first; v[18 + j] = r.reac[j].second; }
+    for (size_t j = 0; j < r.prod.size(); ++j) { v[12 + r.reac.size() + j] = r.prod[j].first; v[18 + r.reac.size() + j] = r.prod[j].second; }
+    for (int j = 0; j < RI; ++j) ri += std::to_string(v[j]) + ",";
+    double d[RD] = {std::log(r.k.A > 0 ? r.k.A : 1e-300), r.k.beta, -r.k.E, 0, 0, 0, r.default_eff, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (r.has_k0) { d[3] = std::log(r.k0.A); d[4] = r.k0.beta; d[5] = -r.k0.E; }
+    if (r.blend == Blend::Troe) { d[7] = 1.0 - r.troe[0]; d[8] = r.troe[0]; d[9] = -1.0 / r.troe[1]; d[10] = -1.0 / r.troe[2]; d[11] = -r.troe[3]; }
+    if (r.blend == Blend::Sri) { d[7] = r.sri[0]; d[8] = -r.sri[1]; d[9] = -1.0 / r.sri[2]; d[10] = std::log(r.sri[3]); d[11] = r.sri[4]; }
+    for (int j = 0; j < RD; ++j) rd += (mixed ? F(d[j]) : D(d[j])) + ",";
+    // efficiency table entries: (species, alpha - default) ; collider: (species, 0)
+    if (r.third_body()) {
+      if (r.collider >= 0) { eff += fmt("{%d, %s},", r.collider, D(0.0).c_str()); eo += 1; }
+      else for (auto& x : r.eff) if (x.second != r.default_eff) { eff += fmt("{%d, %s},", x.first, D(x.second - r.default_eff).c_str()); ++eo; }
+    }
+    for (auto& t : r.plog) { plog += fmt("%s,%s,%s,%s,", D(std::log(t[0])).c_str(), D(std::log(t[1])).c_str(), D(t[2]).c_str(), D(-t[3]).c_str()); ++po; }
+    (void)e;
+  }
+  g(fmt("__device__ const int kx_ri[%d] = {%s0};", RI * m.nr() + 1, ri.c_str()));
+  g(fmt("__device__ const %s kx_rd[%d] = {%s0};", mixed ? "float" : "double", RD * m.nr() + 1, rd.c_str()));
+  g("struct kx_eff_t { int k; double a; };");
+  g(fmt("__device__ const kx_eff_t kx_eff[%d] = {%s{0, 0.0}};", eo + 1, eff.c_str()));
+  g(fmt("__device__ const double kx_plog[%d] = {%s0.0};", 4 * po + 1, plog.c_str()));
+  // NASA-7 Gibbs coefficients as a polynomial in T plus a5/T - a0 ln T, both ranges, and Tmid
+  for (int k = 0; k < m.ns; ++k) {
+    for (int rg = 0; rg < 2; ++rg) {
+      const double* a = rg == 0 ? &m.a_lo[7 * k] : &m.a_hi[7 * k];
+      const double cfs[7] = {a[0] - a[6], -a[1] / 2.0, -a[2] / 6.0, -a[3] / 12.0, -a[4] / 20.0, a[5], -a[0]};
+      for (int j = 0; j < 7; ++j) nasa += D(cfs[j]) + ",";
+      nasa += D(0.0) + ",";
+    }
+    tm += D(m.Tmid[k]) + ",";
+  }
+  g(fmt("__device__ const double kx_gc[%d] = {%s0.0};", 16 * m.ns + 1, nasa.c_str()));
+  g(fmt("__device__ const double kx_tmid[%d] = {%s0.0};", m.ns + 1, tm.c_str()));
+  std::string iw, lw;
+  for (int k = 0; k < m.ns; ++k) { iw += D(1.0 / m.W[k]) + ","; lw += D(std::log(m.W[k])) + ","; }
+  g(fmt("__device__ const double kx_riw[%d] = {%s0.0};", m.ns + 1, iw.c_str()));
+  g(fmt("__device__ const double kx_rlw[%d] = {%s0.0};", m.ns + 1, lw.c_str()));
+}
+
+void emit_rates_table64(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts& c) {
+  emit_rate_tables(g, m, false);
+  const int ns = m.ns;
+  o("const double lnT = log(T);");
+  o("const double iT = 1.0 / T;");
+  o("const double lnP = kx_log(P);");
+  o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
+  o(fmt("double C[%d], g[%d]%s;", ns, ns, rop ? "" : fmt(", w[%d]", ns).c_str()));
+  o("double sig = 0.0;");
+  o(fmt("for (int k = 0; k < %d; ++k) { const double y = Y_[(long long)k * ld + i] * kx_riw[k]; C[k] = y; sig += y; }", ns));
+  o("if (!(sig > 0.0 && sig < KX_INF)) KX_BAD_POINT");
+  o("const double fC = cM / sig;");
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o("  C[k] *= fC;");
+  o("  const double* a = kx_gc + 16 * k + (T < kx_tmid[k] ? 0 : 8);");
+  o("  g[k] = fma(a[6], lnT, fma(a[5], iT, fma(fma(fma(fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0])));");
+  if (!rop) o("  w[k] = 0.0;");
+  o("}");
+  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
+  c.fp64 += ns * 9.0 + 6; c.div64 += 2; c.log64 += 2;
+  o("#pragma unroll 1");
+  o(fmt("for (int r = 0; r < %d; ++r) {", m.nr()));
+  o(fmt("  const int* h = kx_ri + %d * r; const double* d = kx_rd + %d * r;", RI, RD));
+  o("  const int kind = h[0];");
+  o("  double lkf = fma(d[1], lnT, fma(d[2], iT, d[0]));");
+  o("  double kf, X = 0.0;");
+  o("  if (kind >= 1 && kind <= 3) {");
+  o("    if (h[6] < 0) X = C[kx_eff[h[5]].k];");
+  o("    else { X = d[6] * cM; for (int e = 0; e < h[6]; ++e) X = fma(kx_eff[h[5] + e].a, C[kx_eff[h[5] + e].k], X); }");
+  o("  }");
+  o("  if (kind == 2 || kind == 3) {");
+  o("    const double lk0 = fma(d[4], lnT, fma(d[5], iT, d[3]));");
+  o("    const double lnPr = fmax(lk0 - lkf + kx_log(X), -690.77552789821368);");
+  o("    const double Pr = kx_exp(lnPr);");
+  o("    double F = 1.0;");
+  o("    if (h[7] == 1) {");
+  o("      const double lFc = kx_log(d[7] * kx_exp(T * d[9]) + d[8] * kx_exp(T * d[10]) + kx_exp(d[11] * iT)) * KX_INV_LN10;");
+  o("      const double xx = fma(lnPr, KX_INV_LN10, fma(-0.67, lFc, -0.4));");
+  o("      const double ff = xx / (fma(-1.27, lFc, 0.75) - 0.14 * xx);");
+  o("      F = kx_exp(KX_LN10 * lFc / fma(ff, ff, 1.0));");
+  o("    } else if (h[7] == 2) {");
+  o("      const double lPr = lnPr * KX_INV_LN10;");
+  o("      const double base = d[7] * kx_exp(d[8] * iT) + kx_exp(T * d[9]);");
+  o("      F = kx_exp(d[10] + fma(d[11], lnT, kx_log(base) / fma(lPr, lPr, 1.0)));");
+  o("    }");
+  o("    if (kind == 2) kf = kx_exp(lkf) * (Pr / (1.0 + Pr)) * F;");
+  o("    else { kf = kx_exp(lk0) * (1.0 / (1.0 + Pr)) * F; }");
+  o("    lkf = kx_log(kf);");
+  o("  } else if (kind == 4) {");
+  o("    const double* t = kx_plog + 4 * h[8]; const int np = h[9];");
+  o("    if (lnP <= t[0]) lkf = fma(t[2], lnT, fma(t[3], iT, t[1]));");
+  o("    else if (lnP >= t[4 * (np - 1)]) { const double* u = t + 4 * (np - 1); lkf = fma(u[2], lnT, fma(u[3], iT, u[1])); }");
+  o("    else { int j = 0; while (!(lnP < t[4 * (j + 1)])) ++j; const double* u = t + 4 * j;");
+  o("      const double l1 = fma(u[2], lnT, fma(u[3], iT, u[1])), l2 = fma(u[6], lnT, fma(u[7], iT, u[5]));");
+  o("      lkf = fma(l2 - l1, (lnP - u[0]) / (u[4] - u[0]), l1); }");
+  o("    kf = kx_exp(lkf);");
+  o("  } else {");
+  o("    kf = h[10] ? exp(d[0]) : kx_exp(lkf);");
+  o("  }");
+  o("  double Rf = kf, Rr = 0.0;");
+  o("  const int nre = h[2], npr = h[3];");
+  o("  for (int j = 0; j < nre; ++j) { const double cj = C[h[12 + j]]; Rf *= cj; if (h[18 + j] == 2) Rf *= cj; }");
+  o("  if (h[1]) {");
+  o("    double sg = 0.0;");
+  o("    for (int j = 0; j < nre + npr; ++j) { const double nu = (j < nre ? -1.0 : 1.0) * h[18 + j]; sg = fma(nu, g[h[12 + j]], sg); }");
+  o("    const double lnKc = fma((double)h[4], lnPRT, -sg);");
+  o("    Rr = kx_exp(lkf - lnKc);");
+  o("    for (int j = nre; j < nre + npr; ++j) { const double cj = C[h[12 + j]]; Rr *= cj; if (h[18 + j] == 2) Rr *= cj; }");
+  o("  }");
+  o("  double q = Rf - Rr;");
+  o("  if (kind == 1) q *= X;");
+  if (rop) o("  out_[(long long)r * ld + i] = q;");
+  else {
+    o("  for (int j = 0; j < nre + npr; ++j) { const double nu = (j < nre ? -1.0 : 1.0) * h[18 + j]; w[h[12 + j]] = fma(nu, q, w[h[12 + j]]); }");
+  }
+  o("}");
+  if (!rop) o(fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = w[k];", ns));
+  // counts: per reaction ~ 2 (lkf) + exps + products + lnKc + scatter
+  for (const Reaction& r : m.rx) {
+    c.fp64 += 2 + 2 * (r.reac.size() + r.prod.size()) + 3 + (r.reac.size() + r.prod.size());
+    c.exp64 += r.reversible ? 2 : 1;
+    if (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) { c.exp64 += 6; c.log64 += 3; c.div64 += 3; c.fp64 += 12; }
+  }
+}
+
+// mixed precision, table driven (see emit_rates_mixed for the split)
+void emit_rates_table_mixed(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts& c) {
+  emit_rate_tables(g, m, true);
+  const int ns = m.ns;
+  o("const double lnT = log(T);");
+  o("const double iT = 1.0 / T;");
+  o("const float lnTf = kx_d2f(lnT), iTf = kx_d2f(iT), Tf = kx_d2f(T);");
+  o("const float lnPf = __logf(kx_d2f(P));");
+  o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
+  o(fmt("double mu[%d]; float lC[%d], Cf[%d];%s", ns, ns, ns, rop ? "" : fmt(" double w[%d];", ns).c_str()));
+  o("double sig = 0.0;");
+  o(fmt("for (int k = 0; k < %d; ++k) sig = fma(Y_[(long long)k * ld + i], kx_riw[k], sig);", ns));
+  o("if (!(sig > 0.0 && sig < KX_INF)) KX_BAD_POINT");
+  o("const double fC = cM / sig;");
+  o("const double lnfC = kx_log(fC);");
+  o("const float cMf = kx_d2f(cM), fCf = kx_d2f(fC);");
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o("  const double Yk = Y_[(long long)k * ld + i];");
+  o("  const double lnC = fmax(kx_log(Yk) + (lnfC - kx_rlw[k]), -700.0);");
+  o("  lC[k] = kx_d2f(lnC);");
+  o("  Cf[k] = kx_d2f(Yk * kx_riw[k]) * fCf;");
+  o("  const double* a = kx_gc + 16 * k + (T < kx_tmid[k] ? 0 : 8);");
+  o("  mu[k] = lnC + fma(a[6], lnT, fma(a[5], iT, fma(fma(fma(fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0])));");
+  if (!rop) o("  w[k] = 0.0;");
+  o("}");
+  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
+  c.fp64 += ns * 12.0 + 6; c.log64 += ns + 2; c.div64 += 2;
+  o("#pragma unroll 1");
+  o(fmt("for (int r = 0; r < %d; ++r) {", m.nr()));
+  o(fmt("  const int* h = kx_ri + %d * r; const float* d = kx_rd + %d * r;", RI, RD));
+  o("  const int kind = h[0];");
+  o("  float lkf = fmaf(d[1], lnTf, fmaf(d[2], iTf, d[0]));");
+  o("  float lX = 0.0f;");
+  o("  if (kind >= 1 && kind <= 3) {");
+  o("    float X;");
+  o("    if (h[6] < 0) X = Cf[kx_eff[h[5]].k];");
+  o("    else { X = d[6] * cMf; for (int e = 0; e < h[6]; ++e) X = fmaf((float)kx_eff[h[5] + e].a, Cf[kx_eff[h[5] + e].k], X); }");
+  o("    lX = __logf(X);");
+  o("  }");
+  o("  if (kind == 2 || kind == 3) {");
+  o("    const float lk0 = fmaf(d[4], lnTf, fmaf(d[5], iTf, d[3]));");
+  o("    const float lnPr = fmaxf(lk0 - lkf + lX, -690.0f);");
+  o("    float lnF = 0.0f;");
+  o("    if (h[7] == 1) {");
+  o("      const float lFc = __log10f(d[7] * __expf(Tf * d[9]) + d[8] * __expf(Tf * d[10]) + __expf(d[11] * iTf));");
+  o("      const float xx = fmaf(lnPr, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
+  o("      const float ff = __fdividef(xx, fmaf(-1.27f, lFc, 0.75f) - 0.14f * xx);");
+  o("      lnF = __fdividef(2.30258509f * lFc, fmaf(ff, ff, 1.0f));");
+  o("    } else if (h[7] == 2) {");
+  o("      const float lPr = lnPr * 0.434294482f;");
+  o("      const float base = d[7] * __expf(d[8] * iTf) + __expf(Tf * d[9]);");
+  o("      lnF = d[10] + d[11] * lnTf + __fdividef(__logf(base), fmaf(lPr, lPr, 1.0f));");
+  o("    }");
+  o("    lkf = (kind == 2 ? lkf + kx_ln_pr_ratio(lnPr) : lk0 + kx_ln_inv_1p(lnPr)) + lnF;");
+  o("    lX = 0.0f;");
+  o("  } else if (kind == 4) {");
+  o("    const double* t = kx_plog + 4 * h[8]; const int np = h[9]; const double lnP = (double)lnPf;");
+  o("    double l;");
+  o("    if (lnP <= t[0]) l = fma(t[2], lnT, fma(t[3], iT, t[1]));");
+  o("    else if (lnP >= t[4 * (np - 1)]) { const double* u = t + 4 * (np - 1); l = fma(u[2], lnT, fma(u[3], iT, u[1])); }");
+  o("    else { int j = 0; while (!(lnP < t[4 * (j + 1)])) ++j; const double* u = t + 4 * j;");
+  o("      const double l1 = fma(u[2], lnT, fma(u[3], iT, u[1])), l2 = fma(u[6], lnT, fma(u[7], iT, u[5]));");
+  o("      l = fma(l2 - l1, (lnP - u[0]) / (u[4] - u[0]), l1); }");
+  o("    lkf = kx_d2f(l);");
+  o("  }");
+  o("  const int nre = h[2], npr = h[3];");
+  o("  float lnRf = lkf + lX;");
+  o("  for (int j = 0; j < nre; ++j) lnRf = fmaf((float)h[18 + j], lC[h[12 + j]], lnRf);");
+  o("  double q;");
+  o("  if (h[1]) {");
+  o("    double s = (double)(-h[4]) * lnPRT;");
+  o("    for (int j = 0; j < nre + npr; ++j) { const double nu = (j < nre ? -1.0 : 1.0) * h[18 + j]; s = fma(nu, mu[h[12 + j]], s); }");
+  o("    q = kx_net_rate(lnRf, s);");
+  o("  } else {");
+  o("    q = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+  o("  }");
+  if (rop) o("  out_[(long long)r * ld + i] = q;");
+  else o("  for (int j = 0; j < nre + npr; ++j) { const double nu = (j < nre ? -1.0 : 1.0) * h[18 + j]; w[h[12 + j]] = fma(nu, q, w[h[12 + j]]); }");
+  o("}");
+  if (!rop) o(fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = w[k];", ns));
+  for (const Reaction& r : m.rx) {
+    c.fp64 += 1 + 2 * (r.reac.size() + r.prod.size());
+    c.fp32 += 4 + r.reac.size();
+    c.exp32 += 2;
+    if (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) { c.exp32 += 5; c.log32 += 3; c.fp32 += 14; }
+  }
+}
+
 // ------------------------------------------------------------------ adjoint
 // Vector-Jacobian product of the production rates at fixed p.  With
 // a_i = sum_k nu_ki v_k, v^T wdot = sum_i a_i q_i, so each reaction adds
@@ -1292,7 +1537,10 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       const bool rop = kind == KernelKind::Rop;
       outs = "double* __restrict__ out_";
       nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);
-      if (opt.mixed) emit_rates_mixed(body, m, rop, c);
+      const bool table = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
+      if (table && opt.mixed) emit_rates_table_mixed(body, globals, m, rop, c);
+      else if (table) emit_rates_table64(body, globals, m, rop, c);
+      else if (opt.mixed) emit_rates_mixed(body, m, rop, c);
       else emit_rates64(body, m, opt, rop, c);
       break;
     }

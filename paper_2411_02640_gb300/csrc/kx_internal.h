@@ -68,6 +68,7 @@ struct EmitOptions {
   int block = 128;
   int part = 0;             // transport: 0 all outputs, 1 viscosity and conductivity, 2 diffusion
   int maxrreg = 0;          // register cap per thread (0: compiler choice)
+  int rates_mode = 0;       // 0 auto, 1 unrolled, 2 table driven (large mechanisms)
 };
 
 // Operation counts per point, tallied while emitting (library calls such as

@@ -1,0 +1,248 @@
+"""Continuous-batching server for production-rate / transport requests.
+
+CFD ranks (threads or processes of the host code) submit batches of
+thermochemical states of any size for any of several device-resident
+mechanisms.  A scheduler thread
+
+  * admits pending requests as stream slots and device memory free up
+    (admission is capped by a device-memory budget in bytes);
+  * coalesces the admitted requests that share (mechanism, precision,
+    transport) into one launch over their concatenated states -- the
+    kernels are grid-stride loops sized to the resident capacity of the
+    GPU, so a coalesced batch is one persistent launch;
+  * runs each batch on one of several CUDA streams (copy in, kernels, copy
+    out), so batches of different mechanisms overlap on the device while
+    new requests keep arriving;
+  * completes a request's Future when its batch's event has fired, and
+    records its latency (submit to completion).
+
+Every state's computation is independent of the others in its batch and
+runs the same instruction sequence wherever it lands, so a request's
+result is bit-identical alone and in the mix.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from .kx import Mechanism
+
+
+@dataclass
+class Request:
+    mech: str
+    T: np.ndarray
+    p: np.ndarray
+    Y: np.ndarray                 # [N_s, n]
+    precision: str
+    transport: bool
+    future: cf.Future
+    t_submit: float = 0.0
+    t_done: float = 0.0
+
+    @property
+    def n(self) -> int:
+        return int(self.T.shape[0])
+
+
+@dataclass
+class Result:
+    wdot: np.ndarray
+    mu: Optional[np.ndarray] = None
+    lam: Optional[np.ndarray] = None
+    Dk: Optional[np.ndarray] = None
+    latency_s: float = 0.0
+
+
+@dataclass
+class _Batch:
+    key: tuple
+    reqs: List[Request]
+    stream: object
+    event: object
+    nbytes: int
+    outs: Dict[str, object] = field(default_factory=dict)
+    offsets: List[int] = field(default_factory=list)
+
+
+class Server:
+    """``Server({"name": Mechanism, ...}, hbm_budget=bytes, streams=4,
+    coalesce=True, max_batch_points=2**22)``; ``submit`` returns a
+    Future[Result].  With ``coalesce=False`` and ``streams=1`` it serves one
+    request at a time (the baseline the batching is compared with)."""
+
+    def __init__(self, mechanisms: Dict[str, Mechanism], hbm_budget: int = 16 << 30, streams: int = 4,
+                 coalesce: bool = True, max_batch_points: int = 1 << 22, device: int = 0):
+        import torch
+        self.torch = torch
+        self.mechs = mechanisms
+        self.budget = int(hbm_budget)
+        self.used = 0
+        self.coalesce = coalesce
+        self.max_batch = int(max_batch_points)
+        self.device = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.free_streams = collections.deque(self.streams)
+        self.pending: "collections.OrderedDict[tuple, collections.deque]" = collections.OrderedDict()
+        self.inflight: List[_Batch] = []
+        self.lock = threading.Condition()
+        self.running = False
+        self.thread: Optional[threading.Thread] = None
+        self.latencies: List[float] = []
+        self.points_done = 0
+        self.launches = 0
+
+    # ---------------------------------------------------------------- API
+    def bytes_per_point(self, name: str, transport: bool) -> int:
+        ns = self.mechs[name].n_species
+        return 8 * ((2 + ns) + ns + ((2 + ns) if transport else 0))
+
+    def submit(self, name: str, T, p, Y, precision: str = "mixed", transport: bool = False) -> cf.Future:
+        if name not in self.mechs:
+            raise KeyError(name)
+        fut: cf.Future = cf.Future()
+        req = Request(name, np.ascontiguousarray(T, np.float64), np.ascontiguousarray(p, np.float64),
+                      np.ascontiguousarray(Y, np.float64), precision, bool(transport), fut, time.perf_counter())
+        if req.n * self.bytes_per_point(name, transport) > self.budget:
+            fut.set_exception(MemoryError(f"request of {req.n} states exceeds the device-memory budget"))
+            return fut
+        with self.lock:
+            self.pending.setdefault((name, precision, bool(transport)), collections.deque()).append(req)
+            self.lock.notify()
+        return fut
+
+    def start(self) -> "Server":
+        self.running = True
+        self.thread = threading.Thread(target=self._loop, name="kx-serve", daemon=True)
+        self.thread.start()
+        return self
+
+    def stop(self, timeout: float = 60.0) -> None:
+        with self.lock:
+            self.running = False
+            self.lock.notify()
+        if self.thread:
+            self.thread.join(timeout)
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *a):
+        self.stop()
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return {"requests": len(self.latencies), "points": self.points_done, "launches": self.launches,
+                "p50_ms": float(np.quantile(lat, 0.5) * 1e3), "p99_ms": float(np.quantile(lat, 0.99) * 1e3)}
+
+    # ---------------------------------------------------------------- scheduler
+    def _loop(self) -> None:
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self.lock:
+                if not self.running and not self.inflight and not any(self.pending.values()):
+                    return
+                idle = not self._launch_ready()
+            self._complete()
+            if idle:
+                with self.lock:
+                    if self.running and not any(self.pending.values()):
+                        self.lock.wait(timeout=0.002 if self.inflight else 0.05)
+                if self.inflight:
+                    time.sleep(0.0002)
+
+    def _launch_ready(self) -> bool:
+        """Admit and launch as many batches as streams and memory allow
+        (lock held).  Oldest pending request first."""
+        launched = False
+        while self.free_streams:
+            key = self._oldest_key()
+            if key is None:
+                break
+            q = self.pending[key]
+            bpp = self.bytes_per_point(key[0], key[2])
+            reqs, pts = [], 0
+            while q and (not reqs or self.coalesce):
+                r = q[0]
+                if reqs and pts + r.n > self.max_batch:
+                    break
+                if self.used + (pts + r.n) * bpp > self.budget:
+                    break
+                reqs.append(q.popleft())
+                pts += r.n
+            if not reqs:
+                break                       # the oldest request waits for memory
+            self._launch(key, reqs, pts * bpp)
+            launched = True
+        return launched
+
+    def _oldest_key(self):
+        best, t = None, None
+        for k, q in self.pending.items():
+            if q and (t is None or q[0].t_submit < t):
+                best, t = k, q[0].t_submit
+        return best
+
+    def _launch(self, key, reqs: List[Request], nbytes: int) -> None:
+        torch = self.torch
+        name, prec, transport = key
+        mech = self.mechs[name]
+        ns = mech.n_species
+        stream = self.free_streams.popleft()
+        self.used += nbytes
+        n = sum(r.n for r in reqs)
+        with torch.cuda.stream(stream):
+            T = torch.empty(n, dtype=torch.float64, device=self.device)
+            p = torch.empty_like(T)
+            Y = torch.empty((ns, n), dtype=torch.float64, device=self.device)
+            offs, o = [], 0
+            for r in reqs:
+                offs.append(o)
+                T[o:o + r.n].copy_(torch.from_numpy(r.T), non_blocking=True)
+                p[o:o + r.n].copy_(torch.from_numpy(r.p), non_blocking=True)
+                Y[:, o:o + r.n].copy_(torch.from_numpy(r.Y), non_blocking=True)
+                o += r.n
+            w = mech.production_rates(T, p, Y, precision=prec, stream=stream)
+            outs = {"wdot": w.to("cpu", non_blocking=True)}
+            if transport:
+                mu, lam, D = mech.transport(T, p, Y, precision=prec, stream=stream)
+                outs.update(mu=mu.to("cpu", non_blocking=True), lam=lam.to("cpu", non_blocking=True),
+                            Dk=D.to("cpu", non_blocking=True))
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.launches += 1
+        self.inflight.append(_Batch(key, reqs, stream, ev, nbytes, outs, offs))
+
+    def _complete(self) -> None:
+        done = []
+        with self.lock:
+            for b in self.inflight:
+                if b.event.query():
+                    done.append(b)
+            for b in done:
+                self.inflight.remove(b)
+                self.used -= b.nbytes
+                self.free_streams.append(b.stream)
+            if done:
+                self.lock.notify()
+        now = time.perf_counter()
+        for b in done:
+            for r, o in zip(b.reqs, b.offsets):
+                w = b.outs["wdot"][:, o:o + r.n].numpy()
+                res = Result(wdot=w)
+                if r.transport:
+                    res.mu = b.outs["mu"][o:o + r.n].numpy()
+                    res.lam = b.outs["lam"][o:o + r.n].numpy()
+                    res.Dk = b.outs["Dk"][:, o:o + r.n].numpy()
+                r.t_done = now
+                res.latency_s = now - r.t_submit
+                self.latencies.append(res.latency_s)
+                self.points_done += r.n
+                r.future.set_result(res)

@@ -1,0 +1,88 @@
+"""The continuous-batching server: results identical alone and in the mix,
+admission under a device-memory budget, rejection of oversize requests,
+and agreement with direct library calls."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2411_02640_gb300 import synth
+from tests.gpu_common import mechanism, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+MECHS = ["h2o2_9_21", "gri_53_325"]
+
+
+def _req(name, n, start, seed):
+    m = synth.mechanism(name)
+    return synth.make_states(m.n_species, synth.STATE_SPECS[name], start, n)
+
+
+@pytest.fixture(scope="module")
+def server_parts():
+    torch_cuda()
+    return {name: mechanism(name) for name in MECHS}
+
+
+def _workload(seed=0, count=24):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        name = MECHS[i % 2]
+        n = int(np.exp(rng.uniform(np.log(1000), np.log(60000))))
+        out.append((name, _req(name, n, int(rng.integers(0, 1 << 20)), i), "mixed" if rng.random() < 0.7 else "fp64",
+                    bool(rng.random() < 0.3)))
+    return out
+
+
+def test_result_identical_alone_and_in_the_mix(server_parts):
+    from paper_2411_02640_gb300.serve import Server
+    work = _workload()
+    # in the mix: submitted together from several "CFD rank" threads
+    with Server(server_parts, hbm_budget=2 << 30, streams=4) as srv:
+        futs = [None] * len(work)
+
+        def rank(idx):
+            for i in idx:
+                name, (T, p, Y), prec, tr = work[i]
+                futs[i] = srv.submit(name, T, p, Y, precision=prec, transport=tr)
+
+        th = [threading.Thread(target=rank, args=(range(r, len(work), 3),)) for r in range(3)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        mixed = [f.result(timeout=300) for f in futs]
+        st = srv.stats()
+    assert st["requests"] == len(work)
+    assert st["launches"] < len(work)          # some requests were coalesced
+    # alone: one request at a time, no coalescing
+    with Server(server_parts, hbm_budget=2 << 30, streams=1, coalesce=False) as srv:
+        alone = [srv.submit(name, T, p, Y, precision=prec, transport=tr).result(timeout=300)
+                 for name, (T, p, Y), prec, tr in work]
+    for a, b, (name, _, prec, tr) in zip(mixed, alone, work):
+        assert np.array_equal(a.wdot, b.wdot, equal_nan=True), name
+        if tr:
+            assert np.array_equal(a.mu, b.mu) and np.array_equal(a.lam, b.lam) and np.array_equal(a.Dk, b.Dk)
+
+
+def test_agrees_with_direct_calls_and_budget(server_parts):
+    import torch
+    from paper_2411_02640_gb300.serve import Server
+    name = "gri_53_325"
+    mech = server_parts[name]
+    T, p, Y = _req(name, 5000, 123, 0)
+    bpp = 8 * (2 + 53 + 53 + 2 + 53)
+    # a budget that admits one request at a time: everything still completes
+    with Server(server_parts, hbm_budget=int(6000 * bpp), streams=4) as srv:
+        futs = [srv.submit(name, T, p, Y, precision="fp64", transport=True) for _ in range(5)]
+        res = [f.result(timeout=300) for f in futs]
+        big = srv.submit(name, np.ones(100000), np.ones(100000), np.ones((53, 100000)), transport=True)
+        with pytest.raises(MemoryError):
+            big.result(timeout=10)
+    Td, pd, Yd = (torch.tensor(a, device="cuda") for a in (T, p, Y))
+    w = mech.production_rates(Td, pd, Yd).cpu().numpy()
+    mu, lam, D = (t.cpu().numpy() for t in mech.transport(Td, pd, Yd))
+    for r in res:
+        assert np.array_equal(r.wdot, w) and np.array_equal(r.mu, mu) and np.array_equal(r.Dk, D)
