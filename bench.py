@@ -343,7 +343,7 @@ def serve_pools(points: int):
     for name in SERVE_MECHS:
         m = synth.mechanism(name)
         T, p, Y = synth.make_states(m.n_species, synth.STATE_SPECS[name], 0, points)
-        pools[name] = tuple(np.concatenate([a, a], axis=-1) for a in (T, p, Y))
+        pools[name] = tuple(torch.from_numpy(np.concatenate([a, a], axis=-1)).pin_memory() for a in (T, p, Y))
     return pools
 
 
@@ -391,7 +391,7 @@ def run_serve_suite(args, sweep=True):
     budget = 48 << 30
     # warm every kernel once
     for name, m in mechs.items():
-        T, p, Y = (torch.from_numpy(a[..., :4096].copy()).cuda() for a in pools[name])
+        T, p, Y = (a[..., :4096].contiguous().cuda() for a in pools[name])
         for prec in ("fp64", "mixed"):
             m.production_rates(T, p, Y, precision=prec)
             m.transport(T, p, Y, precision=prec)

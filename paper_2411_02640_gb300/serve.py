@@ -37,9 +37,9 @@ from .kx import Mechanism
 @dataclass
 class Request:
     mech: str
-    T: np.ndarray
-    p: np.ndarray
-    Y: np.ndarray                 # [N_s, n]
+    T: object                     # float64 host tensors: T[n], p[n], Y[N_s, n]
+    p: object
+    Y: object
     precision: str
     transport: bool
     future: cf.Future
@@ -107,8 +107,17 @@ class Server:
         if name not in self.mechs:
             raise KeyError(name)
         fut: cf.Future = cf.Future()
-        req = Request(name, np.ascontiguousarray(T, np.float64), np.ascontiguousarray(p, np.float64),
-                      np.ascontiguousarray(Y, np.float64), precision, bool(transport), fut, time.perf_counter())
+        torch = self.torch
+
+        def host(a):
+            # numpy arrays (any row stride) or CPU tensors; pinned memory makes the copies asynchronous
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.asarray(a, np.float64))
+            if t.dtype != torch.float64 or t.is_cuda:
+                raise TypeError("requests carry float64 host arrays")
+            return t
+        req = Request(name, host(T), host(p), host(Y), precision, bool(transport), fut, time.perf_counter())
+        if req.Y.dim() != 2 or req.Y.shape[0] != self.mechs[name].n_species or req.Y.shape[1] != req.n:
+            raise ValueError("Y must be [N_s, n]")
         if req.n * self.bytes_per_point(name, transport) > self.budget:
             fut.set_exception(MemoryError(f"request of {req.n} states exceeds the device-memory budget"))
             return fut
@@ -205,16 +214,21 @@ class Server:
             offs, o = [], 0
             for r in reqs:
                 offs.append(o)
-                T[o:o + r.n].copy_(torch.from_numpy(r.T), non_blocking=True)
-                p[o:o + r.n].copy_(torch.from_numpy(r.p), non_blocking=True)
-                Y[:, o:o + r.n].copy_(torch.from_numpy(r.Y), non_blocking=True)
+                T[o:o + r.n].copy_(r.T, non_blocking=True)
+                p[o:o + r.n].copy_(r.p, non_blocking=True)
+                for k in range(ns):                 # one contiguous row per species on both sides
+                    Y[k, o:o + r.n].copy_(r.Y[k], non_blocking=True)
                 o += r.n
             w = mech.production_rates(T, p, Y, precision=prec, stream=stream)
-            outs = {"wdot": w.to("cpu", non_blocking=True)}
+
+            def down(t):
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t, non_blocking=True)
+                return h
+            outs = {"wdot": down(w)}
             if transport:
                 mu, lam, D = mech.transport(T, p, Y, precision=prec, stream=stream)
-                outs.update(mu=mu.to("cpu", non_blocking=True), lam=lam.to("cpu", non_blocking=True),
-                            Dk=D.to("cpu", non_blocking=True))
+                outs.update(mu=down(mu), lam=down(lam), Dk=down(D))
             ev = torch.cuda.Event()
             ev.record(stream)
         self.launches += 1

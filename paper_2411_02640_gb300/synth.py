@@ -616,3 +616,29 @@ def mechanism_file(name: str, directory: str) -> str:
         write_mechanism(mechanism(name), tmp)
         os.replace(tmp, path)
     return path
+
+
+def make_states_torch(ns: int, spec: StateSpec, count: int, seed: int, device="cuda"):
+    """A large batch of states drawn directly in device memory with torch's
+    seeded generator (same distributions as make_states; a different
+    stream of numbers).  For full-size runs whose states the CPU could not
+    draw in reasonable time; a sample of them can be copied back for the
+    oracle."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    T = torch.empty(count, dtype=torch.float64, device=device).uniform_(spec.T_range[0], spec.T_range[1], generator=g)
+    a0, a1 = spec.p_atm_range
+    if a0 == a1:
+        p = torch.full((count,), a0 * P_ATM, dtype=torch.float64, device=device)
+    else:
+        u = torch.empty(count, dtype=torch.float64, device=device).uniform_(math.log(a0), math.log(a1), generator=g)
+        p = P_ATM * torch.exp(u)
+    Y = torch.empty((ns, count), dtype=torch.float64, device=device)
+    chunk = 1 << 20
+    for s0 in range(0, count, chunk):
+        c = min(chunk, count - s0)
+        alpha = torch.full((ns, c), spec.alpha, dtype=torch.float64, device=device)
+        G = torch._standard_gamma(alpha, generator=g)
+        Y[:, s0:s0 + c] = G / G.sum(dim=0, keepdim=True)
+    return T, p, Y
