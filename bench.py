@@ -287,6 +287,7 @@ def run_kx(args):
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         achieved = f64 * n / (per[dom] * 1e-3) / 1e9
         peak = fp64_peak_gops(sm_max)
+        traffic = profiled_traffic(mech, names[dom], n)
         mnames = kernels["mixed"]
         mdom = int(np.argmax(mper))
         m64 = ops_per_point(mech, mnames[mdom])
@@ -307,7 +308,8 @@ def run_kx(args):
                                    "achieved": m64 * n / (mper[mdom] * 1e-3) / 1e9, "peak": peak,
                                    "unit": "G fp64 instr/s", "frac": m64 * n / (mper[mdom] * 1e-3) / 1e9 / peak}},
             "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                         "unit": "G fp64 instr/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "G fp64 instr/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes": 8 * (2 + ns + ns) * n,
                          "per_point_fp64_instr": f64,
                          "peak_source": f"152 SMs x 2 DFMA/clk x {sm_max:.0f} MHz (float64 pipe; unit counts and "
                                         "max SM clock)"},
@@ -402,6 +404,19 @@ def run_serve_suite(args, sweep=True):
         out["batching"].append(serve_run(mechs, pools, r, args.serve_requests, 105, True, 4, budget))
         out["one_at_a_time"].append(serve_run(mechs, pools, r, args.serve_requests, 105, False, 1, budget))
     return out
+
+
+def profiled_traffic(mech, name, n):
+    """DRAM bytes of one launch from the committed ncu capture of this exact
+    kernel (matched by the hash of its emitted source), scaled to n states;
+    None when no capture of the current kernel exists."""
+    import glob
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"traffic_{name}_*.json")):
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("mechanism") == MECH and d.get("source_hash") == mech.source_hash(name):
+            return d["bytes_per_state"] * n
+    return None
 
 
 def ops_per_point(mech, name):

@@ -149,6 +149,18 @@ kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* l
  * float32 divisions.  counts must hold 8 doubles. */
 kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts);
 
+/* 64-bit FNV-1a hash of a kernel's emitted source: identifies the exact
+ * kernel that a profile was taken of. */
+kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash);
+
+/* Copy `rows` rows of n float64 values between host (pinned or pageable)
+ * and device buffers with leading dimensions dst_ld and src_ld (in
+ * elements), asynchronously on `stream`, in one call: staging of strided
+ * state arrays for the serving loop.  The paper has no counterpart; it is
+ * host plumbing around the method. */
+kx_status kx_copy_rows_async(void* dst, int64_t dst_ld, const void* src, int64_t src_ld, int64_t rows, int64_t n,
+                             void* stream);
+
 const char* kx_status_string(kx_status s);
 
 /* Message of the calling thread's last failed call (empty if none). */

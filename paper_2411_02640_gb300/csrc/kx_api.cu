@@ -478,4 +478,23 @@ kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts) {
   return KX_OK;
 }
 
+kx_status kx_copy_rows_async(void* dst, int64_t dst_ld, const void* src, int64_t src_ld, int64_t rows, int64_t n,
+                             void* stream) {
+  if (rows < 0 || n < 0 || dst_ld < n || src_ld < n) return fail(KX_ERR_ARG, "bad row copy shape");
+  if (rows == 0 || n == 0) return KX_OK;
+  if (!dst || !src) return fail(KX_ERR_ARG, "null pointer");
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)dst_ld * sizeof(double), src, (size_t)src_ld * sizeof(double),
+                                    (size_t)n * sizeof(double), (size_t)rows, cudaMemcpyDefault, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+  return KX_OK;
+}
+
+kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash) {
+  if (!h || !kernel || !hash) return fail(KX_ERR_ARG, "null argument");
+  kx_status s = kx_kernel_info(h, kernel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (s != KX_OK) return s;
+  *hash = fnv1a(find_kernel(h, kernel)->source);
+  return KX_OK;
+}
+
 }  // extern "C"

@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.kx_kernel_op_counts.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
+        L.kx_kernel_source_hash.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64)]
+        L.kx_copy_rows_async.argtypes = [vp, i64, vp, i64, i64, i64, vp]
         L.kx_status_string.argtypes = [ctypes.c_int]
         L.kx_status_string.restype = ctypes.c_char_p
         L.kx_last_error.restype = ctypes.c_char_p
@@ -205,6 +207,11 @@ class Mechanism:
                                              _stream(stream)))
         return gT, gY
 
+    def source_hash(self, name: str) -> str:
+        h = ctypes.c_uint64()
+        _check(lib().kx_kernel_source_hash(self.h, name.encode(), ctypes.byref(h)))
+        return f"{h.value:016x}"
+
     def op_counts(self, name: str) -> dict:
         """Per-point operation counts the emitter tallied for one kernel."""
         c = (ctypes.c_double * 8)()
@@ -218,3 +225,12 @@ class Mechanism:
                                     ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(ex)))
         return dict(registers=r.value, spill_bytes=lb.value, compile_seconds=cs.value, fp64_ops=f64.value,
                     fp32_ops=f32.value, exps=ex.value)
+
+
+def copy_rows(dst, src, stream=None) -> None:
+    """dst[:, :] = src[:, :] for float64 2-D tensors with unit column stride
+    (host or device, any row stride), one asynchronous 2-D copy."""
+    rows, n = src.shape
+    assert dst.shape[0] == rows and dst.shape[1] == n and src.stride(1) == 1 and dst.stride(1) == 1
+    _check(lib().kx_copy_rows_async(dst.data_ptr(), dst.stride(0), src.data_ptr(), src.stride(0), rows, n,
+                                    _stream(stream)))

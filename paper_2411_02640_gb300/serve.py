@@ -31,7 +31,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .kx import Mechanism
+from .kx import Mechanism, copy_rows
 
 
 @dataclass
@@ -114,6 +114,8 @@ class Server:
             t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.asarray(a, np.float64))
             if t.dtype != torch.float64 or t.is_cuda:
                 raise TypeError("requests carry float64 host arrays")
+            if t.dim() == 2 and t.stride(1) != 1:
+                t = t.contiguous()
             return t
         req = Request(name, host(T), host(p), host(Y), precision, bool(transport), fut, time.perf_counter())
         if req.Y.dim() != 2 or req.Y.shape[0] != self.mechs[name].n_species or req.Y.shape[1] != req.n:
@@ -216,8 +218,7 @@ class Server:
                 offs.append(o)
                 T[o:o + r.n].copy_(r.T, non_blocking=True)
                 p[o:o + r.n].copy_(r.p, non_blocking=True)
-                for k in range(ns):                 # one contiguous row per species on both sides
-                    Y[k, o:o + r.n].copy_(r.Y[k], non_blocking=True)
+                copy_rows(Y[:, o:o + r.n], r.Y, stream=stream)   # one 2-D copy of the species rows
                 o += r.n
             w = mech.production_rates(T, p, Y, precision=prec, stream=stream)
 
