@@ -1576,7 +1576,14 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
   // a register cap is expressed as a minimum number of resident blocks (ptxas
   // ignores --maxrregcount for kernels that carry launch bounds)
-  const int min_blocks = opt.maxrreg > 0 ? std::max(1, 65536 / (opt.maxrreg * opt.block)) : 0;
+  // the unrolled float64 rate kernels run best at 128 registers (four blocks of 128 per SM):
+  // the extra warps hide the latency of the exp tables and dependent float64 chains better
+  // than the spills they cost (measured on the 53/325 mechanism)
+  int rreg = opt.maxrreg;
+  const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed &&
+                              !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
+  if (rreg == 0 && unrolled_rates) rreg = 128;
+  const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;
   s << ") " << entry

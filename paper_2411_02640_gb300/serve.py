@@ -34,7 +34,7 @@ import numpy as np
 from .kx import Mechanism, copy_rows
 
 
-@dataclass
+@dataclass(eq=False)
 class Request:
     mech: str
     T: object                     # float64 host tensors: T[n], p[n], Y[N_s, n]
@@ -60,7 +60,7 @@ class Result:
     latency_s: float = 0.0
 
 
-@dataclass
+@dataclass(eq=False)
 class _Batch:
     key: tuple
     reqs: List[Request]
@@ -241,8 +241,10 @@ class Server:
             for b in self.inflight:
                 if b.event.query():
                     done.append(b)
+            if done:
+                ids = {id(b) for b in done}
+                self.inflight = [b for b in self.inflight if id(b) not in ids]
             for b in done:
-                self.inflight.remove(b)
                 self.used -= b.nbytes
                 self.free_streams.append(b.stream)
             if done:
