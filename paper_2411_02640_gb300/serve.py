@@ -97,6 +97,7 @@ class Server:
         self.latencies: List[float] = []
         self.points_done = 0
         self.launches = 0
+        self.error: Optional[BaseException] = None
 
     # ---------------------------------------------------------------- API
     def bytes_per_point(self, name: str, transport: bool) -> int:
@@ -106,6 +107,8 @@ class Server:
     def submit(self, name: str, T, p, Y, precision: str = "mixed", transport: bool = False) -> cf.Future:
         if name not in self.mechs:
             raise KeyError(name)
+        if self.error is not None:
+            raise RuntimeError(f"serving loop failed: {self.error!r}")
         fut: cf.Future = cf.Future()
         torch = self.torch
 
@@ -154,6 +157,20 @@ class Server:
 
     # ---------------------------------------------------------------- scheduler
     def _loop(self) -> None:
+        try:
+            self._run()
+        except BaseException as exc:            # fail every waiting request instead of hanging it
+            with self.lock:
+                self.running = False
+                waiting = [r for q in self.pending.values() for r in q] + [r for b in self.inflight for r in b.reqs]
+                self.pending.clear()
+                self.inflight = []
+            for r in waiting:
+                if not r.future.done():
+                    r.future.set_exception(RuntimeError(f"serving loop failed: {exc!r}"))
+            self.error = exc
+
+    def _run(self) -> None:
         torch = self.torch
         torch.cuda.set_device(self.device)
         while True:

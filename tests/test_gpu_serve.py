@@ -86,3 +86,23 @@ def test_agrees_with_direct_calls_and_budget(server_parts):
     mu, lam, D = (t.cpu().numpy() for t in mech.transport(Td, pd, Yd))
     for r in res:
         assert np.array_equal(r.wdot, w) and np.array_equal(r.mu, mu) and np.array_equal(r.Dk, D)
+
+
+def test_failure_in_the_loop_fails_the_waiting_requests(server_parts, monkeypatch):
+    """A fault injected on the host (a launch that raises) fails every
+    waiting request with an error instead of leaving it hanging."""
+    from paper_2411_02640_gb300.serve import Server
+    srv = Server(server_parts, hbm_budget=1 << 30, streams=2)
+
+    def boom(*a, **k):
+        raise RuntimeError("injected launch failure")
+    monkeypatch.setattr(srv, "_launch", boom)
+    srv.start()
+    T, p, Y = _req("h2o2_9_21", 2000, 0, 0)
+    futs = [srv.submit("h2o2_9_21", T, p, Y) for _ in range(3)]
+    for f in futs:
+        with pytest.raises(RuntimeError, match="injected"):
+            f.result(timeout=30)
+    with pytest.raises(RuntimeError):
+        srv.submit("h2o2_9_21", T, p, Y)
+    srv.stop()
