@@ -97,9 +97,9 @@ def test_failure_in_the_loop_fails_the_waiting_requests(server_parts, monkeypatc
     def boom(*a, **k):
         raise RuntimeError("injected launch failure")
     monkeypatch.setattr(srv, "_launch", boom)
-    srv.start()
     T, p, Y = _req("h2o2_9_21", 2000, 0, 0)
-    futs = [srv.submit("h2o2_9_21", T, p, Y) for _ in range(3)]
+    futs = [srv.submit("h2o2_9_21", T, p, Y) for _ in range(3)]     # queued before the loop starts
+    srv.start()
     for f in futs:
         with pytest.raises(RuntimeError, match="injected"):
             f.result(timeout=30)
