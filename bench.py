@@ -105,11 +105,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def shard(rank: int, n: int):
+    """The states of one rank under weak scaling: its own contiguous range
+    [rank * n, (rank + 1) * n) of the seeded state stream."""
+    return rank * n, n
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time: one all-reduce (max) of a scalar."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def make_inputs(rank: int, n: int):
     from paper_2411_02640_gb300 import synth
     m = synth.mechanism(MECH)
-    # each rank draws its own shard of the seeded state stream
-    return synth.make_states(m.n_species, synth.STATE_SPECS[MECH], rank * n, n)
+    start, count = shard(rank, n)
+    return synth.make_states(m.n_species, synth.STATE_SPECS[MECH], start, count)
 
 
 def cpu_baseline(seconds_target: float = 15.0):
@@ -239,10 +253,9 @@ def run_kx(args):
     with ClockSampler(local) as clk:
         for prec in ("fp64", "mixed"):
             total, per = timed(prec, args.steps, args.warmup)
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
             if world > 1:
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            results[prec] = (t.item(), per)
+                total = max_over_ranks(total, dist, dev)
+            results[prec] = (total, per)
     clocks = clk.summary()
 
     # end to end through the public API from pinned host buffers
@@ -267,10 +280,10 @@ def run_kx(args):
         e2e_step()
     e1.record(stream)
     barrier()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    e2e_total = e0.elapsed_time(e1)
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = t.item() / args.steps
+        e2e_total = max_over_ranks(e2e_total, dist, dev)
+    e2e_ms = e2e_total / args.steps
 
     if rank == 0:
         pk = peaks()

@@ -207,7 +207,13 @@ class Server:
                 pts += r.n
             if not reqs:
                 break                       # the oldest request waits for memory
-            self._launch(key, reqs, pts * bpp)
+            try:
+                self._launch(key, reqs, pts * bpp)
+            except BaseException as exc:
+                for r in reqs:              # taken off the queue: fail them here
+                    if not r.future.done():
+                        r.future.set_exception(RuntimeError(f"serving loop failed: {exc!r}"))
+                raise
             launched = True
         return launched
 

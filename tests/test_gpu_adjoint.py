@@ -76,3 +76,59 @@ def test_jacobian_assembly_matches_oracle(torch):
         Jr = o.jacobian(T[i], p[i], Y[:, i])
         sc = np.abs(Jr).max(axis=1, keepdims=True)
         assert np.all(np.abs(J[i] - Jr) <= 1e-9 * sc + 1e-300)
+
+
+def test_adjoint_throughput_and_jacobian_assembly_timing(torch):
+    """The 53/325 adjoint at 2^18 states (random N(0,1) cotangents) and the
+    dense Jacobian assembled from 54 adjoint calls against a central
+    finite-difference Jacobian (108 production-rate calls) on 2^14 states;
+    prints one JSON line ("adjoint_timing: {...}")."""
+    import json
+    from paper_2411_02640_gb300.autograd import jacobian
+    name = "gri_53_325"
+    mech = mechanism(name)
+    m = synth.mechanism(name)
+    ns = mech.n_species
+    T, p, Y = synth.make_states_torch(ns, synth.STATE_SPECS[name], 1 << 18, seed=104)
+    v = torch.randn((ns, 1 << 18), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    gT, gY = mech.production_rates_vjp(T, p, Y, v)
+    w = mech.production_rates(T, p, Y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    for _ in range(5):
+        mech.production_rates_vjp(T, p, Y, v, out=(gT, gY))
+    ev[1].record()
+    for _ in range(5):
+        mech.production_rates(T, p, Y, out=w)
+    ev[2].record()
+    torch.cuda.synchronize()
+    vjp_ms, fwd_ms = ev[0].elapsed_time(ev[1]) / 5, ev[1].elapsed_time(ev[2]) / 5
+    nj = 1 << 14
+    Tj, pj, Yj = T[:nj].contiguous(), p[:nj].contiguous(), Y[:, :nj].contiguous()
+    J = jacobian(mech, Tj, pj, Yj)
+    torch.cuda.synchronize()
+    ev[0].record()
+    J = jacobian(mech, Tj, pj, Yj)
+    ev[1].record()
+    # central differences, h = 1e-6 relative, one column per input
+    Jfd = torch.empty_like(J)
+    h = 1e-6 * Tj
+    Jfd[:, :, 0] = ((mech.production_rates(Tj + h, pj, Yj) - mech.production_rates(Tj - h, pj, Yj)) / (2 * h)).t()
+    for j in range(ns):
+        hy = 1e-6 * torch.clamp(Yj[j], min=1e-3)
+        Yp, Ym = Yj.clone(), Yj.clone()
+        Yp[j] += hy
+        Ym[j] -= hy
+        Jfd[:, :, 1 + j] = ((mech.production_rates(Tj, pj, Yp) - mech.production_rates(Tj, pj, Ym)) / (2 * hy)).t()
+    ev[2].record()
+    torch.cuda.synchronize()
+    jac_ms, fd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    # the two Jacobians agree to the finite-difference truncation level, row-scaled
+    sc = J.abs().amax(dim=2, keepdim=True) + 1e-300
+    agree = ((J - Jfd).abs() / sc).quantile(0.99).item()
+    stats = {"states_vjp": 1 << 18, "vjp_ms": vjp_ms, "vjp_mpoints_s": (1 << 18) / vjp_ms / 1e3,
+             "forward_ms": fwd_ms, "states_jacobian": nj, "jacobian_54_vjp_ms": jac_ms, "fd_jacobian_108_fwd_ms": fd_ms,
+             "fd_vs_adjoint_p99_row_scaled": agree}
+    print("\nadjoint_timing: " + json.dumps(stats))
+    assert agree < 1e-3
