@@ -1433,14 +1433,26 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
   o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
-  o(fmt("  %s s0 = %s, s1 = %s, s2 = %s;", md.ty, ZERO.c_str(), ZERO.c_str(), ZERO.c_str()));
+  // two partial sums per product (even and odd j): six independent accumulation chains
+  o(fmt("  %s s0 = %s, s1 = %s, s2 = %s, t0 = %s, t1 = %s, t2 = %s;", md.ty, ZERO.c_str(), ZERO.c_str(), ZERO.c_str(),
+        ZERO.c_str(), ZERO.c_str(), ZERO.c_str()));
   o(fmt("  const %s* a = kx_wa + %d * k;", md.st, ns));
-  o("  #pragma unroll 4");
-  o(fmt("  for (int j = 0; j < %d; ++j) {", ns));
-  o(fmt("    const %s A = %s;", md.ty, ld("a[j]").c_str()));
+  o("  #pragma unroll 2");
+  o(fmt("  for (int j = 0; j + 1 < %d; j += 2) {", ns));
+  o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
   o(fmt("    s0 = %s; s1 = %s; s2 = %s;", FMA("A", ld(fmt("sX[j * %d + t]", B)), "s0").c_str(),
         FMA("A", ld(fmt("sZ1[j * %d + t]", B)), "s1").c_str(), FMA("A", ld(fmt("sZ2[j * %d + t]", B)), "s2").c_str()));
+  o(fmt("    t0 = %s; t1 = %s; t2 = %s;", FMA("Ab", ld(fmt("sX[(j + 1) * %d + t]", B)), "t0").c_str(),
+        FMA("Ab", ld(fmt("sZ1[(j + 1) * %d + t]", B)), "t1").c_str(), FMA("Ab", ld(fmt("sZ2[(j + 1) * %d + t]", B)), "t2").c_str()));
   o("  }");
+  if (ns % 2) {
+    const int j = ns - 1;
+    o(fmt("  { const %s A = %s;", md.ty, ld(fmt("a[%d]", j)).c_str()));
+    o(fmt("    s0 = %s; s1 = %s; s2 = %s; }", FMA("A", ld(fmt("sX[%d + t]", j * B)), "s0").c_str(),
+          FMA("A", ld(fmt("sZ1[%d + t]", j * B)), "s1").c_str(), FMA("A", ld(fmt("sZ2[%d + t]", j * B)), "s2").c_str()));
+  }
+  const std::string ONE = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0";
+  o(fmt("  s0 = %s; s1 = %s; s2 = %s;", FMA("t0", ONE, "s0").c_str(), FMA("t1", ONE, "s1").c_str(), FMA("t2", ONE, "s2").c_str()));
   const std::string two_s1 = md.kind == TrMode::DF ? "kx_mk(2.f * s1.hi, 2.f * s1.lo)" : md.kind == TrMode::F32 ? "2.0f * s1" : "2.0 * s1";
   o(fmt("  const %s den = %s;", md.ty, FMA("u", FMA("u", "s2", two_s1), "s0").c_str()));
   o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD(ld(fmt("sX[k * %d + t]", B))).c_str(), TOD(MUL("u", "u")).c_str(),
