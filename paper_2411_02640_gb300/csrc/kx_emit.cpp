@@ -1301,6 +1301,9 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   const double L0 = md.kind == TrMode::F64 ? 0.0 : 0.5 * (std::log(300.0) + std::log(3000.0));
   const double SC = md.kind == TrMode::F32 ? 1.4426950408889634 : 1.0;   // exp2 form for float32
   const int B = opt.block;
+  // float64-accurate viscosity keeps two vectors per species (X, v = 1/u) in shared memory
+  // and forms z1, z2 in the loop: two multiplies per pair buy twice the resident warps
+  const bool two_arrays = md.kind != TrMode::F32 && opt.part != 2;
   // ---- element literal, load, store and arithmetic spelled per mode
   auto lit = [&](double v) -> std::string {
     if (md.kind == TrMode::F64) return D(v);
@@ -1418,9 +1421,13 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("  " + st(fmt("sX[k * %d + t]", B), "X"));
   o(fmt("  const %s* pv = kx_pv + 5 * k; const %s* pl = kx_pl + 5 * k;", md.st, md.st));
   o(fmt("  const %s v = %s;", md.ty, EXP(horner("pv")).c_str()));
-  o(fmt("  const %s z1 = %s;", md.ty, MUL("X", "v").c_str()));
-  o("  " + st(fmt("sZ1[k * %d + t]", B), "z1"));
-  o("  " + st(fmt("sZ2[k * %d + t]", B), MUL("z1", "v")));
+  if (two_arrays) {
+    o("  " + st(fmt("sZ1[k * %d + t]", B), "v"));          // z1 = X v and z2 = z1 v are formed in the Wilke loop
+  } else {
+    o(fmt("  const %s z1 = %s;", md.ty, MUL("X", "v").c_str()));
+    o("  " + st(fmt("sZ1[k * %d + t]", B), "z1"));
+    o("  " + st(fmt("sZ2[k * %d + t]", B), MUL("z1", "v")));
+  }
   o(fmt("  const %s ll = %s;", md.ty, horner("pl").c_str()));
   o("  sl = " + FMA("X", EXP("ll"), "sl") + ";");
   o("  sil = " + FMA("X", EXP(NEG("ll")), "sil") + ";");
@@ -1440,16 +1447,22 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("  #pragma unroll 2");
   o(fmt("  for (int j = 0; j + 1 < %d; j += 2) {", ns));
   o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
-  o(fmt("    s0 = %s; s1 = %s; s2 = %s;", FMA("A", ld(fmt("sX[j * %d + t]", B)), "s0").c_str(),
-        FMA("A", ld(fmt("sZ1[j * %d + t]", B)), "s1").c_str(), FMA("A", ld(fmt("sZ2[j * %d + t]", B)), "s2").c_str()));
-  o(fmt("    t0 = %s; t1 = %s; t2 = %s;", FMA("Ab", ld(fmt("sX[(j + 1) * %d + t]", B)), "t0").c_str(),
-        FMA("Ab", ld(fmt("sZ1[(j + 1) * %d + t]", B)), "t1").c_str(), FMA("Ab", ld(fmt("sZ2[(j + 1) * %d + t]", B)), "t2").c_str()));
+  // the three vectors of species j: X_j, z1_j = X_j v_j, z2_j = z1_j v_j
+  auto vecs = [&](const std::string& jj, const char* sfx) {
+    if (!two_arrays)
+      return fmt("const %s x%s = %s, y%s = %s, z%s = %s;", md.ty, sfx, ld(fmt("sX[%s * %d + t]", jj.c_str(), B)).c_str(), sfx,
+                 ld(fmt("sZ1[%s * %d + t]", jj.c_str(), B)).c_str(), sfx, ld(fmt("sZ2[%s * %d + t]", jj.c_str(), B)).c_str());
+    return fmt("const %s x%s = %s, v%s = %s; const %s y%s = %s; const %s z%s = %s;", md.ty, sfx,
+               ld(fmt("sX[%s * %d + t]", jj.c_str(), B)).c_str(), sfx, ld(fmt("sZ1[%s * %d + t]", jj.c_str(), B)).c_str(), md.ty,
+               sfx, MUL(fmt("x%s", sfx), fmt("v%s", sfx)).c_str(), md.ty, sfx, MUL(fmt("y%s", sfx), fmt("v%s", sfx)).c_str());
+  };
+  o("    " + vecs("j", "a") + " " + vecs("(j + 1)", "b"));
+  o(fmt("    s0 = %s; s1 = %s; s2 = %s;", FMA("A", "xa", "s0").c_str(), FMA("A", "ya", "s1").c_str(), FMA("A", "za", "s2").c_str()));
+  o(fmt("    t0 = %s; t1 = %s; t2 = %s;", FMA("Ab", "xb", "t0").c_str(), FMA("Ab", "yb", "t1").c_str(), FMA("Ab", "zb", "t2").c_str()));
   o("  }");
   if (ns % 2) {
-    const int j = ns - 1;
-    o(fmt("  { const %s A = %s;", md.ty, ld(fmt("a[%d]", j)).c_str()));
-    o(fmt("    s0 = %s; s1 = %s; s2 = %s; }", FMA("A", ld(fmt("sX[%d + t]", j * B)), "s0").c_str(),
-          FMA("A", ld(fmt("sZ1[%d + t]", j * B)), "s1").c_str(), FMA("A", ld(fmt("sZ2[%d + t]", j * B)), "s2").c_str()));
+    o(fmt("  { const %s A = %s; %s", md.ty, ld(fmt("a[%d]", ns - 1)).c_str(), vecs(std::to_string(ns - 1), "a").c_str()));
+    o(fmt("    s0 = %s; s1 = %s; s2 = %s; }", FMA("A", "xa", "s0").c_str(), FMA("A", "ya", "s1").c_str(), FMA("A", "za", "s2").c_str()));
   }
   const std::string ONE = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0";
   o(fmt("  s0 = %s; s1 = %s; s2 = %s;", FMA("t0", ONE, "s0").c_str(), FMA("t1", ONE, "s1").c_str(), FMA("t2", ONE, "s2").c_str()));
@@ -1532,7 +1545,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
 
 // Shared memory per thread of the transport kernels, in bytes.
 int transport_smem_per_thread(const Mechanism& m, bool mixed, int part) {
-  return (part == 2 ? 2 : 3) * m.ns * (mixed ? 4 : 8);
+  // diffusion: X and S; viscosity: X, X/u, X/u^2 (float32) or X and 1/u (float64 accuracy)
+  return ((part == 2 || !mixed) ? 2 : 3) * m.ns * (mixed ? 4 : 8);
 }
 
 // ------------------------------------------------------------------ kernels

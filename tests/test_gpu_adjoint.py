@@ -126,7 +126,8 @@ def test_adjoint_throughput_and_jacobian_assembly_timing(torch):
     jac_ms, fd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     # the two Jacobians agree to the finite-difference truncation level, row-scaled
     sc = J.abs().amax(dim=2, keepdim=True) + 1e-300
-    agree = ((J - Jfd).abs() / sc).quantile(0.99).item()
+    rel = ((J - Jfd).abs() / sc).flatten()
+    agree = rel[:: max(1, rel.numel() // (1 << 22))].quantile(0.99).item()
     stats = {"states_vjp": 1 << 18, "vjp_ms": vjp_ms, "vjp_mpoints_s": (1 << 18) / vjp_ms / 1e3,
              "forward_ms": fwd_ms, "states_jacobian": nj, "jacobian_54_vjp_ms": jac_ms, "fd_jacobian_108_fwd_ms": fd_ms,
              "fd_vs_adjoint_p99_row_scaled": agree}
