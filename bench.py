@@ -206,7 +206,7 @@ def run_kx(args):
 
     n = args.points
     path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
-    mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg)
+    mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg, rates_mode=args.rates_mode)
     ns = mech.n_species
     T, p, Y = make_inputs(rank, n)
     dev = torch.device("cuda", local)
@@ -448,6 +448,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=POINTS, help="states per GPU (profiling of smaller cases)")
     ap.add_argument("--maxrreg", type=int, default=0, help="register cap for the generated kernels (0: compiler)")
+    ap.add_argument("--rates-mode", type=int, default=0, help="0 automatic, 1 unrolled, 2 table-driven rate kernels")
     ap.add_argument("--serve", action="store_true", help="serving sweep (rates x batching vs one at a time) only")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sample in the default line")

@@ -233,6 +233,38 @@ __device__ __forceinline__ kx_df kx_df_exp(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+
+// e^x of a float64 x with two float64 operations: x is split into a float
+// pair (one subtraction), the reduction x = k ln2/256 + r and e^r 2^(j/256)
+// run in double-float arithmetic on the float32 pipe (ln2/256 split in three
+// floats, the first of 5 significant bits so that k E1 is exact for
+// |k| < 2^19), the float-pair mantissa returns to float64 (one addition) and
+// 2^(k>>8) is an exponent-field add.  Relative error about 2e-12 (the
+// 48-bit float pair that holds x), used where the error bar allows it.
+__device__ __forceinline__ double kx_exp_r(double x) {
+#ifdef KX_LIBMATH
+  return exp(x);
+#else
+  if (!(fabs(x) < 700.0)) return exp(x);
+  const float xh = kx_d2f(x);
+  const float xl = kx_d2f(x - kx_f2d(xh));
+  const float tk = __fmaf_rn(xh, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_E1F, xh);
+  const float p = __fmul_rn(kf, KX_E2F);
+  const float pe = __fmaf_rn(kf, KX_E2F, -p);
+  kx_df r = kx_ts(t1, -p);
+  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(xl, pe), __fmul_rn(kf, KX_E3F))));
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df sv = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  sv = kx_qts(sv.hi, __fadd_rn(sv.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), sv, kx_mk(tj.x, tj.y));
+  const double vd = kx_f2d(v.hi) + kx_f2d(v.lo);
+  return __hiloint2double(__double2hiint(vd) + (int)((unsigned)(k >> 8) << 20), __double2loint(vd));
+#endif
+}
 #endif  // KX_TDF
 )KXPRE";
 
@@ -1593,7 +1625,12 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
   const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport;
-  const bool tdf = kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0;
+  // table-driven float64 rate kernels take their exponentials from kx_exp_r (error ~2e-12 against
+  // a 1e-10 bar); the unrolled ones keep kx_exp, whose short inline sequence keeps compile time
+  // of the straight-line code in check
+  const bool table_rates = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
+  const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates;
+  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64;
   s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
   s << "#define KX_TDF " << tdf << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
@@ -1615,12 +1652,16 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << ") " << entry
     << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
     << outs << ", long long n)\n{\n";
+  std::string text = body.o.str();
+  if (rates64) {
+    for (size_t at = text.find("kx_exp("); at != std::string::npos; at = text.find("kx_exp(", at + 8)) text.replace(at, 7, "kx_exp_r(");
+  }
   s << "  kx_load_tables();\n";
   s << "  for (long long i = (long long)blockIdx.x * " << opt.block << " + threadIdx.x; i < n; i += (long long)gridDim.x * "
     << opt.block << ") {\n";
   s << "    const double T = T_[i], P = P_[i];\n";
   s << "    if (!(T > 0.0 && P > 0.0 && T < KX_INF && P < KX_INF)) { " << nan_fill << " continue; }\n";
-  s << body.o.str();
+  s << text;
   s << "  }\n}\n";
   if (counts) *counts = c;
   return s.str();
