@@ -69,8 +69,14 @@ typedef struct {
                          1 per-species exp(-G_k/RT) products, one division per reaction */
   int tr_mode;        /* float64 transport: 0 (default) double-float arithmetic on the float32
                          pipe (float64 accuracy, ~2^-47 per operation), 1 native float64 */
-  int rates_mode;     /* production-rate kernels: 0 (default) automatic -- fully unrolled up to 64
-                         species and 400 reactions, table driven beyond; 1 unrolled; 2 table driven */
+  int rates_mode;     /* native float64 and mixed production-rate kernels: 0 (default) automatic --
+                         fully unrolled up to 64 species and 400 reactions, table driven beyond;
+                         1 unrolled; 2 table driven */
+  int rates_arith;    /* arithmetic of the KX_FP64 production rates and rates of progress:
+                         0 (default) or 2 double-float (float32 pairs, ~2^-47 per operation) in
+                         log space on the float32 pipe, one table-driven loop per reaction class,
+                         wdot accumulated in float pairs under a per-state power-of-two scale;
+                         1 native float64 */
   int maxrreg;        /* register cap per thread for the generated kernels; 0 = compiler choice */
   int block;          /* threads per block; 0 = 128 */
   int lazy;           /* 0: compile the production-rate, thermo and transport kernels at load

@@ -284,6 +284,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.kc_mode < 0 || h->opt.kc_mode > 1) return fail(KX_ERR_ARG, "kc_mode must be 0 or 1");
   if (h->opt.tr_mode < 0 || h->opt.tr_mode > 1) return fail(KX_ERR_ARG, "tr_mode must be 0 or 1");
   if (h->opt.rates_mode < 0 || h->opt.rates_mode > 2) return fail(KX_ERR_ARG, "rates_mode must be 0, 1 or 2");
+  if (h->opt.rates_arith < 0 || h->opt.rates_arith > 2) return fail(KX_ERR_ARG, "rates_arith must be 0, 1 or 2");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
   h->opt.cache_dir = nullptr;
@@ -312,6 +313,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.part = sp.part;
     k->eopt.maxrreg = h->opt.maxrreg;
     k->eopt.rates_mode = h->opt.rates_mode;
+    k->eopt.rates_arith = h->opt.rates_arith;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
       const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);

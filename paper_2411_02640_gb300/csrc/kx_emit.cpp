@@ -25,9 +25,11 @@
 // falloff arithmetic in float32, keeps ln K_c (through species chemical
 // potentials G_k/RT + ln C_k), the forward/reverse cancellation and the
 // accumulation of wdot in float64 (see emit_rates_mixed).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <set>
 #include <sstream>
@@ -71,6 +73,8 @@ __device__ __forceinline__ double kx_f2d(float f) {
 }
 // Nearest integer of a float with |t| < 2^22, without the XU pipe.
 __device__ __forceinline__ int kx_rint(float t) { return __float_as_int(t + KX_RND_F) - 0x4b400000; }
+// Float of an integer with |n| < 2^22, without the conversion unit.
+__device__ __forceinline__ float kx_i2f(int n) { return __int_as_float(0x4b400000 + n) - KX_RND_F; }
 
 #if KX_T64
 __shared__ double kx_s_exp[256];
@@ -167,6 +171,9 @@ __device__ __forceinline__ float kx_ln_inv_1p(float lnPr) {
 #if KX_TDF
 __shared__ float2 kx_s_dexp[256];
 #endif
+#if KX_TDFR
+__shared__ float4 kx_s_dlog[256];
+#endif
 __device__ __forceinline__ void kx_load_tables() {
 #if KX_T64 && !defined(KX_LIBMATH)
   for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_exp[t] = kx_exp2_tab[t];
@@ -174,6 +181,9 @@ __device__ __forceinline__ void kx_load_tables() {
 #endif
 #if KX_TDF
   for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_dexp[t] = kx_dexp2_tab[t];
+#endif
+#if KX_TDFR
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) kx_s_dlog[t] = kx_dlog_tab[t];
 #endif
   __syncthreads();
 }
@@ -266,6 +276,145 @@ __device__ __forceinline__ double kx_exp_r(double x) {
 #endif
 }
 #endif  // KX_TDF
+
+#if KX_TDFR
+// ---- double-float arithmetic for the float64-accurate production rates
+// (log-space rates on the float32 pipe; the few float64 operations left are
+// the final conversion of each production rate).
+#define KX_INF_F __int_as_float(0x7f800000)
+// a + b (error about 2^-47 (|a| + |b|))
+__device__ __forceinline__ kx_df kx_df_add(kx_df a, kx_df b) {
+  const kx_df s = kx_ts(a.hi, b.hi);
+  return kx_qts(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ kx_df kx_df_neg(kx_df a) { return kx_mk(-a.hi, -a.lo); }
+__device__ __forceinline__ kx_df kx_df_sub(kx_df a, kx_df b) { return kx_df_add(a, kx_df_neg(b)); }
+// a b with b a float
+__device__ __forceinline__ kx_df kx_df_mulf(kx_df a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  return kx_qts(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+// a / b: a reciprocal estimate refined by one Newton step, then one
+// correction of the quotient from the exact remainder a - q1 b
+__device__ __forceinline__ kx_df kx_df_div(kx_df a, kx_df b) {
+  float rb = __fdividef(1.0f, b.hi);
+  rb = __fmaf_rn(rb, __fmaf_rn(-b.hi, rb, 1.0f), rb);
+  const float q1 = __fmul_rn(a.hi, rb);
+  const float p = __fmul_rn(q1, b.hi);
+  const float pe = __fmaf_rn(q1, b.hi, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), __fmaf_rn(-q1, b.lo, a.lo));
+  return kx_qts(q1, __fmul_rn(r, rb));
+}
+// Float pair of a double: the high part keeps 24 significant bits
+// (truncation), the low part the remaining 29 bits rounded once.  Values
+// below float's normal range give 0; above it, +-inf (nan stays nan).
+__device__ __forceinline__ kx_df kx_d2df_i(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  if (e < -126) return kx_mk(0.0f, 0.0f);
+  if (e > 127) return kx_mk(__double2float_rn(x), 0.0f);
+  const unsigned sgn = (unsigned)hi & 0x80000000u;
+  const float h = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29));
+  const unsigned r29 = lo & 0x1fffffffu;
+  const float l = __fmaf_rn(__fsub_rn(__int_as_float(0x4b000000 | (int)(r29 >> 6)), 8388608.0f), 0x1p-46f,
+                            __fmul_rn(__fsub_rn(__int_as_float(0x4b000000 | (int)(r29 & 63u)), 8388608.0f), 0x1p-52f));
+  return kx_mk(h, __uint_as_float(sgn | __float_as_uint(__fmul_rn(l, __int_as_float((e + 127) << 23)))));
+}
+// e ln2 + log(c_j) + log1p((m - c_j)/c_j) for a positive value 2^e m, m =
+// mh + ml in [1, 2) with its top 8 fraction bits j (Tang's table-driven log
+// with a float-pair table of 1/c_j and log c_j; |r| <= 1/512, the r^2/2 term
+// exact as a product pair, the rest of the series in float32, below 3e-9).
+__device__ __forceinline__ kx_df kx_df_log_core(int e, int j, float mh, float ml) {
+  const float c = __int_as_float(0x3f800000 | ((2 * j + 1) << 14));
+  const float4 t = kx_s_dlog[j];
+  const kx_df d = kx_qts(__fsub_rn(mh, c), ml);
+  const float rh = __fmul_rn(d.hi, t.x);
+  const float rl = __fmaf_rn(d.hi, t.y, __fmaf_rn(d.lo, t.x, __fmaf_rn(d.hi, t.x, -rh)));
+  const float hr = __fmul_rn(-0.5f, rh);
+  const float h2 = __fmul_rn(hr, rh);
+  const float h2e = __fmaf_rn(hr, rh, -h2);
+  const float p = __fmaf_rn(__fmaf_rn(__fmaf_rn(rh, -0.166666672f, 0.2f), rh, -0.25f), rh, 0.333333343f);
+  const float tail = __fmul_rn(__fmul_rn(__fmul_rn(rh, rh), rh), p);
+  const kx_df l1 = kx_qts(rh, h2);
+  const float l1lo = __fadd_rn(l1.lo, __fadd_rn(__fadd_rn(rl, h2e), __fmaf_rn(-rh, rl, tail)));
+  const float ef = __fsub_rn(__int_as_float(0x4b400000 + e), KX_RND_F);
+  const float a1 = __fmul_rn(ef, KX_LN2_1F);
+  const float p2 = __fmul_rn(ef, KX_LN2_2F);
+  const float p2e = __fmaf_rn(ef, KX_LN2_2F, -p2);
+  const kx_df s = kx_ts(a1, t.z);
+  const kx_df u = kx_ts(s.hi, p2);
+  const kx_df v = kx_ts(u.hi, l1.hi);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s.lo, u.lo), __fadd_rn(v.lo, p2e)),
+                             __fadd_rn(__fmaf_rn(ef, KX_LN2_3F, t.w), l1lo));
+  return kx_qts(v.hi, lo);
+}
+// ln x of a positive normal double
+__device__ __forceinline__ kx_df kx_df_log_d(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned r29 = lo & 0x1fffffffu;
+  const float mh = __int_as_float(0x3f800000 | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
+  const float ml = __fmaf_rn(__fsub_rn(__int_as_float(0x4b000000 | (int)(r29 >> 6)), 8388608.0f), 0x1p-46f,
+                             __fmul_rn(__fsub_rn(__int_as_float(0x4b000000 | (int)(r29 & 63u)), 8388608.0f), 0x1p-52f));
+  return kx_df_log_core((hi >> 20) - 1023, (hi >> 12) & 0xff, mh, ml);
+}
+// ln x of a float pair; x.hi must be positive and normal, else -1e4 is
+// returned, a stand-in for ln 0 that every caller clamps
+__device__ __forceinline__ kx_df kx_df_log(kx_df x) {
+  if (!(x.hi >= 1.17549435e-38f && x.hi < KX_INF_F)) return kx_mk(-1.0e4f, 0.0f);
+  const int b = __float_as_int(x.hi);
+  const int e = (b >> 23) - 127;
+  const float mh = __int_as_float((b & 0x7fffff) | 0x3f800000);
+  const float ml = __fmul_rn(x.lo, __int_as_float((127 - e) << 23));
+  return kx_df_log_core(e, (b >> 15) & 0xff, mh, ml);
+}
+// e^x of a float pair as a float pair: 0 for x <= -87, inf for x >= 88.7
+// (reduction and tail as in kx_df_exp)
+__device__ __forceinline__ kx_df kx_df_exp_s(kx_df x) {
+  if (!(x.hi > -87.0f)) return kx_mk(0.0f, 0.0f);
+  if (!(x.hi < 88.7f)) return kx_mk(KX_INF_F, 0.0f);
+  const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_C1F, x.hi);
+  const float p = __fmul_rn(kf, KX_C2F);
+  const float pe = __fmaf_rn(kf, KX_C2F, -p);
+  kx_df r = kx_ts(t1, -p);
+  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_C3F))));
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const float sc = __int_as_float(((k >> 8) + 127) << 23);
+  return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
+}
+// S ln2 as a float pair (exact product terms for |S| < 2^11)
+__device__ __forceinline__ kx_df kx_df_ln2_mul(int S) {
+  const float sf = __fsub_rn(__int_as_float(0x4b400000 + S), KX_RND_F);
+  const float p2 = __fmul_rn(sf, KX_LN2_2F);
+  const kx_df s = kx_qts(__fmul_rn(sf, KX_LN2_1F), p2);
+  return kx_qts(s.hi, __fadd_rn(s.lo, __fmaf_rn(sf, KX_LN2_3F, __fmaf_rn(sf, KX_LN2_2F, -p2))));
+}
+// (a.hi + a.lo) 2^S as a double: one float64 addition, the power of two
+// added to the exponent field (ldexp only when the result leaves the normal
+// range)
+__device__ __forceinline__ double kx_df2d_s(kx_df a, int S) {
+  if (a.hi == 0.0f) return 0.0;
+  if (!(fabsf(a.hi) < KX_INF_F)) return (double)a.hi;
+  const double d = kx_f2d(a.hi) + kx_f2d(a.lo);
+  const int hi = __double2hiint(d);
+  const int E = ((hi >> 20) & 0x7ff) + S;
+  if (E > 0 && E < 0x7ff) return __hiloint2double(hi + (int)((unsigned)S << 20), __double2loint(d));
+  return ldexp(d, S);
+}
+// ln(1 + y) for 0 <= y <= 1 (absolute error about 1e-15)
+__device__ __forceinline__ kx_df kx_df_log1p(kx_df y) {
+  const kx_df s = kx_qts(1.0f, y.hi);
+  return kx_df_log(kx_qts(s.hi, __fadd_rn(s.lo, y.lo)));
+}
+#endif  // KX_TDFR
 )KXPRE";
 
 namespace {
@@ -1053,6 +1202,393 @@ void emit_rates_table_mixed(Out& o, Out& g, const Mechanism& m, bool rop, OpCoun
   }
 }
 
+// ------------------------------------------------------------------ rates, float64 accuracy on the float32 pipe
+// Every quantity of the log-space rate evaluation is a float pair
+// (double-float, about 2^-47 per operation): ln T, 1/T, ln |C_k|, G_k/RT,
+// mu_k = G_k/RT + ln |C_k|, ln k_f, the falloff blending, ln |R_f| and
+// ln(|R_r|/|R_f|) = sum nu mu - (sum nu) ln(p_atm/(R T)).  The net rate is
+// the larger rate times 1 -+ e^-|ln ratio| (minus when R_f and R_r have the
+// same sign; a negative mass fraction makes a concentration, and the
+// products it enters, negative), and wdot is accumulated in float pairs
+// scaled by 2^-S, where S is chosen per state from a float32 upper bound of
+// every reaction's larger rate (a pre-pass over the reactions), so that the
+// largest scaled rate is near 2^64 and nothing can overflow; terms more than
+// 2^190 below the largest rate underflow to zero.  wdot_k = w_k 2^S leaves
+// through one float64 addition per species.
+//
+// Reactions are grouped into classes of one code shape (kind, reversibility,
+// blending, numbers of reactant and product entries, a coefficient nu
+// counting as nu entries of the species); each class is one loop over its
+// table with straight-line code, warp-uniform loads and no inner loops over
+// species.  Each state's species vectors ({ln |C|, mu} as a float4 and the
+// float-pair accumulators) live in per-thread local arrays, so the kernel
+// compiles in seconds for any mechanism size.
+std::string fpair(double v) {
+  const float h = (float)v;
+  const float l = (float)(v - (double)h);
+  return F(h) + "," + F(l);
+}
+
+std::string DFc(double v) { return "kx_mk(" + fpair(v) + ")"; }
+
+// float32-pipe instruction estimates of the double-float primitives (for the
+// operation counts)
+constexpr double kDfAdd = 11, kDfMul = 7, kDfFma = 15, kDfMulf = 5, kDfDiv = 16, kDfExp = 30, kDfLog = 40;
+
+struct DfClass {
+  Kind kind;
+  bool rev;
+  Blend blend;
+  int nre, npr;
+  std::vector<int> rx;
+};
+
+std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
+  std::vector<int> e;
+  for (auto& s : side)
+    for (int n = 0; n < s.second; ++n) e.push_back(s.first);
+  return e;
+}
+
+void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts& c) {
+  const int ns = m.ns;
+  // ---- classes and their tables
+  std::vector<DfClass> cls;
+  for (int i = 0; i < m.nr(); ++i) {
+    const Reaction& r = m.rx[i];
+    const int nre = (int)entries(r.reac).size(), npr = (int)entries(r.prod).size();
+    const Blend bl = (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) ? r.blend : Blend::Lindemann;
+    auto it = std::find_if(cls.begin(), cls.end(), [&](const DfClass& d) {
+      return d.kind == r.kind && d.rev == r.reversible && d.blend == bl && d.nre == nre && d.npr == npr;
+    });
+    if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, {}}); it = cls.end() - 1; }
+    it->rx.push_back(i);
+  }
+  std::string eff, plog, plogp;
+  int eo = 0, po = 0;
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    const DfClass& d = cls[ci];
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const int NF = fo ? 7 : tb ? 3 : 2;
+    std::string si, sf, se;
+    for (int i : d.rx) {
+      const Reaction& r = m.rx[i];
+      auto er = entries(r.reac), ep = entries(r.prod);
+      for (int k : er) si += std::to_string(k) + ",";
+      for (int k : ep) si += std::to_string(k) + ",";
+      si += std::to_string(i) + ",";
+      for (int j = E + 1; j < P; ++j) si += "0,";
+      double maxeff = r.default_eff;
+      for (auto& x : r.eff) maxeff = std::max(maxeff, x.second);
+      sf += "{" + fpair(std::log(r.k.A > 0 ? r.k.A : 1e-300)) + "," + fpair(r.k.beta) + "},";
+      sf += "{" + fpair(-r.k.E) + "," + F(std::log(std::max(maxeff, 1e-30))) + ",0.0f},";
+      if (tb) {
+        double p[5] = {0, 0, 0, 0, 0};
+        if (r.blend == Blend::Troe) { p[0] = 1.0 - r.troe[0]; p[1] = r.troe[0]; p[2] = -1.0 / r.troe[1]; p[3] = -1.0 / r.troe[2]; p[4] = -r.troe[3]; }
+        if (r.blend == Blend::Sri) { p[0] = r.sri[0]; p[1] = -r.sri[1]; p[2] = -1.0 / r.sri[2]; p[3] = std::log(r.sri[3]); p[4] = r.sri[4]; }
+        const double la0 = r.has_k0 ? std::log(r.k0.A > 0 ? r.k0.A : 1e-300) : 0.0;
+        sf += "{" + fpair(r.default_eff) + "," + fpair(la0) + "},";
+        if (fo) {
+          sf += "{" + fpair(r.k0.beta) + "," + fpair(-r.k0.E) + "},";
+          sf += "{" + fpair(p[0]) + "," + fpair(p[1]) + "},";
+          sf += "{" + fpair(p[2]) + "," + fpair(p[3]) + "},";
+          sf += "{" + fpair(p[4]) + ",0.0f,0.0f},";
+        }
+        int n = 0;
+        if (r.collider >= 0) { eff += fmt("{%d, 0.0f, 0.0f, 0},", r.collider); n = -1; ++eo; }
+        else for (auto& x : r.eff) if (x.second != r.default_eff) { eff += fmt("{%d, %s, 0},", x.first, fpair(x.second - r.default_eff).c_str()); ++n; ++eo; }
+        se += fmt("{%d,%d},", n < 0 ? eo - 1 : eo - n, n);
+      } else if (d.kind == Kind::Plog) {
+        se += fmt("{%d,%d},", po, (int)r.plog.size());
+        for (auto& t : r.plog) {
+          plog += fpair(std::log(t[0])) + "," + fpair(std::log(t[1])) + "," + fpair(t[2]) + "," + fpair(-t[3]) + ",";
+          long long b;
+          std::memcpy(&b, &t[0], 8);
+          plogp += std::to_string(b) + "LL,";
+          ++po;
+        }
+      }
+    }
+    g(fmt("__device__ const __align__(16) int kx_s%d[%d] = {%s};", (int)ci, P * (int)d.rx.size(), si.c_str()));
+    g(fmt("__device__ const float4 kx_f%d[%d] = {%s};", (int)ci, NF * (int)d.rx.size(), sf.c_str()));
+    if (tb || d.kind == Kind::Plog) g(fmt("__device__ const int2 kx_e%d[%d] = {%s};", (int)ci, (int)d.rx.size(), se.c_str()));
+  }
+  g("struct __align__(16) kx_effd_t { int k; float ahi, alo; int pad; };");
+  g(fmt("__device__ const kx_effd_t kx_effd[%d] = {%s{0, 0.0f, 0.0f, 0}};", eo + 1, eff.c_str()));
+  g(fmt("__device__ const float kx_plogf[%d] = {%s0.0f};", 8 * po + 1, plog.c_str()));
+  g(fmt("__device__ const long long kx_plogp[%d] = {%s0LL};", po + 1, plogp.c_str()));
+  // G/RT coefficients per species and range: T-polynomial c0..c4, a5 (1/T), -a0 (ln T), as float pairs
+  std::string nasa, tmb, iw, lw;
+  for (int k = 0; k < ns; ++k) {
+    for (int rg = 0; rg < 2; ++rg) {
+      const double* a = rg == 0 ? &m.a_lo[7 * k] : &m.a_hi[7 * k];
+      const double cfs[7] = {a[0] - a[6], -a[1] / 2.0, -a[2] / 6.0, -a[3] / 12.0, -a[4] / 20.0, a[5], -a[0]};
+      for (int j = 0; j < 7; ++j) nasa += fpair(cfs[j]) + ",";
+      nasa += "0.0f,0.0f,";
+    }
+    long long b;
+    std::memcpy(&b, &m.Tmid[k], 8);
+    tmb += std::to_string(b) + "LL,";
+    iw += fpair(1.0 / m.W[k]) + ",";
+    lw += fpair(std::log(m.W[k])) + ",";
+  }
+  g(fmt("__device__ const __align__(16) float kx_gcf[%d] = {%s0.0f};", 32 * ns + 4, nasa.c_str()));
+  g(fmt("__device__ const long long kx_tmidb[%d] = {%s0LL};", ns + 1, tmb.c_str()));
+  g(fmt("__device__ const float kx_iwf[%d] = {%s0.0f};", 2 * ns + 1, iw.c_str()));
+  g(fmt("__device__ const float kx_lwf[%d] = {%s0.0f};", 2 * ns + 1, lw.c_str()));
+
+  // ---- per state: T, ln T, 1/T, C_M, sigma, and the species vectors
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  o("#define KX_PF(p) kx_mk((p)[0], (p)[1])");
+  o("const kx_df Td = kx_d2df_i(T);");
+  o("const kx_df lnT = kx_df_log_d(T);");
+  o("const kx_df iT = kx_df_div(kx_mk(1.0f, 0.0f), Td);");
+  if (any_plog) o("const kx_df lnP = kx_df_log_d(P);");
+  o(fmt("const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
+  o(fmt("const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
+  o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k (pair)}", ns));
+  if (!rop) o(fmt("kx_df w[%d];", ns));
+  o("kx_df sig = kx_mk(0.0f, 0.0f);");
+  o(fmt("for (int k = 0; k < %d; ++k) sig = kx_df_fma(kx_d2df_i(Y_[(long long)k * ld + i]), KX_PF(kx_iwf + 2 * k), sig);", ns));
+  o("if (!(sig.hi > 0.0f && sig.hi < KX_INF_F)) KX_BAD_POINT");
+  o("const kx_df fC = kx_df_div(cM, sig);");
+  o("const kx_df lnfC = kx_df_log(fC);");
+  o("const long long Tb = __double_as_longlong(T);");
+  // signs of the concentrations: bit k of the mask words set for Y_k < 0
+  const int nw = (ns + 63) / 64;
+  for (int q = 0; q < nw; ++q) o(fmt("unsigned long long nm%d = 0ull;", q));
+  {
+    std::string sel = fmt("nm%d", nw - 1);
+    for (int q = nw - 2; q >= 0; --q) sel = fmt("((k) < %d ? nm%d : %s)", 64 * (q + 1), q, sel.c_str());
+    o("#define KX_NEG(k) ((int)((" + sel + " >> ((k) & 63)) & 1ull))");
+  }
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o("  const double Yk = Y_[(long long)k * ld + i];");
+  o("  const long long yb = __double_as_longlong(Yk) & 0x7fffffffffffffffLL;");
+  o("  // ln |C_k| = ln |Y_k| - ln W_k + ln(C_M/sigma), floored at -700 (Y_k = 0 or |Y_k| below 1e-304: absent)");
+  o("  kx_df l = kx_mk(-700.0f, 0.0f);");
+  o("  if (yb >= 0x0010000000000000LL && yb < 0x7ff0000000000000LL) {");
+  o("    l = kx_df_add(kx_df_log_d(__longlong_as_double(yb)), kx_df_sub(lnfC, KX_PF(kx_lwf + 2 * k)));");
+  o("    if (!(l.hi > -700.0f)) l = kx_mk(-700.0f, 0.0f);");
+  o("  }");
+  {
+    std::string s = "  if (Yk < 0.0) {";
+    for (int q = 0; q < nw; ++q) s += fmt(" %sif ((k >> 6) == %d) nm%d |= 1ull << (k & 63);", q ? "else " : "", q, q);
+    o(s + " }");
+  }
+  o("  const float* a = kx_gcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("  kx_df gk = kx_df_fma(KX_PF(a + 8), Td, KX_PF(a + 6));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 4));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 2));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 0));");
+  o("  gk = kx_df_fma(KX_PF(a + 10), iT, gk);");
+  o("  gk = kx_df_fma(KX_PF(a + 12), lnT, gk);");
+  o("  const kx_df mk_ = kx_df_add(gk, l);");
+  o("  sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
+  if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
+  o("}");
+  c.fp32 += 40 + 45 + kDfDiv + 2 * kDfMul + kDfAdd + kDfDiv + kDfLog;
+  c.fp32 += ns * (12 + kDfFma) + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
+
+  auto load_species = [&](const DfClass& d, int ci) {
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    std::string s = fmt("  const int4* sp4 = (const int4*)(kx_s%d + %d * r);", ci, P);
+    o(s);
+    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 s%d = sp4[%d];", q, q));
+    auto comp = [](int j) { static const char* xyzw[4] = {"x", "y", "z", "w"}; return fmt("s%d.%s", j / 4, xyzw[j % 4]); };
+    for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, comp(j).c_str()));
+    if (rop) o(fmt("  const int ri = %s;", comp(E).c_str()));
+  };
+
+  // ---- pre-pass: float32 upper bound U of ln max(|R_f|, |R_r|) over the reactions
+  if (!rop) {
+    o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
+    o("float U = -1.0e30f;");
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+      const DfClass& d = cls[ci];
+      const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const int NF = fo ? 7 : tb ? 3 : 2;
+      o("#pragma unroll 1");
+      o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
+      ++o.ind;
+      load_species(d, (int)ci);
+      --o.ind;
+      o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+      o("  const float4 f0 = f[0], f1 = f[1];");
+      o("  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
+      if (d.kind == Kind::ThreeBody) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  b += e.y < 0 ? sv[kx_effd[e.x].k].x : lncMf + f1.z;");
+      } else if (fo) {
+        o("  const float4 f2 = f[2], f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+        o("  // ln F <= max(0, ln F_cent) (Troe); ln d + e ln T + max(0, ln base) (SRI)");
+        if (d.blend == Blend::Troe)
+          o("  const float lf = fmaxf(0.0f, __logf(f4.x * __expf(Tf * f5.x) + f4.z * __expf(Tf * f5.z) + __expf(f6.x * iTf)));");
+        else if (d.blend == Blend::Sri)
+          o("  const float lf = f5.z + f6.x * lnTf + fmaxf(0.0f, __logf(f4.x * __expf(f4.z * iTf) + __expf(Tf * f5.x)));");
+        else
+          o("  const float lf = 0.0f;");
+        if (d.kind == Kind::ChemAct) o("  b = fmaf(f3.x, lnTf, fmaf(f3.z, iTf, f2.z)) + lf;");
+        else o("  b += lf;");
+      } else if (d.kind == Kind::Plog) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  const float* t = kx_plogf + 8 * e.x;");
+        o("  b = -1.0e30f;");
+        o("  for (int j = 0; j < e.y; ++j) b = fmaxf(b, fmaf(t[8 * j + 4], lnTf, fmaf(t[8 * j + 6], iTf, t[8 * j + 2])));");
+      }
+      for (int j = 0; j < d.nre; ++j) o(fmt("  b += sv[k%d].x;", j));
+      if (d.rev) {
+        const int dn = d.npr - d.nre;
+        std::string s = dn == 0 ? std::string("0.0f") : fmt("%s * lnPRTf", F(-dn).c_str());
+        for (int j = 0; j < d.nre; ++j) s += fmt(" - sv[k%d].z", j);
+        for (int j = d.nre; j < d.nre + d.npr; ++j) s += fmt(" + sv[k%d].z", j);
+        o("  b += fmaxf(" + s + ", 0.0f);");
+      }
+      o("  U = fmaxf(U, b);");
+      o("}");
+      c.fp32 += d.rx.size() * (8.0 + 2 * (d.nre + d.npr));
+    }
+    o("// largest scaled rate near 2^63.5; |S| < 2^11 keeps S ln2 exact to the float-pair precision");
+    o("const int S = kx_rint(fminf(fmaxf(U * KX_LOG2E_F, -1000.0f), 1000.0f)) - 63;");
+    o("const kx_df lnS = kx_df_ln2_mul(S);");
+  }
+
+  // ---- main pass, one loop per class
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    const DfClass& d = cls[ci];
+    const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const int NF = fo ? 7 : tb ? 3 : 2;
+    const int E = d.nre + d.npr;
+    o(fmt("// class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
+    o("#pragma unroll 1");
+    o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
+    ++o.ind;
+    load_species(d, (int)ci);
+    --o.ind;
+    o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+    o("  const float4 f0 = f[0], f1 = f[1];");
+    o("  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+    if (tb) {
+      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+      o("  const float4 f2 = f[2];");
+      o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
+      o("  if (e.y < 0) {");
+      o("    const int kc = kx_effd[e.x].k;");
+      o("    X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + i]), KX_PF(kx_iwf + 2 * kc)), fC);");
+      o("  } else {");
+      o("    kx_df t = kx_mk(0.0f, 0.0f);");
+      o("    for (int j = 0; j < e.y; ++j) {");
+      o("      const kx_effd_t q = kx_effd[e.x + j];");
+      o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + i]), KX_PF(kx_iwf + 2 * q.k)), t);");
+      o("    }");
+      o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+      o("  }");
+      c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
+    }
+    if (fo) {
+      o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+      o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
+      o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+      o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+      o("  kx_df lnF = kx_mk(0.0f, 0.0f);");
+      const std::string il10 = DFc(1.0 / std::log(10.0));
+      if (d.blend == Blend::Troe) {
+        o("  kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
+        o("  Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
+        o("  Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
+        o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+        o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+        o(fmt("  const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
+              DFc(0.75).c_str()));
+        o(fmt("  lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
+        c.fp32 += d.rx.size() * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
+      } else if (d.blend == Blend::Sri) {
+        o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+        o("  const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
+        o("  lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
+        c.fp32 += d.rx.size() * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
+      }
+      o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
+      o("  const bool small = lnPr.hi < 0.0f;");
+      o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
+      if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
+      else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
+      c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
+    } else if (d.kind == Kind::Plog) {
+      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+      o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+      o("  const long long Pb = __double_as_longlong(P);");
+      o("  if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
+      o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
+      o("  else {");
+      o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+      o("    const float* u = t + 8 * j;");
+      o("    const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
+      o("    const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
+      o("    lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
+      o("  }");
+      c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
+    }
+    // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
+    for (int j = 0; j < E; ++j) o(fmt("  const float4 v%d = sv[k%d];", j, j));
+    o(rop ? "  kx_df lf = lk;" : "  kx_df lf = kx_df_sub(lk, lnS);");
+    for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add(lf, kx_mk(v%d.x, v%d.y));", j, j));
+    std::string sfx = "0", srx = "0";
+    for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+    for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+    o("  int sf = " + sfx + ";");
+    o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
+    o("  bool rev = false;");
+    c.fp32 += d.rx.size() * (2 * kDfFma + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
+    if (d.rev) {
+      const int dn = d.npr - d.nre;
+      o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
+      std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+      o("    kx_df dl = " + first + ";");
+      for (int j = 1; j < E; ++j)
+        o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
+      if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+      o("    const int sr = " + srx + ";");
+      o("    rev = dl.hi > 0.0f;");
+      o("    if (rev) L = kx_df_add(lf, dl);");
+      o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
+      o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
+      o("    const float pm = sf == sr ? -1.0f : 1.0f;");
+      o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
+      o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
+      o("    if (sf == sr) sf ^= (int)rev;");
+      o("  }");
+      c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+    }
+    if (rop) {
+      o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
+      o("  kx_df q = kx_df_mul(kx_df_exp_s(kx_df_sub(L, kx_df_ln2_mul(Sr))), fac);");
+      c.fp32 += d.rx.size() * (kDfAdd + 10);
+    } else {
+      o("  kx_df q = kx_df_mul(kx_df_exp_s(L), fac);");
+    }
+    o("  if (sf) q = kx_df_neg(q);");
+    if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
+    if (rop) {
+      o("  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
+      c.fp64 += d.rx.size();
+    } else {
+      for (int j = 0; j < E; ++j) o(fmt("  w[k%d] = kx_df_%s(w[k%d], q);", j, j < d.nre ? "sub" : "add", j));
+      c.fp32 += d.rx.size() * E * kDfAdd;
+    }
+    o("}");
+  }
+  if (!rop) {
+    o(fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));
+    c.fp64 += ns;
+  }
+}
+
 // ------------------------------------------------------------------ adjoint
 // Vector-Jacobian product of the production rates at fixed p.  With
 // a_i = sum_k nu_ki v_k, v^T wdot = sum_i a_i q_i, so each reaction adds
@@ -1596,7 +2132,8 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       outs = "double* __restrict__ out_";
       nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);
       const bool table = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
-      if (table && opt.mixed) emit_rates_table_mixed(body, globals, m, rop, c);
+      if (!opt.mixed && opt.rates_arith != 1) emit_rates_class_df(body, globals, m, rop, c);
+      else if (table && opt.mixed) emit_rates_table_mixed(body, globals, m, rop, c);
       else if (table) emit_rates_table64(body, globals, m, rop, c);
       else if (opt.mixed) emit_rates_mixed(body, m, rop, c);
       else emit_rates64(body, m, opt, rop, c);
@@ -1624,15 +2161,17 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport;
+  const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && opt.rates_arith != 1;
+  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates;
   // table-driven float64 rate kernels take their exponentials from kx_exp_r (error ~2e-12 against
   // a 1e-10 bar); the unrolled ones keep kx_exp, whose short inline sequence keeps compile time
   // of the straight-line code in check
   const bool table_rates = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
-  const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates;
-  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64;
+  const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates && !df_rates;
+  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates;
   s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
   s << "#define KX_TDF " << tdf << "\n";
+  s << "#define KX_TDFR " << df_rates << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
@@ -1643,7 +2182,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   // the extra warps hide the latency of the exp tables and dependent float64 chains better
   // than the spills they cost (measured on the 53/325 mechanism)
   int rreg = opt.maxrreg;
-  const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed &&
+  const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
   if (rreg == 0 && unrolled_rates) rreg = 128;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;

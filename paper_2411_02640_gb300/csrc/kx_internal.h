@@ -69,6 +69,7 @@ struct EmitOptions {
   int part = 0;             // transport: 0 all outputs, 1 viscosity and conductivity, 2 diffusion
   int maxrreg = 0;          // register cap per thread (0: compiler choice)
   int rates_mode = 0;       // 0 auto, 1 unrolled, 2 table driven (large mechanisms)
+  int rates_arith = 0;      // float64-accurate rates: 0/2 double-float (reaction classes), 1 native float64
 };
 
 // Operation counts per point, tallied while emitting (library calls such as

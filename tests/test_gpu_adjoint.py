@@ -111,12 +111,14 @@ def test_adjoint_throughput_and_jacobian_assembly_timing(torch):
     ev[0].record()
     J = jacobian(mech, Tj, pj, Yj)
     ev[1].record()
-    # central differences, h = 1e-6 relative, one column per input
+    # central differences, one column per input; the float64-accurate forward path rounds at about
+    # 1e-12 of the per-point scale (float pairs), so the step that balances truncation (h^2) against
+    # rounding (eps/h) is h ~ eps^(1/3) = 1e-4 relative
     Jfd = torch.empty_like(J)
-    h = 1e-6 * Tj
+    h = 1e-4 * Tj
     Jfd[:, :, 0] = ((mech.production_rates(Tj + h, pj, Yj) - mech.production_rates(Tj - h, pj, Yj)) / (2 * h)).t()
     for j in range(ns):
-        hy = 1e-6 * torch.clamp(Yj[j], min=1e-3)
+        hy = 1e-4 * torch.clamp(Yj[j], min=1e-3)
         Yp, Ym = Yj.clone(), Yj.clone()
         Yp[j] += hy
         Ym[j] -= hy
