@@ -160,6 +160,19 @@ __device__ __forceinline__ double kx_net_rate(float lnRf, double lnrho) {
   return a > 0.0f ? -mag : mag;
 }
 
+// Net rate of progress from ln |R_f| and a = ln(|R_r|/|R_f|) (float32, a
+// rounded once from its float-pair sum), with the signs sf, sr (1: negative)
+// of the two rates: the larger magnitude times 1 - e^-|a| for equal signs
+// (the cancellation near equilibrium resolved from a) or 1 + e^-|a| for
+// opposite signs.
+__device__ __forceinline__ double kx_net_rate_s(float lnRf, float a, int sf, int sr) {
+  const float e = lnRf + fmaxf(a, 0.0f);
+  const float fac = sf == sr ? -expm1f(-fabsf(a)) : 1.0f + __expf(-fabsf(a));
+  const double mag = kx_pow2_scaled(e * KX_LOG2E_F, fac);
+  const int neg = sf == sr ? ((a > 0.0f) != (sf != 0)) : sf;
+  return neg ? -mag : mag;
+}
+
 // ln(Pr/(1+Pr)) and ln(1/(1+Pr)) from ln Pr without overflow (float32).
 __device__ __forceinline__ float kx_ln_pr_ratio(float lnPr) {
   return lnPr < 0.0f ? lnPr - log1pf(__expf(lnPr)) : -log1pf(__expf(-lnPr));
@@ -209,6 +222,14 @@ __device__ __forceinline__ kx_df kx_df_fma(kx_df a, kx_df b, kx_df c) {
   const float pe = __fmaf_rn(a.hi, b.hi, -p);
   const kx_df s = kx_ts(p, c.hi);
   return kx_qts(s.hi, __fadd_rn(s.lo, __fadd_rn(pe, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, c.lo)))));
+}
+// a*b + c without the final renormalisation (inner Horner steps: the next
+// step only needs hi + lo, not |lo| <= ulp(hi)/2)
+__device__ __forceinline__ kx_df kx_df_fma_u(kx_df a, kx_df b, kx_df c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  const kx_df s = kx_ts(p, c.hi);
+  return kx_mk(s.hi, __fadd_rn(s.lo, __fadd_rn(pe, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, c.lo)))));
 }
 __device__ __forceinline__ kx_df kx_df_mul(kx_df a, kx_df b) {
   const float p = __fmul_rn(a.hi, b.hi);
@@ -451,6 +472,18 @@ std::string F(double v) {
   return s[0] == '-' ? "(" + s + ")" : s;
 }
 
+std::string fpair(double v) {
+  const float h = (float)v;
+  const float l = (float)(v - (double)h);
+  return F(h) + "," + F(l);
+}
+
+std::string DFc(double v) { return "kx_mk(" + fpair(v) + ")"; }
+
+// float32-pipe instruction estimates of the double-float primitives (for the
+// operation counts)
+constexpr double kDfAdd = 11, kDfMul = 7, kDfFma = 15, kDfMulf = 5, kDfDiv = 16, kDfExp = 30, kDfLog = 40;
+
 struct Out {
   std::ostringstream o;
   int ind = 1;
@@ -527,6 +560,35 @@ void emit_gibbs64(Out& o, const Mechanism& m, int k, const std::string& flag, Op
   o(fmt("const double g_%d = fma(%s, lnT, fma(%s, iT, %s));", k, sel(flag, -lo[0], -hi[0]).c_str(),
         sel(flag, lo[5], hi[5]).c_str(), h.c_str()));
   c.fp64 += 6;
+}
+
+// G/RT of species k as a float pair: the same polynomial with float-pair
+// immediates (range selected by the flag) and float-pair T, ln T, 1/T.
+void emit_gibbs_df(Out& o, const Mechanism& m, int k, const std::string& flag, OpCounts& c) {
+  const double* lo = &m.a_lo[7 * k];
+  const double* hi = &m.a_hi[7 * k];
+  auto co = [&](const double* a, int n) {
+    switch (n) {
+      case 0: return a[0] - a[6];
+      case 1: return -a[1] / 2.0;
+      case 2: return -a[2] / 6.0;
+      case 3: return -a[3] / 12.0;
+      case 4: return -a[4] / 20.0;
+      case 5: return a[5];
+      default: return -a[0];
+    }
+  };
+  auto dsel = [&](int n) {
+    const double a = co(lo, n), b = co(hi, n);
+    if (a == b) return DFc(a);
+    const float ah = (float)a, bh = (float)b;
+    return fmt("kx_mk(%s ? %s : %s, %s ? %s : %s)", flag.c_str(), F(ah).c_str(), F(bh).c_str(), flag.c_str(),
+               F((float)(a - (double)ah)).c_str(), F((float)(b - (double)bh)).c_str());
+  };
+  std::string h = dsel(4);
+  for (int n = 3; n >= 0; --n) h = fmt("kx_df_fma(%s, Td, %s)", h.c_str(), dsel(n).c_str());
+  o(fmt("const kx_df g_%d = kx_df_fma(%s, lnT, kx_df_fma(%s, iT, %s));", k, dsel(6).c_str(), dsel(5).c_str(), h.c_str()));
+  c.fp32 += 6 * kDfFma + 14;
 }
 
 std::string nasa_flag(const Mechanism& m, int k, const std::map<double, int>& flags) {
@@ -825,45 +887,70 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
   const auto used = species_used(m);
   const auto need_g = gibbs_needed(m);
   const auto flags = tmid_flags(m);
-  o("const double lnT = log(T);");
-  o("const double iT = 1.0 / T;");
-  o("const float lnTf = kx_d2f(lnT), iTf = kx_d2f(iT), Tf = kx_d2f(T);");
-  c.log64 += 1; c.div64 += 1;
+  o("const kx_df Td = kx_d2df_i(T);");
+  o("const kx_df lnT = kx_df_log_d(T);");
+  o("const kx_df iT = kx_df_div(kx_mk(1.0f, 0.0f), Td);");
+  o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi;");
+  c.fp32 += 45 + 12 + kDfDiv;
   bool any_plog = false;
   for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
   if (any_plog) { o("const float lnPf = __logf(kx_d2f(P));"); c.log32 += 1; }
-  o(fmt("const double cM = P * iT * %s;", D(1.0 / R_U).c_str()));
-  std::string sum;
+  o(fmt("const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
+  // y_k = Y_k/W_k and sigma = sum y_k as float pairs; C_k = y_k C_M/sigma
+  std::string s0;
   for (int k = 0; k < m.ns; ++k) {
     o(fmt("const double Yk_%d = Y_[(long long)%d * ld + i];", k, k));
-    o(fmt("const double y_%d = Yk_%d * %s;", k, k, D(1.0 / m.W[k]).c_str()));
-    sum += (k ? " + y_" : "y_") + std::to_string(k);
+    o(fmt("const kx_df y_%d = kx_df_mul(kx_d2df_i(Yk_%d), %s);", k, k, DFc(1.0 / m.W[k]).c_str()));
   }
-  o("const double sig = " + sum + ";");
-  o("if (!(sig > 0.0 && sig < KX_INF)) KX_BAD_POINT");
-  o("const double fC = cM / sig;");
-  o("const double lnfC = kx_log(fC);");
-  o("const float cMf = kx_d2f(cM), fCf = kx_d2f(fC);");
-  c.fp64 += 2 * m.ns + 2; c.div64 += 1; c.log64 += 1;
+  // pairwise sum of the y_k (short dependence chains)
+  std::vector<std::string> terms;
+  for (int k = 0; k < m.ns; ++k) terms.push_back(fmt("y_%d", k));
+  int tmp = 0;
+  while (terms.size() > 1) {
+    std::vector<std::string> next;
+    for (size_t j = 0; j + 1 < terms.size(); j += 2) {
+      o(fmt("const kx_df sg%d = kx_df_add(%s, %s);", tmp, terms[j].c_str(), terms[j + 1].c_str()));
+      next.push_back(fmt("sg%d", tmp++));
+    }
+    if (terms.size() % 2) next.push_back(terms.back());
+    terms = next;
+  }
+  o("const kx_df sig = " + terms[0] + ";");
+  o("if (!(sig.hi > 0.0f && sig.hi < KX_INF_F)) KX_BAD_POINT");
+  o("const kx_df fC = kx_df_div(cM, sig);");
+  o("const kx_df lnfC = kx_df_log(fC);");
+  o("const float cMf = cM.hi, fCf = fC.hi;");
+  c.fp32 += m.ns * (12 + kDfMul + kDfAdd) + kDfDiv + kDfLog;
   bool any_tb = false;
   for (auto& r : m.rx) any_tb |= r.third_body();
   for (int k = 0; k < m.ns; ++k) {
     if (!used[k]) continue;
-    // ln C_k = ln Y_k - ln W_k + ln fC, floored at ln(1e-304) so that an absent species gives 0 rates, not nan
-    o(fmt("const double lnC_%d = fmax(kx_log(Yk_%d) + (lnfC - %s), -700.0);", k, k, D(std::log(m.W[k])).c_str()));
-    o(fmt("const float lnCf_%d = kx_d2f(lnC_%d);", k, k));
-    if (any_tb) o(fmt("const float Cf_%d = kx_d2f(y_%d) * fCf;", k, k));
-    c.log64 += 1; c.fp64 += 2; c.fp32 += 1;
+    // ln |C_k| = ln |Y_k| - ln W_k + ln(C_M/sigma) as a float pair, floored at -700 (absent species:
+    // zero rates, not nan); the sign of C_k is kept apart
+    o(fmt("const long long yb_%d = __double_as_longlong(Yk_%d) & 0x7fffffffffffffffLL;", k, k));
+    o(fmt("kx_df lnC_%d = kx_mk(-700.0f, 0.0f);", k));
+    o(fmt("if (yb_%d >= 0x0010000000000000LL && yb_%d < 0x7ff0000000000000LL) {", k, k));
+    o(fmt("  lnC_%d = kx_df_add(kx_df_log_d(__longlong_as_double(yb_%d)), kx_df_sub(lnfC, %s));", k, k, DFc(std::log(m.W[k])).c_str()));
+    o(fmt("  if (!(lnC_%d.hi > -700.0f)) lnC_%d = kx_mk(-700.0f, 0.0f);", k, k));
+    o("}");
+    o(fmt("const float lnCf_%d = lnC_%d.hi;", k, k));
+    o(fmt("const int ng_%d = __double_as_longlong(Yk_%d) < 0LL;", k, k));
+    if (any_tb) o(fmt("const float Cf_%d = y_%d.hi * fCf;", k, k));
+    c.fp32 += kDfLog + 12 + 2 * kDfAdd + 4;
   }
-  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
+  for (auto& f : flags) {
+    long long b;
+    std::memcpy(&b, &f.first, 8);
+    o(fmt("const bool lo%d = __double_as_longlong(T) < %lldLL;", f.second, b));
+  }
   for (int k = 0; k < m.ns; ++k)
     if (need_g[k]) {
-      emit_gibbs64(o, m, k, nasa_flag(m, k, flags), c);
-      o(fmt("const double mu_%d = g_%d + lnC_%d;", k, k, k));
-      c.fp64 += 1;
+      emit_gibbs_df(o, m, k, nasa_flag(m, k, flags), c);
+      o(fmt("const kx_df mu_%d = kx_df_add(g_%d, lnC_%d);", k, k, k));
+      c.fp32 += kDfAdd;
     }
-  o(fmt("const double lnPRT = %s - lnT;", D(std::log(P_ATM / R_U)).c_str()));
-  c.fp64 += 1;
+  o(fmt("const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
+  c.fp32 += kDfAdd;
   if (!rop)
     for (int k = 0; k < m.ns; ++k) o(fmt("double w_%d = 0.0;", k));
   for (int i = 0; i < m.nr(); ++i) {
@@ -927,14 +1014,33 @@ void emit_rates_mixed(Out& o, const Mechanism& m, bool rop, OpCounts& c) {
       c.fp32 += 1;
     }
     o("const float lnRf = " + lnRf + ";");
+    // signs of prod C^nu' and prod C^nu'' (negative mass fractions)
+    std::string sf = "0", sr = "0";
+    for (auto& e : r.reac) if (e.second % 2) sf += fmt(" ^ ng_%d", e.first);
+    for (auto& e : r.prod) if (e.second % 2) sr += fmt(" ^ ng_%d", e.first);
     if (r.reversible) {
+      // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T)) in float pairs, rounded to float32 once
       const int dn = sum_nu(r);
-      std::string s = nu_sum(r, "mu", c);
-      if (dn != 0) { s = fmt("fma(%s, lnPRT, %s)", D(-dn).c_str(), s.c_str()); c.fp64 += 1; }
-      o("const double q = kx_net_rate(lnRf, " + s + ");");
-      c.exp32 += 2; c.fp32 += 6;
+      std::map<int, int> nu;
+      for (auto& e : r.prod) nu[e.first] += e.second;
+      for (auto& e : r.reac) nu[e.first] -= e.second;
+      std::string acc;
+      for (auto& kv : nu) {
+        if (kv.second == 0) continue;
+        const std::string term = kv.second == 1 || kv.second == -1 ? fmt("mu_%d", kv.first)
+                                                                 : fmt("kx_df_mulf(mu_%d, %s)", kv.first, F(std::abs(kv.second)).c_str());
+        if (acc.empty()) acc = kv.second > 0 ? term : "kx_df_neg(" + term + ")";
+        else acc = fmt("kx_df_%s(%s, %s)", kv.second > 0 ? "add" : "sub", acc.c_str(), term.c_str());
+        c.fp32 += kDfAdd;
+      }
+      if (acc.empty()) acc = "kx_mk(0.0f, 0.0f)";
+      if (dn != 0) { acc = fmt("kx_df_add(%s, kx_df_mulf(lnPRT, %s))", acc.c_str(), F(-dn).c_str()); c.fp32 += kDfAdd + kDfMulf; }
+      o("const float lnra = (" + acc + ").hi;");
+      o("const double q = kx_net_rate_s(lnRf, lnra, " + sf + ", " + sr + ");");
+      c.exp32 += 2; c.fp32 += 10;
     } else {
-      o("const double q = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+      o("const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+      o("const double q = (" + sf + ") ? -q0 : q0;");
       c.exp32 += 1; c.fp32 += 2;
     }
     if (rop) {
@@ -1223,18 +1329,6 @@ void emit_rates_table_mixed(Out& o, Out& g, const Mechanism& m, bool rop, OpCoun
 // species.  Each state's species vectors ({ln |C|, mu} as a float4 and the
 // float-pair accumulators) live in per-thread local arrays, so the kernel
 // compiles in seconds for any mechanism size.
-std::string fpair(double v) {
-  const float h = (float)v;
-  const float l = (float)(v - (double)h);
-  return F(h) + "," + F(l);
-}
-
-std::string DFc(double v) { return "kx_mk(" + fpair(v) + ")"; }
-
-// float32-pipe instruction estimates of the double-float primitives (for the
-// operation counts)
-constexpr double kDfAdd = 11, kDfMul = 7, kDfFma = 15, kDfMulf = 5, kDfDiv = 16, kDfExp = 30, kDfLog = 40;
-
 struct DfClass {
   Kind kind;
   bool rev;
@@ -1276,8 +1370,21 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
     for (int i : d.rx) {
       const Reaction& r = m.rx[i];
       auto er = entries(r.reac), ep = entries(r.prod);
-      for (int k : er) si += std::to_string(k) + ",";
-      for (int k : ep) si += std::to_string(k) + ",";
+      {
+        // entry j: species k | (c << 16), c = the species' net coefficient on its first entry, 0 on
+        // repeats (so that the accumulators are updated once per species)
+        std::vector<int> ek(er);
+        ek.insert(ek.end(), ep.begin(), ep.end());
+        std::map<int, int> net;
+        for (int k : er) net[k] -= 1;
+        for (int k : ep) net[k] += 1;
+        std::set<int> seen;
+        for (int k : ek) {
+          const int cc = seen.count(k) ? 0 : net[k];
+          seen.insert(k);
+          si += std::to_string(k + 65536 * cc) + ",";
+        }
+      }
       si += std::to_string(i) + ",";
       for (int j = E + 1; j < P; ++j) si += "0,";
       double maxeff = r.default_eff;
@@ -1393,14 +1500,30 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
   c.fp32 += 40 + 45 + kDfDiv + 2 * kDfMul + kDfAdd + kDfDiv + kDfLog;
   c.fp32 += ns * (12 + kDfFma) + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
 
-  auto load_species = [&](const DfClass& d, int ci) {
+  // Class loops are software-pipelined: each iteration loads the next
+  // reaction's record and species vectors, and the accumulators of the
+  // previous reaction, before computing its own rate; the previous rate is
+  // added to its accumulators at the end.  Local-memory latency thus hides
+  // behind one reaction's arithmetic.
+  static const char* xyzw[4] = {"x", "y", "z", "w"};
+  auto comp = [&](const char* base, int j) { return fmt("%s%d.%s", base, j / 4, xyzw[j % 4]); };
+  auto spc = [&](const char* base, int j) { return fmt("(%s & 0xffff)", comp(base, j).c_str()); };
+  auto prologue = [&](const DfClass& d, int ci) {
     const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
-    std::string s = fmt("  const int4* sp4 = (const int4*)(kx_s%d + %d * r);", ci, P);
-    o(s);
-    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 s%d = sp4[%d];", q, q));
-    auto comp = [](int j) { static const char* xyzw[4] = {"x", "y", "z", "w"}; return fmt("s%d.%s", j / 4, xyzw[j % 4]); };
-    for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, comp(j).c_str()));
-    if (rop) o(fmt("  const int ri = %s;", comp(E).c_str()));
+    o(fmt("const int4* sp4 = (const int4*)kx_s%d;", ci));
+    for (int q = 0; q < P / 4; ++q) o(fmt("int4 c%d = sp4[%d];", q, q));
+    for (int j = 0; j < E; ++j) o(fmt("float4 v%d = sv[%s];", j, spc("c", j).c_str()));
+  };
+  auto prefetch = [&](const DfClass& d) {
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    o(fmt("  const int rn = r + 1 < %d ? r + 1 : r;", (int)d.rx.size()));
+    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 n%d = sp4[%d * rn + %d];", q, P / 4, q));
+    for (int j = 0; j < E; ++j) o(fmt("  const float4 u%d = sv[%s];", j, spc("n", j).c_str()));
+  };
+  auto advance = [&](const DfClass& d) {
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    for (int q = 0; q < P / 4; ++q) o(fmt("  c%d = n%d;", q, q));
+    for (int j = 0; j < E; ++j) o(fmt("  v%d = u%d;", j, j));
   };
 
   // ---- pre-pass: float32 upper bound U of ln max(|R_f|, |R_r|) over the reactions
@@ -1412,11 +1535,12 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
       const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
       const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
       const int NF = fo ? 7 : tb ? 3 : 2;
+      o("{");
+      ++o.ind;
+      prologue(d, (int)ci);
       o("#pragma unroll 1");
       o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
-      ++o.ind;
-      load_species(d, (int)ci);
-      --o.ind;
+      prefetch(d);
       o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
       o("  const float4 f0 = f[0], f1 = f[1];");
       o("  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
@@ -1440,15 +1564,18 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
         o("  b = -1.0e30f;");
         o("  for (int j = 0; j < e.y; ++j) b = fmaxf(b, fmaf(t[8 * j + 4], lnTf, fmaf(t[8 * j + 6], iTf, t[8 * j + 2])));");
       }
-      for (int j = 0; j < d.nre; ++j) o(fmt("  b += sv[k%d].x;", j));
+      for (int j = 0; j < d.nre; ++j) o(fmt("  b += v%d.x;", j));
       if (d.rev) {
         const int dn = d.npr - d.nre;
         std::string s = dn == 0 ? std::string("0.0f") : fmt("%s * lnPRTf", F(-dn).c_str());
-        for (int j = 0; j < d.nre; ++j) s += fmt(" - sv[k%d].z", j);
-        for (int j = d.nre; j < d.nre + d.npr; ++j) s += fmt(" + sv[k%d].z", j);
+        for (int j = 0; j < d.nre; ++j) s += fmt(" - v%d.z", j);
+        for (int j = d.nre; j < d.nre + d.npr; ++j) s += fmt(" + v%d.z", j);
         o("  b += fmaxf(" + s + ", 0.0f);");
       }
       o("  U = fmaxf(U, b);");
+      advance(d);
+      o("}");
+      --o.ind;
       o("}");
       c.fp32 += d.rx.size() * (8.0 + 2 * (d.nre + d.npr));
     }
@@ -1464,12 +1591,22 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
     const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
     const int NF = fo ? 7 : tb ? 3 : 2;
     const int E = d.nre + d.npr;
-    o(fmt("// class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
+    o(fmt("{   // class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
+    ++o.ind;
+    prologue(d, (int)ci);
+    if (!rop) {
+      std::string pdecl = "int";
+      for (int j = 0; j < E; ++j) pdecl += fmt("%s p%d = 0", j ? "," : "", j);
+      o(pdecl + ";   // entries of the previous reaction (coefficient 0: nothing to add)");
+      o("kx_df qp = kx_mk(0.0f, 0.0f);");
+    }
     o("#pragma unroll 1");
     o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
-    ++o.ind;
-    load_species(d, (int)ci);
-    --o.ind;
+    if (!rop)
+      for (int j = 0; j < E; ++j) o(fmt("  const kx_df wl%d = w[p%d & 0xffff];", j, j));
+    prefetch(d);
+    for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
+    if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
     o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
     o("  const float4 f0 = f[0], f1 = f[1];");
     o("  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
@@ -1535,7 +1672,6 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
       c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
     }
     // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
-    for (int j = 0; j < E; ++j) o(fmt("  const float4 v%d = sv[k%d];", j, j));
     o(rop ? "  kx_df lf = lk;" : "  kx_df lf = kx_df_sub(lk, lnS);");
     for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add(lf, kx_mk(v%d.x, v%d.y));", j, j));
     std::string sfx = "0", srx = "0";
@@ -1578,9 +1714,20 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
       o("  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
       c.fp64 += d.rx.size();
     } else {
-      for (int j = 0; j < E; ++j) o(fmt("  w[k%d] = kx_df_%s(w[k%d], q);", j, j < d.nre ? "sub" : "add", j));
-      c.fp32 += d.rx.size() * E * kDfAdd;
+      // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
+      for (int j = 0; j < E; ++j)
+        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add(wl%d, kx_df_mulf(qp, kx_i2f(cj))); }", j, j, j));
+      o("  qp = q;");
+      for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
+      c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
     }
+    advance(d);
+    o("}");
+    if (!rop)
+      for (int j = 0; j < E; ++j)
+        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add(w[kk], kx_df_mulf(qp, kx_i2f(cj))); } }",
+              j, j));
+    --o.ind;
     o("}");
   }
   if (!rop) {
@@ -2008,6 +2155,29 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
   o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
+  if (two_arrays) {
+    // float64 accuracy: den_k = sum_j a_kj X_j (1 + u_k v_j)^2 with w = 1 + u_k v_j formed per pair
+    // (three products and one accumulation per pair; even and odd j in two chains)
+    const std::string ONE1 = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : "1.0";
+    o(fmt("  %s s0 = %s, t0 = %s;", md.ty, ZERO.c_str(), ZERO.c_str()));
+    o(fmt("  const %s* a = kx_wa + %d * k;", md.st, ns));
+    o("  #pragma unroll 2");
+    o(fmt("  for (int j = 0; j + 1 < %d; j += 2) {", ns));
+    o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
+    o(fmt("    const %s xa = %s, va = %s, xb = %s, vb = %s;", md.ty, ld(fmt("sX[j * %d + t]", B)).c_str(),
+          ld(fmt("sZ1[j * %d + t]", B)).c_str(), ld(fmt("sX[(j + 1) * %d + t]", B)).c_str(), ld(fmt("sZ1[(j + 1) * %d + t]", B)).c_str()));
+    o(fmt("    const %s wa = %s, wb = %s;", md.ty, FMA("u", "va", ONE1).c_str(), FMA("u", "vb", ONE1).c_str()));
+    o(fmt("    s0 = %s;", FMA(MUL("A", "xa"), MUL("wa", "wa"), "s0").c_str()));
+    o(fmt("    t0 = %s;", FMA(MUL("Ab", "xb"), MUL("wb", "wb"), "t0").c_str()));
+    o("  }");
+    if (ns % 2) {
+      o(fmt("  { const %s A = %s, xa = %s, va = %s;", md.ty, ld(fmt("a[%d]", ns - 1)).c_str(), ld(fmt("sX[%d * %d + t]", ns - 1, B)).c_str(),
+            ld(fmt("sZ1[%d * %d + t]", ns - 1, B)).c_str()));
+      o(fmt("    const %s wa = %s;", md.ty, FMA("u", "va", ONE1).c_str()));
+      o(fmt("    s0 = %s; }", FMA(MUL("A", "xa"), MUL("wa", "wa"), "s0").c_str()));
+    }
+    o(fmt("  const %s den = %s;", md.ty, FMA("t0", ONE1, "s0").c_str()));
+  } else {
   // two partial sums per product (even and odd j): six independent accumulation chains
   o(fmt("  %s s0 = %s, s1 = %s, s2 = %s, t0 = %s, t1 = %s, t2 = %s;", md.ty, ZERO.c_str(), ZERO.c_str(), ZERO.c_str(),
         ZERO.c_str(), ZERO.c_str(), ZERO.c_str()));
@@ -2036,6 +2206,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o(fmt("  s0 = %s; s1 = %s; s2 = %s;", FMA("t0", ONE, "s0").c_str(), FMA("t1", ONE, "s1").c_str(), FMA("t2", ONE, "s2").c_str()));
   const std::string two_s1 = md.kind == TrMode::DF ? "kx_mk(2.f * s1.hi, 2.f * s1.lo)" : md.kind == TrMode::F32 ? "2.0f * s1" : "2.0 * s1";
   o(fmt("  const %s den = %s;", md.ty, FMA("u", FMA("u", "s2", two_s1), "s0").c_str()));
+  }
   o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD(ld(fmt("sX[k * %d + t]", B))).c_str(), TOD(MUL("u", "u")).c_str(),
         TOD("den").c_str()));
   o("}");
@@ -2056,7 +2227,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   std::string vec, pre, take, pair_exp;
   if (md.kind == TrMode::DF) {
     vec = "float4";
-    pair_exp = "const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma(kx_df_fma(kx_df_fma(kx_mk(c2.x, c2.y), L, kx_mk(c1.z, c1.w)), L, "
+    pair_exp = "const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(c2.x, c2.y), L, kx_mk(c1.z, c1.w)), L, "
                "kx_mk(c1.x, c1.y)), L, kx_mk(c0.z, c0.w)), L, kx_mk(c0.x, c0.y)));";
   } else if (md.kind == TrMode::F64) {
     vec = "double2";
@@ -2162,29 +2333,36 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
   const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && opt.rates_arith != 1;
-  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates;
+  const bool table_sel = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
+  const bool mixed_unrolled = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && opt.mixed && !table_sel;
+  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates && !mixed_unrolled;
   // table-driven float64 rate kernels take their exponentials from kx_exp_r (error ~2e-12 against
   // a 1e-10 bar); the unrolled ones keep kx_exp, whose short inline sequence keeps compile time
   // of the straight-line code in check
   const bool table_rates = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
   const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates && !df_rates;
-  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates;
+  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates || mixed_unrolled;
   s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
   s << "#define KX_TDF " << tdf << "\n";
-  s << "#define KX_TDFR " << df_rates << "\n";
+  s << "#define KX_TDFR " << (df_rates || mixed_unrolled) << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
   // a register cap is expressed as a minimum number of resident blocks (ptxas
-  // ignores --maxrregcount for kernels that carry launch bounds)
-  // the unrolled float64 rate kernels run best at 128 registers (four blocks of 128 per SM):
-  // the extra warps hide the latency of the exp tables and dependent float64 chains better
-  // than the spills they cost (measured on the 53/325 mechanism)
+  // ignores --maxrregcount for kernels that carry launch bounds).  Defaults,
+  // measured on the 53/325 mechanism: the unrolled rate kernels (native
+  // float64 and mixed) run best at 128 registers (four blocks of 128 per SM):
+  // the extra warps hide instruction fetch, table and dependence latency
+  // better than the spills they cost; the viscosity kernels and the float32
+  // diffusion kernel, whose residency is set by shared memory, run best with
+  // the compiler allowed 128 registers (more independent chains in flight);
+  // the float-pair diffusion and rate kernels are left to the compiler.
   int rreg = opt.maxrreg;
-  const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && !df_rates &&
+  const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
   if (rreg == 0 && unrolled_rates) rreg = 128;
+  if (rreg == 0 && kind == KernelKind::Transport && (opt.part == 1 || opt.mixed)) rreg = 128;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;
