@@ -1938,31 +1938,46 @@ void emit_vjp64(Out& o, const Mechanism& m, OpCounts& c) {
 }
 
 // ------------------------------------------------------------------ thermo
+// Mixture cp and h in float-pair arithmetic on the float32 pipe (float64
+// accuracy; the NASA polynomials need no float64 pipe): per species two
+// Horner evaluations in T with float-pair coefficients of the range given by
+// T < T_mid, weighted by Y_k R/W_k.
 void emit_thermo(Out& o, const Mechanism& m, OpCounts& c) {
   const auto flags = tmid_flags(m);
-  for (auto& f : flags) o(fmt("const bool lo%d = T < %s;", f.second, D(f.first).c_str()));
-  o("const double iT = 1.0 / T;");
-  o("double cp = 0.0, hs = 0.0;");
-  c.div64 += 1;
+  for (auto& f : flags) {
+    long long b;
+    std::memcpy(&b, &f.first, 8);
+    o(fmt("const bool lo%d = __double_as_longlong(T) < %lldLL;", f.second, b));
+  }
+  o("const kx_df Td = kx_d2df_i(T);");
+  o("const kx_df iT = kx_df_div(kx_mk(1.0f, 0.0f), Td);");
+  o("kx_df cp = kx_mk(0.0f, 0.0f), hs = kx_mk(0.0f, 0.0f);");
+  c.fp32 += 12 + kDfDiv;
+  auto dsel = [&](const std::string& fl, double a, double b) {
+    if (a == b) return DFc(a);
+    const float ah = (float)a, bh = (float)b;
+    return fmt("kx_mk(%s ? %s : %s, %s ? %s : %s)", fl.c_str(), F(ah).c_str(), F(bh).c_str(), fl.c_str(),
+               F((float)(a - (double)ah)).c_str(), F((float)(b - (double)bh)).c_str());
+  };
   for (int k = 0; k < m.ns; ++k) {
     const std::string fl = nasa_flag(m, k, flags);
     const double* lo = &m.a_lo[7 * k];
     const double* hi = &m.a_hi[7 * k];
     // cp/R = a0 + a1 T + a2 T^2 + a3 T^3 + a4 T^4
-    std::string cp = sel(fl, lo[4], hi[4]);
-    for (int n = 3; n >= 0; --n) cp = fmt("fma(%s, T, %s)", cp.c_str(), sel(fl, lo[n], hi[n]).c_str());
+    std::string cpk = dsel(fl, lo[4], hi[4]);
+    for (int n = 3; n >= 0; --n) cpk = fmt("kx_df_fma(%s, Td, %s)", cpk.c_str(), dsel(fl, lo[n], hi[n]).c_str());
     // H/RT = a0 + a1/2 T + a2/3 T^2 + a3/4 T^3 + a4/5 T^4 + a5/T
-    std::string h = sel(fl, lo[4] / 5.0, hi[4] / 5.0);
-    for (int n = 3; n >= 0; --n) h = fmt("fma(%s, T, %s)", h.c_str(), sel(fl, lo[n] / (n + 1), hi[n] / (n + 1)).c_str());
-    h = fmt("fma(%s, iT, %s)", sel(fl, lo[5], hi[5]).c_str(), h.c_str());
-    o(fmt("{ const double yr = Y_[(long long)%d * ld + i] * %s;", k, D(R_U / m.W[k]).c_str()));
-    o(fmt("  cp = fma(yr, %s, cp);", cp.c_str()));
-    o(fmt("  hs = fma(yr, %s, hs); }", h.c_str()));
-    c.fp64 += 12;
+    std::string h = dsel(fl, lo[4] / 5.0, hi[4] / 5.0);
+    for (int n = 3; n >= 0; --n) h = fmt("kx_df_fma(%s, Td, %s)", h.c_str(), dsel(fl, lo[n] / (n + 1), hi[n] / (n + 1)).c_str());
+    h = fmt("kx_df_fma(%s, iT, %s)", dsel(fl, lo[5], hi[5]).c_str(), h.c_str());
+    o(fmt("{ const kx_df yr = kx_df_mul(kx_d2df_i(Y_[(long long)%d * ld + i]), %s);", k, DFc(R_U / m.W[k]).c_str()));
+    o(fmt("  cp = kx_df_fma(yr, %s, cp);", cpk.c_str()));
+    o(fmt("  hs = kx_df_fma(yr, %s, hs); }", h.c_str()));
+    c.fp32 += 12 + kDfMul + 11 * kDfFma + 28;
   }
-  o("out0_[i] = cp;");
-  o("out1_[i] = hs * T;");
-  c.fp64 += 1;
+  o("out0_[i] = kx_df2d(cp);");
+  o("out1_[i] = kx_df2d(kx_df_mul(hs, Td));");
+  c.fp64 += 2;
 }
 
 // ------------------------------------------------------------------ transport
@@ -2224,22 +2239,21 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   // the next pair's coefficients are loaded one iteration ahead (the table
   // carries one zero pair of padding), so their latency hides behind the
   // current pair's arithmetic
-  std::string vec, pre, take, pair_exp;
-  if (md.kind == TrMode::DF) {
-    vec = "float4";
-    pair_exp = "const kx_df e = kx_df_exp(kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(c2.x, c2.y), L, kx_mk(c1.z, c1.w)), L, "
-               "kx_mk(c1.x, c1.y)), L, kx_mk(c0.z, c0.w)), L, kx_mk(c0.x, c0.y)));";
-  } else if (md.kind == TrMode::F64) {
-    vec = "double2";
-    pair_exp = "const double e = kx_exp(fma(fma(fma(fma(c2.x, L, c1.y), L, c1.x), L, c0.y), L, c0.x));";
-  } else {
-    vec = "float2";
-    pair_exp = "const float e = exp2f(fmaf(fmaf(fmaf(fmaf(c2.x, L, c1.y), L, c1.x), L, c0.y), L, c0.x));";
-  }
+  std::string vec;
+  // exponential of one pair's polynomial, coefficients in the float4/double2/float2 triple (x, y, z)
+  auto pexp = [&](const char* e, const char* x, const char* y, const char* z) {
+    if (md.kind == TrMode::DF)
+      return fmt("const kx_df %s = kx_df_exp(kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
+                 "kx_mk(%s.x, %s.y)), L, kx_mk(%s.z, %s.w)), L, kx_mk(%s.x, %s.y)));",
+                 e, z, z, y, y, y, y, x, x, x, x);
+    if (md.kind == TrMode::F64)
+      return fmt("const double %s = kx_exp(fma(fma(fma(fma(%s.x, L, %s.y), L, %s.x), L, %s.y), L, %s.x));", e, z, y, y, x, x);
+    return fmt("const float %s = exp2f(fmaf(fmaf(fmaf(fmaf(%s.x, L, %s.y), L, %s.x), L, %s.y), L, %s.x));", e, z, y, y, x, x);
+  };
+  vec = md.kind == TrMode::DF ? "float4" : md.kind == TrMode::F64 ? "double2" : "float2";
   o(fmt("const %s* cq = (const %s*)kx_dc;", vec.c_str(), vec.c_str()));
   o(fmt("%s n0 = cq[0], n1 = cq[1], n2 = cq[2];", vec.c_str()));
-  take = fmt("const %s c0 = n0, c1 = n1, c2 = n2; cq += 3; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];", vec.c_str());
-  pair_exp = take + "\n      " + pair_exp;
+  const std::string take = fmt("const %s c0 = n0, c1 = n1, c2 = n2; cq += 3; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];", vec.c_str());
   if (opt.diff_mode == 2) {
     o("#pragma unroll 1");
     o(fmt("for (int k = 0; k < %d; ++k) {", ns));
@@ -2247,25 +2261,43 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("  #pragma unroll 2");
     o(fmt("  for (int j = 0; j < %d; ++j) {", ns));
     o("    if (j == k) continue;");
-    o("    " + pair_exp);
+    o("    " + take);
+    o("    " + pexp("e", "c0", "c1", "c2"));
     o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
     o("  }");
     o("  " + st(fmt("sS[k * %d + t]", B), "Sk"));
     o("}");
     count_fma(ns * (ns - 1) * 5.0); count_exp(ns * (ns - 1.0));
   } else {
+    // two pairs per iteration with their own row accumulators (four pairs in flight with the
+    // unroll); the coefficient stream is read one pair ahead
     o("#pragma unroll 1");
     o(fmt("for (int k = 0; k < %d; ++k) {", ns - 1));
-    o(fmt("  %s Sk = %s;", md.ty, ld(fmt("sS[k * %d + t]", B)).c_str()));
+    o(fmt("  %s Sk = %s, Sk1 = %s;", md.ty, ld(fmt("sS[k * %d + t]", B)).c_str(), ZERO.c_str()));
     o(fmt("  const %s Xk = %s;", md.ty, ld(fmt("sX[k * %d + t]", B)).c_str()));
+    o("  int j = k + 1;");
     o("  #pragma unroll 2");
-    o(fmt("  for (int j = k + 1; j < %d; ++j) {", ns));
-    o("    " + pair_exp);
+    o(fmt("  for (; j + 1 < %d; j += 2) {", ns));
+    o(fmt("    const %s a0 = n0, a1 = n1, a2 = n2, b0 = cq[3], b1 = cq[4], b2 = cq[5];", vec.c_str()));
+    o("    cq += 6; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];");
+    o("    " + pexp("ea", "a0", "a1", "a2"));
+    o("    " + pexp("eb", "b0", "b1", "b2"));
+    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "ea", "Sk") + ";");
+    o("    Sk1 = " + FMA(ld(fmt("sX[(j + 1) * %d + t]", B)), "eb", "Sk1") + ";");
+    o(fmt("    const %s Sa = %s;", md.ty, FMA("Xk", "ea", ld(fmt("sS[j * %d + t]", B))).c_str()));
+    o(fmt("    const %s Sb = %s;", md.ty, FMA("Xk", "eb", ld(fmt("sS[(j + 1) * %d + t]", B))).c_str()));
+    o("    " + st(fmt("sS[j * %d + t]", B), "Sa"));
+    o("    " + st(fmt("sS[(j + 1) * %d + t]", B), "Sb"));
+    o("  }");
+    o(fmt("  if (j < %d) {", ns));
+    o("    " + take);
+    o("    " + pexp("e", "c0", "c1", "c2"));
     o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
     o(fmt("    const %s Sj = %s;", md.ty, FMA("Xk", "e", ld(fmt("sS[j * %d + t]", B))).c_str()));
     o("    " + st(fmt("sS[j * %d + t]", B), "Sj"));
     o("  }");
-    o("  " + st(fmt("sS[k * %d + t]", B), "Sk"));
+    const std::string ONE2 = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0";
+    o("  " + st(fmt("sS[k * %d + t]", B), FMA("Sk1", ONE2, "Sk")));
     o("}");
     count_fma(ns * (ns - 1) / 2.0 * 6); count_exp(ns * (ns - 1) / 2.0);
   }
@@ -2341,28 +2373,30 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   // of the straight-line code in check
   const bool table_rates = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
   const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates && !df_rates;
-  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates || mixed_unrolled;
+  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates || mixed_unrolled ||
+                   kind == KernelKind::Thermo;
   s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
   s << "#define KX_TDF " << tdf << "\n";
-  s << "#define KX_TDFR " << (df_rates || mixed_unrolled) << "\n";
+  s << "#define KX_TDFR " << (df_rates || mixed_unrolled || kind == KernelKind::Thermo) << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
   // a register cap is expressed as a minimum number of resident blocks (ptxas
   // ignores --maxrregcount for kernels that carry launch bounds).  Defaults,
-  // measured on the 53/325 mechanism: the unrolled rate kernels (native
-  // float64 and mixed) run best at 128 registers (four blocks of 128 per SM):
-  // the extra warps hide instruction fetch, table and dependence latency
-  // better than the spills they cost; the viscosity kernels and the float32
-  // diffusion kernel, whose residency is set by shared memory, run best with
-  // the compiler allowed 128 registers (more independent chains in flight);
-  // the float-pair diffusion and rate kernels are left to the compiler.
+  // measured on the 53/325 mechanism (2^20 states): the unrolled native
+  // float64 rate kernel runs best at 128 registers and the unrolled mixed one
+  // at 96 (more resident warps hide instruction fetch, table and dependence
+  // latency better than the spills they cost); the float-pair rate kernel at
+  // 128 (four blocks: its pipelined loops keep two reactions' operands live);
+  // the transport kernels, whose residency is set by shared memory, with the
+  // compiler allowed 128 registers (more independent chains in flight).
   int rreg = opt.maxrreg;
   const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
-  if (rreg == 0 && unrolled_rates) rreg = 128;
-  if (rreg == 0 && kind == KernelKind::Transport && (opt.part == 1 || opt.mixed)) rreg = 128;
+  if (rreg == 0 && unrolled_rates) rreg = opt.mixed ? 96 : 128;
+  if (rreg == 0 && df_rates) rreg = 128;
+  if (rreg == 0 && kind == KernelKind::Transport) rreg = 128;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;
