@@ -142,6 +142,29 @@ kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const doub
 kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                   const double* v, double* gT, double* gY, int64_t n, void* stream);
 
+/* Bytes of the library's static device scratch array used by
+ * kx_production_rates_noalloc (one array per device). */
+#define KX_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
+
+/* Net production rates wdot[N_s][ld] with the float-pair (float64-accurate)
+ * arithmetic of kx_production_rates, launched without any device allocation
+ * by the call or by the driver on its behalf: the per-state species vectors
+ * (24 N_s bytes per resident thread) live in a file-scope static __device__
+ * array of KX_NOALLOC_SCRATCH_BYTES instead of local memory.  Its address is
+ * taken once per device (cudaGetSymbolAddress) and the kernel is compiled and
+ * loaded when the handle is loaded on that device, so a call only enqueues:
+ * usable inside CUDA graph capture and allocation-free serving loops.  The
+ * grid is sized so that its threads fit the array (grid-stride over the
+ * points); eager calls on one device are ordered through a library event
+ * because they share the array (a call captured into a CUDA graph is not:
+ * the caller keeps captured calls from overlapping other no-alloc calls of
+ * the device).  Pointers, layout, NaN rules and errors as
+ * kx_production_rates; KX_ERR_UNSUPPORTED if one block of threads does not
+ * fit the array (more than ~43,000 species).  The paper has no counterpart:
+ * this is runtime plumbing around its method. */
+kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                      double* wdot, int64_t n, void* stream);
+
 /* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
  * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
  * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp".  Any output pointer may be

@@ -241,6 +241,32 @@ kx_status launch(kx_mech* h, const char* name, void** args, int64_t n, void* str
   return KX_OK;
 }
 
+// Scratch of kx_production_rates_noalloc: a file-scope device array, its
+// address taken once per device, and one event per device that orders the
+// calls sharing it.
+static __device__ __align__(256) unsigned char kx_noalloc_scratch[KX_NOALLOC_SCRATCH_BYTES];
+
+struct NoAllocDevice {
+  std::once_flag once;
+  void* scratch = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaError_t err = cudaSuccess;
+};
+constexpr int kMaxDevices = 64;
+NoAllocDevice g_noalloc[kMaxDevices];
+
+kx_status noalloc_device(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(KX_ERR_UNSUPPORTED, "device index out of range");
+  NoAllocDevice& d = g_noalloc[dev];
+  std::call_once(d.once, [&] {
+    d.err = cudaGetSymbolAddress(&d.scratch, kx_noalloc_scratch);
+    if (d.err == cudaSuccess) d.err = cudaEventCreateWithFlags(&d.done, cudaEventDisableTiming);
+  });
+  if (d.err != cudaSuccess) return cuda_fail(d.err, "no-alloc scratch setup");
+  *out = &d;
+  return KX_OK;
+}
+
 kx_status check_state(kx_mech* h, const double* T, const double* p, const double* Y, int64_t ld, int64_t n) {
   if (!h) return fail(KX_ERR_ARG, "null handle");
   if (n < 0) return fail(KX_ERR_ARG, "negative point count");
@@ -299,6 +325,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
       {"thermo", kx::KernelKind::Thermo, false, 0},       {"visc_fp64", kx::KernelKind::Transport, false, 1},
       {"diff_fp64", kx::KernelKind::Transport, false, 2}, {"visc_mixed", kx::KernelKind::Transport, true, 1},
       {"diff_mixed", kx::KernelKind::Transport, true, 2}, {"vjp", kx::KernelKind::Vjp, false, 0},
+      {"wdot_fp64_noalloc", kx::KernelKind::Wdot, false, 0},
   };
   for (const Spec& sp : specs) {
     std::unique_ptr<Kernel> k(new Kernel());
@@ -314,6 +341,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.maxrreg = h->opt.maxrreg;
     k->eopt.rates_mode = h->opt.rates_mode;
     k->eopt.rates_arith = h->opt.rates_arith;
+    k->eopt.scratch = std::strcmp(sp.name, "wdot_fp64_noalloc") == 0;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
       const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);
@@ -343,11 +371,18 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     for (auto& t : th) t.join();
     for (size_t i = 0; i < st.size(); ++i)
       if (st[i] != KX_OK) return fail(st[i], msg[i]);
-    if (!h->opt.compile_only)
+    if (!h->opt.compile_only) {
       for (Kernel* k : eager) {
         s = ensure_ready(h.get(), *k);
         if (s != KX_OK) return s;
       }
+      // the no-alloc call's scratch address and ordering event, so that the call itself only enqueues
+      int dev = 0;
+      cudaGetDevice(&dev);
+      NoAllocDevice* nd = nullptr;
+      s = noalloc_device(dev, &nd);
+      if (s != KX_OK) return s;
+    }
   }
   *out = h.release();
   return KX_OK;
@@ -379,6 +414,48 @@ kx_status kx_production_rates(kx_handle h, const double* T, const double* p, con
   long long ldl = ld, nl = n;
   void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
   return launch(h, precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed", args, n, stream);
+}
+
+kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
+                                      double* wdot, int64_t n, void* stream) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (n > 0 && !wdot) return fail(KX_ERR_ARG, "null output");
+  if (n == 0) return KX_OK;
+  if (h->opt.compile_only) return fail(KX_ERR_UNSUPPORTED, "handle was loaded with compile_only");
+  Kernel* k = find_kernel(h, "wdot_fp64_noalloc");
+  s = ensure_ready(h, *k);
+  if (s != KX_OK) return s;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  NoAllocDevice* nd = nullptr;
+  s = noalloc_device(dev, &nd);
+  if (s != KX_OK) return s;
+  const int B = k->eopt.block;
+  const int64_t fit = (int64_t)(KX_NOALLOC_SCRATCH_BYTES / (size_t)kx::rates_scratch_per_thread(h->m)) / B;
+  if (fit < 1) return fail(KX_ERR_UNSUPPORTED, "one block of the rate kernel does not fit the no-alloc scratch");
+  const int64_t want = (n + B - 1) / B;
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(want, (int64_t)k->max_blocks), fit);
+  long long ldl = ld, nl = n, nthr = (long long)grid * B;
+  unsigned char* scr = (unsigned char*)nd->scratch;
+  void* args[] = {&T, &p, &Y, &ldl, &wdot, &scr, &nthr, &nl};
+  // eager calls are ordered through the device's event; inside stream capture the graph's own
+  // dependencies order the captured launch (an event recorded outside a capture cannot be waited on)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  const bool order = cap == cudaStreamCaptureStatusNone;
+  if (order) {
+    e = cudaStreamWaitEvent((cudaStream_t)stream, nd->done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  e = cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(B), args, k->smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
+  if (order) {
+    e = cudaEventRecord(nd->done, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  }
+  return KX_OK;
 }
 
 kx_status kx_rates_of_progress(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* q,

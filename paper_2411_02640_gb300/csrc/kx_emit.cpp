@@ -411,6 +411,12 @@ __device__ __forceinline__ kx_df kx_df_exp_s(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+// Element k of a per-thread vector kept in global scratch at stride s.
+template <typename V> struct kx_strided {
+  V* p;
+  long long s;
+  __device__ __forceinline__ V& operator[](int k) const { return p[(long long)k * s]; }
+};
 // S ln2 as a float pair (exact product terms for |S| < 2^11)
 __device__ __forceinline__ kx_df kx_df_ln2_mul(int S) {
   const float sf = __fsub_rn(__int_as_float(0x4b400000 + S), KX_RND_F);
@@ -1344,7 +1350,7 @@ std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
   return e;
 }
 
-void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts& c) {
+void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
   const int ns = m.ns;
   // ---- classes and their tables
   std::vector<DfClass> cls;
@@ -1456,8 +1462,15 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, bool rop, OpCounts&
   if (any_plog) o("const kx_df lnP = kx_df_log_d(P);");
   o(fmt("const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
   o(fmt("const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
-  o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k (pair)}", ns));
-  if (!rop) o(fmt("kx_df w[%d];", ns));
+  if (opt.scratch && !rop) {
+    // species vectors in the caller's global scratch, element k of this thread at k * nthr + gtid
+    o("const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;");
+    o("const kx_strided<float4> sv{(float4*)kx_scr + gtid, nthr};   // {ln |C_k| (pair), mu_k (pair)}");
+    o(fmt("const kx_strided<kx_df> w{(kx_df*)(kx_scr + (long long)%d * 16 * nthr) + gtid, nthr};", ns));
+  } else {
+    o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k (pair)}", ns));
+    if (!rop) o(fmt("kx_df w[%d];", ns));
+  }
   o("kx_df sig = kx_mk(0.0f, 0.0f);");
   o(fmt("for (int k = 0; k < %d; ++k) sig = kx_df_fma(kx_d2df_i(Y_[(long long)k * ld + i]), KX_PF(kx_iwf + 2 * k), sig);", ns));
   o("if (!(sig.hi > 0.0f && sig.hi < KX_INF_F)) KX_BAD_POINT");
@@ -2333,9 +2346,10 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
     case KernelKind::Rop: {
       const bool rop = kind == KernelKind::Rop;
       outs = "double* __restrict__ out_";
+      if (opt.scratch && !rop) outs += ", unsigned char* __restrict__ kx_scr, long long nthr";
       nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);
       const bool table = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
-      if (!opt.mixed && opt.rates_arith != 1) emit_rates_class_df(body, globals, m, rop, c);
+      if (!opt.mixed && (opt.rates_arith != 1 || opt.scratch)) emit_rates_class_df(body, globals, m, opt, rop, c);
       else if (table && opt.mixed) emit_rates_table_mixed(body, globals, m, rop, c);
       else if (table) emit_rates_table64(body, globals, m, rop, c);
       else if (opt.mixed) emit_rates_mixed(body, m, rop, c);
@@ -2364,7 +2378,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && opt.rates_arith != 1;
+  const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && (opt.rates_arith != 1 || opt.scratch);
   const bool table_sel = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
   const bool mixed_unrolled = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && opt.mixed && !table_sel;
   const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates && !mixed_unrolled;

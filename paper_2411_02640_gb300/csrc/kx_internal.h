@@ -70,6 +70,8 @@ struct EmitOptions {
   int maxrreg = 0;          // register cap per thread (0: compiler choice)
   int rates_mode = 0;       // 0 auto, 1 unrolled, 2 table driven (large mechanisms)
   int rates_arith = 0;      // float64-accurate rates: 0/2 double-float (reaction classes), 1 native float64
+  bool scratch = false;     // float-pair rates: species vectors in a global scratch array passed by the
+                            // caller (strided by the grid's thread count) instead of local memory
 };
 
 // Operation counts per point, tallied while emitting (library calls such as
@@ -81,6 +83,10 @@ struct OpCounts {
 // CUDA C++ source of one kernel, entry point named `entry`.
 std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
                         OpCounts* counts);
+
+// Global scratch bytes per thread of the float-pair rate kernel built with
+// EmitOptions::scratch ({ln |C|, mu} float4 and a float-pair accumulator per species).
+inline int rates_scratch_per_thread(const Mechanism& m) { return 24 * m.ns; }
 
 // Dynamic shared memory per thread that a kernel of this kind needs.
 int transport_smem_per_thread(const Mechanism& m, bool mixed, int part);

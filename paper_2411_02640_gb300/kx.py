@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
         L.kx_mechanism_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double)]
         L.kx_production_rates.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
+        L.kx_production_rates_noalloc.argtypes = [vp, dp, dp, dp, i64, dp, i64, vp]
         L.kx_rates_of_progress.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_thermo.argtypes = [vp, dp, dp, dp, i64, dp, dp, i64, vp]
         L.kx_transport.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, ctypes.c_int, vp]
@@ -155,6 +156,14 @@ class Mechanism:
         assert out.shape[0] == self.n_species and (n == 0 or out.stride(0) == ld)
         _check(lib().kx_production_rates(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _PREC[precision],
                                           _stream(stream)))
+        return out
+
+    def production_rates_noalloc(self, T, p, Y, out, stream=None):
+        """kx_production_rates_noalloc: float64-accurate production rates into a
+        preallocated ``out`` with no device allocation by the call."""
+        n, ld = self._state(T, p, Y)
+        assert out.shape[0] == self.n_species and (n == 0 or out.stride(0) == ld)
+        _check(lib().kx_production_rates_noalloc(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _stream(stream)))
         return out
 
     def rates_of_progress(self, T, p, Y, out=None, precision="fp64", stream=None):
