@@ -182,6 +182,33 @@ kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts);
  * kernel that a profile was taken of. */
 kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash);
 
+/* Outputs of kx_evaluate_host (bit mask). */
+#define KX_OUT_WDOT 1
+#define KX_OUT_THERMO 2
+#define KX_OUT_TRANSPORT 4
+
+/* Device bytes per state that kx_evaluate_host stages per chunk slot (two
+ * slots are used): inputs, and the outputs selected by `outputs`. */
+int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
+
+/* Production rates, thermo and/or transport for states held in HOST memory
+ * (pinned for asynchronous copies), pipelined in chunks over two streams:
+ * while one chunk's kernels run on one stream, the next chunk's inputs are
+ * copied in and the previous chunk's outputs copied out on the other, so the
+ * host<->device copies overlap the arithmetic.  T, p [n], Y [N_s][ld] are
+ * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
+ * are host outputs, those not selected by `outputs` may be NULL.
+ * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk
+ * is the largest that fits two slots of kx_evaluate_host_bytes_per_state
+ * bytes per state (at most `max_chunk` states when max_chunk > 0).  Returns
+ * after enqueueing on stream_a and stream_b; the caller synchronises both.
+ * Arithmetic and error rules as the single calls.  The paper has no
+ * counterpart: this is host IO plumbing around its method. */
+kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* wdot,
+                           double* cp, double* hmass, double* mu, double* lambda, double* Dk, int64_t ldo, int64_t n,
+                           kx_precision precision, int outputs, void* workspace, size_t workspace_bytes,
+                           int64_t max_chunk, void* stream_a, void* stream_b);
+
 /* Copy `rows` rows of n float64 values between host (pinned or pageable)
  * and device buffers with leading dimensions dst_ld and src_ld (in
  * elements), asynchronously on `stream`, in one call: staging of strided

@@ -12,6 +12,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -554,6 +555,68 @@ kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts) {
   const kx::OpCounts& c = find_kernel(h, kernel)->ops;
   const double v[8] = {c.fp64, c.fp32, c.exp64, c.log64, c.div64, c.exp32, c.log32, c.div32};
   std::memcpy(counts, v, sizeof v);
+  return KX_OK;
+}
+
+int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs) {
+  if (!h) return 0;
+  const int64_t ns = h->m.ns;
+  int64_t v = 2 + ns;                                   // T, p, Y
+  if (outputs & KX_OUT_WDOT) v += ns;
+  if (outputs & KX_OUT_THERMO) v += 2;
+  if (outputs & KX_OUT_TRANSPORT) v += 2 + ns;
+  return 8 * v;
+}
+
+kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* wdot,
+                           double* cp, double* hmass, double* mu, double* lambda, double* Dk, int64_t ldo, int64_t n,
+                           kx_precision precision, int outputs, void* workspace, size_t workspace_bytes,
+                           int64_t max_chunk, void* stream_a, void* stream_b) {
+  kx_status s = check_state(h, T, p, Y, ld, n);
+  if (s != KX_OK) return s;
+  if (outputs <= 0 || outputs > 7) return fail(KX_ERR_ARG, "no outputs selected");
+  if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
+  if (((outputs & KX_OUT_WDOT) && !wdot) || ((outputs & KX_OUT_THERMO) && (!cp || !hmass)) ||
+      ((outputs & KX_OUT_TRANSPORT) && (!mu || !lambda || !Dk)))
+    return fail(KX_ERR_ARG, "null output");
+  if (ldo < n) return fail(KX_ERR_ARG, "output leading dimension smaller than the point count");
+  if (n == 0) return KX_OK;
+  const int64_t ns = h->m.ns, per = kx_evaluate_host_bytes_per_state(h, outputs);
+  // chunk: two slots in the workspace, a multiple of 256 states (32-byte aligned rows)
+  int64_t c = (int64_t)(workspace_bytes / (2 * (size_t)per)) / 256 * 256;
+  if (max_chunk > 0) c = std::min(c, std::max<int64_t>(256, max_chunk / 256 * 256));
+  if (c < 256) return fail(KX_ERR_ARG, "workspace smaller than two chunks of 256 states");
+  c = std::min(c, (n + 255) / 256 * 256);
+  cudaStream_t st[2] = {(cudaStream_t)stream_a, (cudaStream_t)stream_b};
+  for (int64_t c0 = 0, i = 0; c0 < n; c0 += c, ++i) {
+    const int64_t m = std::min(c, n - c0);
+    cudaStream_t q = st[i % 2];
+    double* b = (double*)((char*)workspace + (size_t)(i % 2) * (size_t)c * (size_t)per);
+    double *dT = b, *dp = dT + c, *dY = dp + c, *nx = dY + ns * c;
+    double *dw = nullptr, *dcp = nullptr, *dh = nullptr, *dmu = nullptr, *dl = nullptr, *dD = nullptr;
+    if (outputs & KX_OUT_WDOT) { dw = nx; nx += ns * c; }
+    if (outputs & KX_OUT_THERMO) { dcp = nx; dh = nx + c; nx += 2 * c; }
+    if (outputs & KX_OUT_TRANSPORT) { dmu = nx; dl = nx + c; dD = nx + 2 * c; nx += (2 + ns) * c; }
+    cudaError_t e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p + c0, m * 8, cudaMemcpyHostToDevice, q);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    if ((s = kx_copy_rows_async(dY, c, Y + c0, ld, ns, m, q)) != KX_OK) return s;
+    if ((outputs & KX_OUT_WDOT) && (s = kx_production_rates(h, dT, dp, dY, c, dw, m, precision, q)) != KX_OK) return s;
+    if ((outputs & KX_OUT_THERMO) && (s = kx_thermo(h, dT, dp, dY, c, dcp, dh, m, q)) != KX_OK) return s;
+    if ((outputs & KX_OUT_TRANSPORT) && (s = kx_transport(h, dT, dp, dY, c, dmu, dl, dD, m, precision, q)) != KX_OK) return s;
+    if ((outputs & KX_OUT_WDOT) && (s = kx_copy_rows_async(wdot + c0, ldo, dw, c, ns, m, q)) != KX_OK) return s;
+    if (outputs & KX_OUT_THERMO) {
+      e = cudaMemcpyAsync(cp + c0, dcp, m * 8, cudaMemcpyDeviceToHost, q);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hmass + c0, dh, m * 8, cudaMemcpyDeviceToHost, q);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    if (outputs & KX_OUT_TRANSPORT) {
+      e = cudaMemcpyAsync(mu + c0, dmu, m * 8, cudaMemcpyDeviceToHost, q);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(lambda + c0, dl, m * 8, cudaMemcpyDeviceToHost, q);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+      if ((s = kx_copy_rows_async(Dk + c0, ldo, dD, c, ns, m, q)) != KX_OK) return s;
+    }
+  }
   return KX_OK;
 }
 

@@ -55,6 +55,10 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_double)]
         L.kx_production_rates.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_production_rates_noalloc.argtypes = [vp, dp, dp, dp, i64, dp, i64, vp]
+        L.kx_evaluate_host_bytes_per_state.argtypes = [vp, ctypes.c_int]
+        L.kx_evaluate_host_bytes_per_state.restype = i64
+        L.kx_evaluate_host.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, dp, dp, dp, i64, i64, ctypes.c_int, ctypes.c_int,
+                                       vp, ctypes.c_size_t, i64, vp, vp]
         L.kx_rates_of_progress.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_thermo.argtypes = [vp, dp, dp, dp, i64, dp, dp, i64, vp]
         L.kx_transport.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, i64, ctypes.c_int, vp]
@@ -164,6 +168,32 @@ class Mechanism:
         n, ld = self._state(T, p, Y)
         assert out.shape[0] == self.n_species and (n == 0 or out.stride(0) == ld)
         _check(lib().kx_production_rates_noalloc(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out), n, _stream(stream)))
+        return out
+
+    OUT_WDOT, OUT_THERMO, OUT_TRANSPORT = 1, 2, 4
+
+    def evaluate_host_bytes_per_state(self, outputs: int) -> int:
+        return int(lib().kx_evaluate_host_bytes_per_state(self.h, outputs))
+
+    def evaluate_host(self, T, p, Y, out: dict, outputs: int = 7, precision="fp64", workspace=None,
+                      max_chunk: int = 0, streams=None):
+        """kx_evaluate_host: host (pinned) states in, host outputs out, the
+        copies overlapped with the kernels in chunks over two streams.  ``out``
+        holds host tensors under the keys wdot, cp, h, mu, lam, Dk (those of
+        the selected outputs); ``workspace`` a device uint8 tensor; ``streams``
+        two torch streams.  Returns after enqueueing; synchronise both streams."""
+        import torch
+        if not all(isinstance(t, torch.Tensor) and t.dtype == torch.float64 and not t.is_cuda for t in (T, p, Y)):
+            raise TypeError("T, p and Y must be host float64 tensors (pinned for asynchronous copies)")
+        if not (T.dim() == 1 and p.shape == T.shape and Y.dim() == 2 and Y.shape[0] == self.n_species
+                and Y.shape[1] == T.shape[0] and T.is_contiguous() and p.is_contiguous() and Y.stride(1) == 1):
+            raise ValueError("T, p [n] contiguous and Y [n_species, n] point-contiguous expected")
+        n, ld = T.shape[0], Y.stride(0)
+        get = lambda k: _ptr(out[k]) if k in out else None
+        ldo = out["wdot"].stride(0) if "wdot" in out else (out["Dk"].stride(0) if "Dk" in out else n)
+        _check(lib().kx_evaluate_host(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, get("wdot"), get("cp"), get("h"), get("mu"),
+                                      get("lam"), get("Dk"), ldo, n, _PREC[precision], outputs, workspace.data_ptr(),
+                                      workspace.numel(), max_chunk, _stream(streams[0]), _stream(streams[1])))
         return out
 
     def rates_of_progress(self, T, p, Y, out=None, precision="fp64", stream=None):
