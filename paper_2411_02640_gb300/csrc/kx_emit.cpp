@@ -1350,8 +1350,85 @@ std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
   return e;
 }
 
+// Mixed-precision body of one reaction class (see emit_rates_mixed for the
+// split): float32 ln k_f, [X], falloff blend and ln |R_f|; the float-pair
+// Gibbs sum ln(|R_r|/|R_f|) rounded once to float32; q as a float64 from
+// kx_net_rate_s.  Species vectors {ln |C|, C (float32), mu (pair)} in v_j.
+void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c) {
+  const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+  const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+  o("  float lk = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
+  if (tb) {
+    o(fmt("  const int2 e = kx_e%d[r];", ci));
+    o("  const float4 f2 = f[2];");
+    o("  float X;   // [X] = eff_default C_M + sum_e (eff_e - eff_default) C_e, float32");
+    o("  if (e.y < 0) X = sv[kx_effd[e.x].k].y;");
+    o("  else { X = f2.x * cMf; for (int j = 0; j < e.y; ++j) { const kx_effd_t q = kx_effd[e.x + j]; X = fmaf(q.ahi, sv[q.k].y, X); } }");
+    c.fp32 += d.rx.size() * 8;
+  }
+  if (d.kind == Kind::ThreeBody) { o("  lk += __logf(X);"); c.log32 += d.rx.size(); }
+  if (fo) {
+    o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+    o("  const float lk0 = fmaf(f3.x, lnTf, fmaf(f3.z, iTf, f2.z));");
+    o("  const float lnPr = fmaxf(lk0 - lk + __logf(X), -690.0f);");
+    o("  float lnF = 0.0f;");
+    if (d.blend == Blend::Troe) {
+      o("  const float lFc = __log10f(f4.x * __expf(Tf * f5.x) + f4.z * __expf(Tf * f5.z) + __expf(f6.x * iTf));");
+      o("  const float xx = fmaf(lnPr, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
+      o("  const float ff = __fdividef(xx, fmaf(-1.27f, lFc, 0.75f) - 0.14f * xx);");
+      o("  lnF = __fdividef(2.30258509f * lFc, fmaf(ff, ff, 1.0f));");
+      c.exp32 += d.rx.size() * 3; c.log32 += d.rx.size(); c.div32 += d.rx.size() * 2; c.fp32 += d.rx.size() * 14;
+    } else if (d.blend == Blend::Sri) {
+      o("  const float lPr = lnPr * 0.434294482f;");
+      o("  const float base = f4.x * __expf(f4.z * iTf) + __expf(Tf * f5.x);");
+      o("  lnF = f5.z + f6.x * lnTf + __fdividef(__logf(base), fmaf(lPr, lPr, 1.0f));");
+      c.exp32 += d.rx.size() * 2; c.log32 += d.rx.size(); c.div32 += d.rx.size(); c.fp32 += d.rx.size() * 8;
+    }
+    if (d.kind == Kind::Falloff) o("  lk = lk + kx_ln_pr_ratio(lnPr) + lnF;");
+    else o("  lk = lk0 + kx_ln_inv_1p(lnPr) + lnF;");
+    c.exp32 += d.rx.size(); c.log32 += d.rx.size() * 2; c.fp32 += d.rx.size() * 6;
+  } else if (d.kind == Kind::Plog) {
+    o(fmt("  const int2 e = kx_e%d[r];", ci));
+    o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+    o("  const long long Pb = __double_as_longlong(P);");
+    o("  if (Pb <= tp[0]) lk = fmaf(t[4], lnTf, fmaf(t[6], iTf, t[2]));");
+    o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = fmaf(u[4], lnTf, fmaf(u[6], iTf, u[2])); }");
+    o("  else {");
+    o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+    o("    const float* u = t + 8 * j;");
+    o("    const float l1 = fmaf(u[4], lnTf, fmaf(u[6], iTf, u[2])), l2 = fmaf(u[12], lnTf, fmaf(u[14], iTf, u[10]));");
+    o("    lk = fmaf(l2 - l1, __fdividef(lnPf - u[0], u[8] - u[0]), l1);");
+    o("  }");
+    c.fp32 += d.rx.size() * 8;
+  }
+  std::string lnRf = "lk";
+  for (int j = 0; j < d.nre; ++j) lnRf += fmt(" + v%d.x", j);
+  o("  const float lnRf = " + lnRf + ";");
+  std::string sfx = "0", srx = "0";
+  for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+  for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+  o("  const int sf = " + sfx + ";");
+  c.fp32 += d.rx.size() * (2 + d.nre);
+  if (d.rev) {
+    const int dn = d.npr - d.nre;
+    o("  // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T)) in float pairs, rounded to float32 once");
+    std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+    o("  kx_df dl = " + first + ";");
+    for (int j = 1; j < E; ++j) o(fmt("  dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
+    if (dn != 0) o(fmt("  dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+    o("  const double q = kx_net_rate_s(lnRf, dl.hi, sf, " + srx + ");");
+    c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + 10); c.exp32 += d.rx.size() * 2;
+  } else {
+    o("  const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+    o("  const double q = sf ? -q0 : q0;");
+    c.exp32 += d.rx.size(); c.fp32 += d.rx.size() * 2;
+  }
+}
+
 void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
   const int ns = m.ns;
+  // mixed precision: float32 rates, float-pair chemical potentials and Gibbs sums, float64 accumulation
+  const bool mx = opt.mixed;
   // ---- classes and their tables
   std::vector<DfClass> cls;
   for (int i = 0; i < m.nr(); ++i) {
@@ -1467,6 +1544,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     o("const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;");
     o("const kx_strided<float4> sv{(float4*)kx_scr + gtid, nthr};   // {ln |C_k| (pair), mu_k (pair)}");
     o(fmt("const kx_strided<kx_df> w{(kx_df*)(kx_scr + (long long)%d * 16 * nthr) + gtid, nthr};", ns));
+  } else if (mx) {
+    o(fmt("float4 sv[%d];   // {ln |C_k|, C_k (float32), mu_k (pair)}", ns));
+    if (!rop) o(fmt("double w[%d];", ns));
   } else {
     o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k (pair)}", ns));
     if (!rop) o(fmt("kx_df w[%d];", ns));
@@ -1507,8 +1587,13 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   o("  gk = kx_df_fma(KX_PF(a + 10), iT, gk);");
   o("  gk = kx_df_fma(KX_PF(a + 12), lnT, gk);");
   o("  const kx_df mk_ = kx_df_add(gk, l);");
-  o("  sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
-  if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
+  if (mx) {
+    o("  sv[k] = make_float4(l.hi, kx_df_mul(kx_d2df_i(Yk), KX_PF(kx_iwf + 2 * k)).hi * fC.hi, mk_.hi, mk_.lo);");
+    if (!rop) o("  w[k] = 0.0;");
+  } else {
+    o("  sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
+    if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
+  }
   o("}");
   c.fp32 += 40 + 45 + kDfDiv + 2 * kDfMul + kDfAdd + kDfDiv + kDfLog;
   c.fp32 += ns * (12 + kDfFma) + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
@@ -1540,7 +1625,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   };
 
   // ---- pre-pass: float32 upper bound U of ln max(|R_f|, |R_r|) over the reactions
-  if (!rop) {
+  if (mx) o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, cMf = cM.hi;");
+  if (mx && any_plog) o("const float lnPf = lnP.hi;");
+  if (!rop && !mx) {
     o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
     o("float U = -1.0e30f;");
     for (size_t ci = 0; ci < cls.size(); ++ci) {
@@ -1611,121 +1698,131 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       std::string pdecl = "int";
       for (int j = 0; j < E; ++j) pdecl += fmt("%s p%d = 0", j ? "," : "", j);
       o(pdecl + ";   // entries of the previous reaction (coefficient 0: nothing to add)");
-      o("kx_df qp = kx_mk(0.0f, 0.0f);");
+      o(mx ? "double qp = 0.0;" : "kx_df qp = kx_mk(0.0f, 0.0f);");
     }
     o("#pragma unroll 1");
     o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
     if (!rop)
-      for (int j = 0; j < E; ++j) o(fmt("  const kx_df wl%d = w[p%d & 0xffff];", j, j));
+      for (int j = 0; j < E; ++j) o(fmt("  const %s wl%d = w[p%d & 0xffff];", mx ? "double" : "kx_df", j, j));
     prefetch(d);
     for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
     if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
     o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
     o("  const float4 f0 = f[0], f1 = f[1];");
-    o("  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
-    if (tb) {
-      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-      o("  const float4 f2 = f[2];");
-      o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
-      o("  if (e.y < 0) {");
-      o("    const int kc = kx_effd[e.x].k;");
-      o("    X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + i]), KX_PF(kx_iwf + 2 * kc)), fC);");
-      o("  } else {");
-      o("    kx_df t = kx_mk(0.0f, 0.0f);");
-      o("    for (int j = 0; j < e.y; ++j) {");
-      o("      const kx_effd_t q = kx_effd[e.x + j];");
-      o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + i]), KX_PF(kx_iwf + 2 * q.k)), t);");
-      o("    }");
-      o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
-      o("  }");
-      c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
-    }
-    if (fo) {
-      o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
-      o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
-      o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
-      o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
-      o("  kx_df lnF = kx_mk(0.0f, 0.0f);");
-      const std::string il10 = DFc(1.0 / std::log(10.0));
-      if (d.blend == Blend::Troe) {
-        o("  kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
-        o("  Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
-        o("  Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
-        o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
-        o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
-        o(fmt("  const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
-              DFc(0.75).c_str()));
-        o(fmt("  lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
-        c.fp32 += d.rx.size() * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
-      } else if (d.blend == Blend::Sri) {
-        o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
-        o("  const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
-        o("  lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
-        c.fp32 += d.rx.size() * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
-      }
-      o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
-      o("  const bool small = lnPr.hi < 0.0f;");
-      o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
-      if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
-      else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
-      c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
-    } else if (d.kind == Kind::Plog) {
-      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-      o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
-      o("  const long long Pb = __double_as_longlong(P);");
-      o("  if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
-      o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
-      o("  else {");
-      o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
-      o("    const float* u = t + 8 * j;");
-      o("    const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
-      o("    const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
-      o("    lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
-      o("  }");
-      c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
-    }
-    // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
-    o(rop ? "  kx_df lf = lk;" : "  kx_df lf = kx_df_sub(lk, lnS);");
-    for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add(lf, kx_mk(v%d.x, v%d.y));", j, j));
-    std::string sfx = "0", srx = "0";
-    for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
-    for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
-    o("  int sf = " + sfx + ";");
-    o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
-    o("  bool rev = false;");
-    c.fp32 += d.rx.size() * (2 * kDfFma + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
-    if (d.rev) {
-      const int dn = d.npr - d.nre;
-      o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
-      std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
-      o("    kx_df dl = " + first + ";");
-      for (int j = 1; j < E; ++j)
-        o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
-      if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-      o("    const int sr = " + srx + ";");
-      o("    rev = dl.hi > 0.0f;");
-      o("    if (rev) L = kx_df_add(lf, dl);");
-      o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
-      o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
-      o("    const float pm = sf == sr ? -1.0f : 1.0f;");
-      o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
-      o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
-      o("    if (sf == sr) sf ^= (int)rev;");
-      o("  }");
-      c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
-    }
-    if (rop) {
-      o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
-      o("  kx_df q = kx_df_mul(kx_df_exp_s(kx_df_sub(L, kx_df_ln2_mul(Sr))), fac);");
-      c.fp32 += d.rx.size() * (kDfAdd + 10);
+    if (mx) {
+      emit_class_mixed_body(o, d, (int)ci, E, c);
     } else {
-      o("  kx_df q = kx_df_mul(kx_df_exp_s(L), fac);");
+      o("  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+      if (tb) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  const float4 f2 = f[2];");
+        o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
+        o("  if (e.y < 0) {");
+        o("    const int kc = kx_effd[e.x].k;");
+        o("    X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + i]), KX_PF(kx_iwf + 2 * kc)), fC);");
+        o("  } else {");
+        o("    kx_df t = kx_mk(0.0f, 0.0f);");
+        o("    for (int j = 0; j < e.y; ++j) {");
+        o("      const kx_effd_t q = kx_effd[e.x + j];");
+        o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + i]), KX_PF(kx_iwf + 2 * q.k)), t);");
+        o("    }");
+        o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+        o("  }");
+        c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
+      }
+      if (fo) {
+        o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+        o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
+        o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+        o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+        o("  kx_df lnF = kx_mk(0.0f, 0.0f);");
+        const std::string il10 = DFc(1.0 / std::log(10.0));
+        if (d.blend == Blend::Troe) {
+          o("  kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
+          o("  Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
+          o("  Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
+          o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+          o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+          o(fmt("  const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
+                DFc(0.75).c_str()));
+          o(fmt("  lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
+          c.fp32 += d.rx.size() * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
+        } else if (d.blend == Blend::Sri) {
+          o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+          o("  const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
+          o("  lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
+          c.fp32 += d.rx.size() * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
+        }
+        o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
+        o("  const bool small = lnPr.hi < 0.0f;");
+        o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
+        if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
+        else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
+        c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
+      } else if (d.kind == Kind::Plog) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+        o("  const long long Pb = __double_as_longlong(P);");
+        o("  if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
+        o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
+        o("  else {");
+        o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+        o("    const float* u = t + 8 * j;");
+        o("    const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
+        o("    const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
+        o("    lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
+        o("  }");
+        c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
+      }
+      // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
+      o(rop ? "  kx_df lf = lk;" : "  kx_df lf = kx_df_sub(lk, lnS);");
+      for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add(lf, kx_mk(v%d.x, v%d.y));", j, j));
+      std::string sfx = "0", srx = "0";
+      for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+      for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+      o("  int sf = " + sfx + ";");
+      o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
+      o("  bool rev = false;");
+      c.fp32 += d.rx.size() * (2 * kDfFma + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
+      if (d.rev) {
+        const int dn = d.npr - d.nre;
+        o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
+        std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+        o("    kx_df dl = " + first + ";");
+        for (int j = 1; j < E; ++j)
+          o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
+        if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+        o("    const int sr = " + srx + ";");
+        o("    rev = dl.hi > 0.0f;");
+        o("    if (rev) L = kx_df_add(lf, dl);");
+        o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
+        o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
+        o("    const float pm = sf == sr ? -1.0f : 1.0f;");
+        o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
+        o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
+        o("    if (sf == sr) sf ^= (int)rev;");
+        o("  }");
+        c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+      }
+      if (rop) {
+        o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
+        o("  kx_df q = kx_df_mul(kx_df_exp_s(kx_df_sub(L, kx_df_ln2_mul(Sr))), fac);");
+        c.fp32 += d.rx.size() * (kDfAdd + 10);
+      } else {
+        o("  kx_df q = kx_df_mul(kx_df_exp_s(L), fac);");
+      }
+      o("  if (sf) q = kx_df_neg(q);");
+      if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
     }
-    o("  if (sf) q = kx_df_neg(q);");
-    if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
     if (rop) {
-      o("  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
+      o(mx ? "  out_[(long long)ri * ld + i] = q;" : "  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
       c.fp64 += d.rx.size();
+    } else if (mx) {
+      for (int j = 0; j < E; ++j)
+        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = fma(kx_f2d(kx_i2f(cj)), qp, wl%d); }", j, j, j));
+      o("  qp = q;");
+      for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
+      c.fp64 += d.rx.size() * E;
     } else {
       // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
       for (int j = 0; j < E; ++j)
@@ -1736,7 +1833,11 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     }
     advance(d);
     o("}");
-    if (!rop)
+    if (!rop && mx)
+      for (int j = 0; j < E; ++j)
+        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(kx_i2f(cj)), qp, w[kk]); } }",
+              j, j));
+    else if (!rop)
       for (int j = 0; j < E; ++j)
         o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add(w[kk], kx_df_mulf(qp, kx_i2f(cj))); } }",
               j, j));
@@ -1744,8 +1845,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     o("}");
   }
   if (!rop) {
-    o(fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));
-    c.fp64 += ns;
+    o(fmt(mx ? "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = w[k];"
+             : "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));
+    c.fp64 += mx ? 0 : ns;
   }
 }
 
@@ -2349,7 +2451,8 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       if (opt.scratch && !rop) outs += ", unsigned char* __restrict__ kx_scr, long long nthr";
       nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);
       const bool table = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
-      if (!opt.mixed && (opt.rates_arith != 1 || opt.scratch)) emit_rates_class_df(body, globals, m, opt, rop, c);
+      if ((!opt.mixed && (opt.rates_arith != 1 || opt.scratch)) || (opt.mixed && opt.rates_mode == 0))
+        emit_rates_class_df(body, globals, m, opt, rop, c);
       else if (table && opt.mixed) emit_rates_table_mixed(body, globals, m, rop, c);
       else if (table) emit_rates_table64(body, globals, m, rop, c);
       else if (opt.mixed) emit_rates_mixed(body, m, rop, c);
@@ -2378,9 +2481,10 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   std::ostringstream s;
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
-  const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && (opt.rates_arith != 1 || opt.scratch);
+  const bool df_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) &&
+                        ((!opt.mixed && (opt.rates_arith != 1 || opt.scratch)) || (opt.mixed && opt.rates_mode == 0));
   const bool table_sel = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
-  const bool mixed_unrolled = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && opt.mixed && !table_sel;
+  const bool mixed_unrolled = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && opt.mixed && !table_sel && !df_rates;
   const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates && !mixed_unrolled;
   // table-driven float64 rate kernels take their exponentials from kx_exp_r (error ~2e-12 against
   // a 1e-10 bar); the unrolled ones keep kx_exp, whose short inline sequence keeps compile time
