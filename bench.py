@@ -177,8 +177,18 @@ def cpu_baseline(seconds_target: float = 15.0):
     o.thermo(T, p, Y)
     o.transport(T, p, Y)
     dt = time.perf_counter() - t0
+    # one core, on a sample of about a second
+    o1 = oracle.Oracle(synth.mechanism_file(MECH, os.path.join(CACHE, "mech")), nthreads=1)
+    n1 = max(64, int(n2 / dt / cores))
+    T1, p1, Y1 = make_inputs(0, n1)
+    t1 = time.perf_counter()
+    o1.production_rates(T1, p1, Y1)
+    o1.thermo(T1, p1, Y1)
+    o1.transport(T1, p1, Y1)
+    dt1 = time.perf_counter() - t1
     return {"value": n2 / dt / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n2} states of the 2^20-state workload, one pass of wdot+thermo+transport"}
+            "sample": f"{n2} states of the 2^20-state workload, one pass of wdot+thermo+transport",
+            "one_core": {"value": n1 / dt1 / 1e6, "sample": f"{n1} states"}}
 
 
 def run_reference(args):
@@ -334,6 +344,26 @@ def run_kx(args):
         dom = int(np.argmax(per))
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         roof = kernel_roofline(mech, names[dom], n, per[dom], sm_max)
+        hbm = float(pk.get("hbm_gbs", 6787.2))
+
+        def step_bound(knames, ms_each):
+            """t_bound of the step: per kernel the slowest of its float64 instructions at the
+            float64 peak, its float32-pipe instructions at the float32 peak and its algorithmic
+            bytes at the measured HBM copy rate; summed over the kernels of the step."""
+            tb, parts = 0.0, {}
+            byt = {"wdot": 8 * (2 + 2 * ns), "thermo": 8 * (2 + ns + 2), "visc": 8 * (2 + ns + 2),
+                   "diff": 8 * (2 + 2 * ns)}
+            for kname, ms_k in zip(knames, ms_each):
+                c = mech.op_counts(kname)
+                t64 = ops_per_point(mech, kname) * n / (fp64_peak_gops(sm_max) * 1e9)
+                t32 = c["fp32"] * n / (fp32_peak_gops(sm_max) * 1e9)
+                tm = byt[kname.split("_")[0]] * n / (hbm * 1e9)
+                t = max(t64, t32, tm)
+                tb += t
+                parts[kname] = {"t_bound_ms": t * 1e3, "measured_ms": ms_k,
+                                "bound": "fp64" if t == t64 else "fp32" if t == t32 else "hbm"}
+            return tb * 1e3, parts
+
         roof["traffic"] = profiled_traffic(mech, names[dom], n)
         roof["algorithmic_bytes"] = 8 * (2 + ns + ns) * n
         mnames = kernels["mixed"]
@@ -351,13 +381,21 @@ def run_kx(args):
                        "points_per_gpu": n, "step": "production_rates + thermo + transport (viscosity/conductivity and diffusion)",
                        "l2": "inputs (461 MB) and outputs larger than L2; no flush"},
             "kernel_ms": {k: v for k, v in zip(names, per)},
+            "grxn_s": value * 1e6 * mech.n_reactions / 1e9,
+            "gdof_s": value * 1e6 * (ns + 2) / 1e9,
             "mixed": {"value": world * n / (mms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": mms,
                       "kernel_ms": {k: v for k, v in zip(mnames, mper)},
                       "dtype": "f32 + f32x2 (Gibbs sums) + f64 (wdot accumulation)",
                       "error": "wdot <= 2e-4 of the per-point scale max_k|W_k wdot_k| (p99 <= 1e-4); "
                                "transport <= 5e-6 relative; thermo float64-accurate",
-                      "roofline": kernel_roofline(mech, mnames[mdom], n, mper[mdom], sm_max)},
+                      "roofline": kernel_roofline(mech, mnames[mdom], n, mper[mdom], sm_max),
+                      "step_roofline": (lambda tb: {"t_bound_ms": tb[0], "measured_ms": mms, "frac": tb[0] / mms,
+                                                    "kernels": tb[1]})(step_bound(mnames, mper))},
             "roofline": roof,
+            "step_roofline": (lambda tb: {"t_bound_ms": tb[0], "measured_ms": ms, "frac": tb[0] / ms, "kernels": tb[1],
+                                          "definition": "per kernel max(float64 instr / float64 peak, float32-pipe "
+                                                        "instr / float32 peak, algorithmic bytes / measured HBM), "
+                                                        "summed over the step"})(step_bound(names, per)),
             "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "api": "kx_evaluate_host",
                     "chunk": chunk,
                     "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n},
@@ -472,6 +510,40 @@ def ops_per_point(mech, name):
     return c["fp64"] + COST["exp64"] * c["exp64"] + COST["log64"] * c["log64"] + COST["div64"] * c["div64"]
 
 
+def run_alternatives(args):
+    """Times kx_production_rates on the bench workload in each of its forms: the float-pair
+    default, native float64 with k_r in log space (kc_mode 0) and native float64 with the
+    paper's per-species exp(-G/RT) products and one division per reaction (kc_mode 1), and the
+    mixed kernel; prints one JSON line with times and the emitter's operation counts."""
+    import torch
+    from paper_2411_02640_gb300 import kx, synth
+    torch.cuda.set_device(0)
+    n = args.points
+    path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
+    T, p, Y = make_inputs(0, n)
+    Td, pd, Yd = (torch.from_numpy(a).cuda() for a in (T, p, Y))
+    forms = {"fp64_float_pair": ({}, "fp64"), "fp64_native_logspace": ({"rates_arith": 1, "kc_mode": 0}, "fp64"),
+             "fp64_native_g3": ({"rates_arith": 1, "kc_mode": 1}, "fp64"), "mixed": ({}, "mixed")}
+    out = {}
+    for label, (opts, prec) in forms.items():
+        mech = kx.Mechanism(path, cache_dir=CACHE, lazy=1, **opts)
+        kname = "wdot_fp64" if prec == "fp64" else "wdot_mixed"
+        w = mech.production_rates(Td, pd, Yd, precision=prec)
+        for _ in range(args.warmup):
+            mech.production_rates(Td, pd, Yd, out=w, precision=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mech.production_rates(Td, pd, Yd, out=w, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[label] = {"ms": ms, "mpoints_s": n / (ms * 1e-3) / 1e6, "op_counts": mech.op_counts(kname),
+                      "registers": mech.kernel_info(kname)["registers"]}
+    print(json.dumps({"metric": "production-rate kernel forms", "points": n, "mechanism": MECH, "forms": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,9 +559,13 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving sweep (rates x batching vs one at a time) only")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sample in the default line")
+    ap.add_argument("--alternatives", action="store_true",
+                    help="time the production-rate kernel in each arithmetic / equilibrium form only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.alternatives:
+        run_alternatives(args)
     elif args.serve:
         print(json.dumps({"metric": "serving", "serving": run_serve_suite(args, sweep=True)}), flush=True)
     else:
