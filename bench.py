@@ -482,7 +482,7 @@ def run_serve_suite(args, sweep=True):
             m.production_rates(T, p, Y, precision=prec)
             m.transport(T, p, Y, precision=prec)
     torch.cuda.synchronize()
-    rates = [2.0, 4.0, 8.0, 16.0] if sweep else [4.0]
+    rates = [2.0, 4.0, 8.0, 16.0, 32.0] if sweep else [16.0]
     out = {"budget_bytes": budget, "mechanisms": list(SERVE_MECHS), "batching": [], "one_at_a_time": []}
     for r in rates:
         out["batching"].append(serve_run(mechs, pools, r, args.serve_requests, 105, True, 4, budget))
@@ -541,7 +541,28 @@ def run_alternatives(args):
         ms = e0.elapsed_time(e1) / args.steps
         out[label] = {"ms": ms, "mpoints_s": n / (ms * 1e-3) / 1e6, "op_counts": mech.op_counts(kname),
                       "registers": mech.kernel_info(kname)["registers"]}
-    print(json.dumps({"metric": "production-rate kernel forms", "points": n, "mechanism": MECH, "forms": out}), flush=True)
+    # transport with the ln fits and with the paper's direct fits (no exponentials)
+    tr = {}
+    for mname in (MECH, MECH + "_direct"):
+        mech = kx.Mechanism(synth.mechanism_file(mname, os.path.join(CACHE, "mech")), cache_dir=CACHE)
+        for prec in ("fp64", "mixed"):
+            res = mech.transport(Td, pd, Yd, precision=prec)
+            for _ in range(args.warmup):
+                mech.transport(Td, pd, Yd, out=res, precision=prec)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            tv = td = 0.0
+            for _ in range(args.steps):
+                ev[0].record()
+                mech.viscosity_conductivity(Td, pd, Yd, out=res[:2], precision=prec)
+                ev[1].record()
+                mech.diffusion(Td, pd, Yd, out=res[2], precision=prec)
+                ev[2].record()
+                torch.cuda.synchronize()
+                tv += ev[0].elapsed_time(ev[1]); td += ev[1].elapsed_time(ev[2])
+            tr[f"{mname}/{prec}"] = {"visc_ms": tv / args.steps, "diff_ms": td / args.steps}
+    print(json.dumps({"metric": "production-rate kernel forms", "points": n, "mechanism": MECH, "forms": out,
+                      "transport_fits": tr}), flush=True)
 
 
 def main():
@@ -557,7 +578,7 @@ def main():
     ap.add_argument("--rates-arith", type=int, default=0,
                     help="float64-accurate rates: 0 double-float (default), 1 native float64")
     ap.add_argument("--serve", action="store_true", help="serving sweep (rates x batching vs one at a time) only")
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sample in the default line")
     ap.add_argument("--alternatives", action="store_true",
                     help="time the production-rate kernel in each arithmetic / equilibrium form only")

@@ -99,6 +99,7 @@ struct Mech {
   std::vector<double> a_lo, a_hi;      // [ns][7]
   std::vector<double> eta, lam;        // [ns][5]
   std::vector<double> dif;             // [ns][ns][5]
+  bool direct = false;                 // fits of eta, lambda and 1/D_kj themselves (else of their logs)
   std::vector<Rxn> rx;
 };
 
@@ -135,6 +136,8 @@ bool parse(const char* path, Mech& m, std::string& err) {
       int s = I(t[1]);
       m.Tmid[s] = D(t[3]);
       for (int j = 0; j < 7; ++j) { m.a_lo[7 * s + j] = D(t[5 + j]); m.a_hi[7 * s + j] = D(t[12 + j]); }
+    } else if (k == "transport_fit") {
+      m.direct = t[1] == "direct";
     } else if (k == "eta" || k == "lambda") {
       int s = I(t[1]);
       for (int j = 0; j < 5; ++j) (k == "eta" ? m.eta : m.lam)[5 * s + j] = D(t[2 + j]);
@@ -349,16 +352,32 @@ double fit(const double* c, double L) {
   return s;
 }
 
+// The same polynomial summed in long double: direct fits of eta, lambda and
+// 1/D_kj have condition numbers up to ~1e6 in the monomial basis of ln T, so
+// a float64 sum would carry ~1e-10 of rounding; extended precision keeps the
+// oracle's own error below the 1e-12 bar.
+double fit_ext(const double* c, double L) {
+  long double s = 0.0L;
+  for (int n = 0; n < 5; ++n) s += (long double)c[n] * std::pow((long double)L, (long double)n);
+  return (double)s;
+}
+
+// Pure-species properties from the fits in ln T (Sec. A.3.4): of ln eta,
+// ln lambda and ln D_kj, exponentiated; or, with direct fits, of eta and
+// lambda themselves and of the reciprocal 1/D_kj (the paper evaluates the
+// reciprocal polynomial of the binary diffusion coefficients, Sec. 2.3.2).
 void species_transport(const Mech& m, double T, double p, double* eta, double* lam, double* Dkj) {
   const double L = std::log(T);
   for (int k = 0; k < m.ns; ++k) {
-    eta[k] = std::exp(fit(&m.eta[5 * k], L));
-    lam[k] = std::exp(fit(&m.lam[5 * k], L));
+    eta[k] = m.direct ? fit_ext(&m.eta[5 * k], L) : std::exp(fit(&m.eta[5 * k], L));
+    lam[k] = m.direct ? fit_ext(&m.lam[5 * k], L) : std::exp(fit(&m.lam[5 * k], L));
   }
   if (Dkj)
     for (int k = 0; k < m.ns; ++k)
-      for (int j = 0; j < m.ns; ++j)
-        Dkj[k * m.ns + j] = std::exp(fit(&m.dif[5 * (k * m.ns + j)], L)) * P_ATM / p;
+      for (int j = 0; j < m.ns; ++j) {
+        const double* c = &m.dif[5 * (k * m.ns + j)];
+        Dkj[k * m.ns + j] = (m.direct ? 1.0 / fit_ext(c, L) : std::exp(fit(c, L))) * P_ATM / p;
+      }
 }
 
 // Wilke/Bird interaction factor phi_kj.  The molecular-weight ratio inside

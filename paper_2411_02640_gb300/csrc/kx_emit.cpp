@@ -236,6 +236,26 @@ __device__ __forceinline__ kx_df kx_df_mul(kx_df a, kx_df b) {
   return kx_qts(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))));
 }
 __device__ __forceinline__ double kx_df2d(kx_df a) { return kx_f2d(a.hi) + kx_f2d(a.lo); }
+// a / b: a reciprocal estimate refined by one Newton step, then one
+// correction of the quotient from the exact remainder a - q1 b
+__device__ __forceinline__ kx_df kx_df_div(kx_df a, kx_df b) {
+  float rb = __fdividef(1.0f, b.hi);
+  rb = __fmaf_rn(rb, __fmaf_rn(-b.hi, rb, 1.0f), rb);
+  const float q1 = __fmul_rn(a.hi, rb);
+  const float p = __fmul_rn(q1, b.hi);
+  const float pe = __fmaf_rn(q1, b.hi, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), __fmaf_rn(-q1, b.lo, a.lo));
+  return kx_qts(q1, __fmul_rn(r, rb));
+}
+// 1/sqrt(x) of a positive float pair: the float32 estimate y, r = 1 - x y^2 in
+// float pairs (y^2 as an exact product pair), y (1 + r/2 + 3r^2/8)
+__device__ __forceinline__ kx_df kx_df_rsqrt(kx_df x) {
+  const float y = rsqrtf(x.hi);
+  const float p = __fmul_rn(y, y);
+  const kx_df xy2 = kx_df_mul(x, kx_mk(p, __fmaf_rn(y, y, -p)));
+  const float r = __fadd_rn(__fsub_rn(1.0f, xy2.hi), -xy2.lo);
+  return kx_qts(y, __fmul_rn(y, __fmaf_rn(__fmul_rn(0.375f, r), r, __fmul_rn(0.5f, r))));
+}
 __device__ __forceinline__ kx_df kx_d2df(double x) {
   const float h = kx_d2f(x);
   return kx_mk(h, kx_d2f(x - kx_f2d(h)));
@@ -314,17 +334,6 @@ __device__ __forceinline__ kx_df kx_df_sub(kx_df a, kx_df b) { return kx_df_add(
 __device__ __forceinline__ kx_df kx_df_mulf(kx_df a, float b) {
   const float p = __fmul_rn(a.hi, b);
   return kx_qts(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
-}
-// a / b: a reciprocal estimate refined by one Newton step, then one
-// correction of the quotient from the exact remainder a - q1 b
-__device__ __forceinline__ kx_df kx_df_div(kx_df a, kx_df b) {
-  float rb = __fdividef(1.0f, b.hi);
-  rb = __fmaf_rn(rb, __fmaf_rn(-b.hi, rb, 1.0f), rb);
-  const float q1 = __fmul_rn(a.hi, rb);
-  const float p = __fmul_rn(q1, b.hi);
-  const float pe = __fmaf_rn(q1, b.hi, -p);
-  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), __fmaf_rn(-q1, b.lo, a.lo));
-  return kx_qts(q1, __fmul_rn(r, rb));
 }
 // Float pair of a double: the high part keeps 24 significant bits
 // (truncation), the low part the remaining 29 bits rounded once.  Values
@@ -2143,8 +2152,12 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   if (opt.mixed) md = {TrMode::F32, "float", "float"};
   else if (opt.tr_mode == 0) md = {TrMode::DF, "kx_df", "float2"};
   else md = {TrMode::F64, "double", "double"};
-  const double L0 = md.kind == TrMode::F64 ? 0.0 : 0.5 * (std::log(300.0) + std::log(3000.0));
-  const double SC = md.kind == TrMode::F32 ? 1.4426950408889634 : 1.0;   // exp2 form for float32
+  // direct fits (of eta, lambda, 1/D themselves) are evaluated without exponentials and, in every
+  // arithmetic, in L = ln T - L0: their monomial form in ln T is badly conditioned (condition numbers
+  // up to ~1e6 for 1/D_kj); the re-expansion is computed in long double
+  const bool direct = m.fit_direct;
+  const double L0 = (md.kind == TrMode::F64 && !direct) ? 0.0 : 0.5 * (std::log(300.0) + std::log(3000.0));
+  const double SC = (md.kind == TrMode::F32 && !direct) ? 1.4426950408889634 : 1.0;   // exp2 form for float32
   const int B = opt.block;
   // float64-accurate viscosity keeps two vectors per species (X, v = 1/u) in shared memory
   // and forms z1, z2 in the loop: two multiplies per pair buy twice the resident warps
@@ -2187,9 +2200,19 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     return r;
   };
   auto coefs = [&](const double* cf, double s, double add, double out[5]) {
-    if (md.kind == TrMode::F64) for (int n = 0; n < 5; ++n) out[n] = cf[n] * s;
+    if (L0 == 0.0) for (int n = 0; n < 5; ++n) out[n] = cf[n] * s;
     else shift_poly(cf, L0, s * SC, out);
     out[0] += add * SC;
+  };
+  // 1/sqrt and sqrt of a positive value in the kernel's arithmetic
+  auto RSQRT = [&](const std::string& a) {
+    return md.kind == TrMode::DF ? fmt("kx_df_rsqrt(%s)", a.c_str()) : md.kind == TrMode::F32 ? fmt("rsqrtf(%s)", a.c_str())
+                                                                                                 : fmt("(1.0 / sqrt(%s))", a.c_str());
+  };
+  auto DIV = [&](const std::string& a, const std::string& b) {
+    return md.kind == TrMode::DF ? fmt("kx_df_div(%s, %s)", a.c_str(), b.c_str())
+                                 : md.kind == TrMode::F32 ? fmt("__fdividef(%s, %s)", a.c_str(), b.c_str())
+                                                          : fmt("((%s) / (%s))", a.c_str(), b.c_str());
   };
   // per-op costs, for the manifest
   const double cf_fma = md.kind == TrMode::DF ? 14 : 1, cf_exp = md.kind == TrMode::DF ? 45 : 1;
@@ -2201,14 +2224,23 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   };
   // ---- module-scope tables
   {
-    std::string pv, pl, wa, dself, w, iw, sqw;
+    std::string pv, pl, wa, dself, w, iw, sqw, w4, iw4;
     for (int k = 0; k < ns; ++k) {
       double d[5];
-      coefs(&m.eta[5 * k], -0.5, 0.25 * std::log(m.W[k]), d);      // ln v_k = -(ln eta_k / 2 - ln W_k / 4)
+      if (direct) coefs(&m.eta[5 * k], 1.0, 0.0, d);                  // eta_k
+      else coefs(&m.eta[5 * k], -0.5, 0.25 * std::log(m.W[k]), d);   // ln v_k = -(ln eta_k / 2 - ln W_k / 4)
       for (int n = 0; n < 5; ++n) pv += lit(d[n]) + ",";
       coefs(&m.lam[5 * k], 1.0, 0.0, d);
       for (int n = 0; n < 5; ++n) pl += lit(d[n]) + ",";
-      for (int n = 0; n < 5; ++n) dself += D(m.dif[5 * ((size_t)k * ns + k) + n]) + ",";
+      if (direct) {   // 1/D_kk in L = ln T - L0
+        double e[5];
+        shift_poly(&m.dif[5 * ((size_t)k * ns + k)], L0, 1.0, e);
+        for (int n = 0; n < 5; ++n) dself += D(e[n]) + ",";
+      } else {
+        for (int n = 0; n < 5; ++n) dself += D(m.dif[5 * ((size_t)k * ns + k) + n]) + ",";
+      }
+      w4 += lit(std::pow(m.W[k], 0.25)) + ",";
+      iw4 += lit(std::pow(m.W[k], -0.25)) + ",";
       w += D(m.W[k]) + ",";
       iw += D(1.0 / m.W[k]) + ",";
       sqw += D(std::sqrt(m.W[k])) + ",";
@@ -2220,7 +2252,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
       for (int j = (opt.diff_mode == 2 ? 0 : k + 1); j < ns; ++j) {
         if (j == k) continue;
         double d[5];
-        coefs(&m.dif[5 * ((size_t)k * ns + j)], -1.0, 0.0, d);
+        coefs(&m.dif[5 * ((size_t)k * ns + j)], direct ? 1.0 : -1.0, 0.0, d);   // 1/D_kj, or -ln D_kj
         for (int n = 0; n < 5; ++n) dc += lit(d[n]) + ",";
         dc += lit(0.0) + ",";                 // each pair padded to 6 entries for vector loads
         ++np;
@@ -2236,10 +2268,12 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     g(fmt("__device__ const double kx_w[%d] = {%s};", ns, w.c_str()));
     g(fmt("__device__ const double kx_iw[%d] = {%s};", ns, iw.c_str()));
     g(fmt("__device__ const double kx_sqw[%d] = {%s};", ns, sqw.c_str()));
+    g(fmt("__device__ const %s kx_w4[%d] = {%s};", T, ns, w4.c_str()));
+    g(fmt("__device__ const %s kx_iw4[%d] = {%s};", T, ns, iw4.c_str()));
   }
   o("const double lnT = log(T);");
   c.log64 += 1;
-  if (md.kind == TrMode::F64) o("const double L = lnT;");
+  if (L0 == 0.0) o("const double L = lnT;");
   else o(fmt("const %s L = %s;", md.ty, FROMD(fmt("lnT - %s", D(L0).c_str())).c_str()));
   o(fmt("%s* const sX = (%s*)kx_dyn;", md.st, md.st));
   o(fmt("%s* const sZ1 = sX + %d;", md.st, ns * B));
@@ -2265,7 +2299,12 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o(fmt("  const %s X = %s;", md.ty, FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig").c_str()));
   o("  " + st(fmt("sX[k * %d + t]", B), "X"));
   o(fmt("  const %s* pv = kx_pv + 5 * k; const %s* pl = kx_pl + 5 * k;", md.st, md.st));
-  o(fmt("  const %s v = %s;", md.ty, EXP(horner("pv")).c_str()));
+  if (direct) {   // v = W^(1/4)/sqrt(eta)
+    o(fmt("  const %s eta = %s;", md.ty, horner("pv").c_str()));
+    o(fmt("  const %s v = %s;", md.ty, MUL(RSQRT("eta"), ld("kx_w4[k]")).c_str()));
+  } else {
+    o(fmt("  const %s v = %s;", md.ty, EXP(horner("pv")).c_str()));
+  }
   if (two_arrays) {
     o("  " + st(fmt("sZ1[k * %d + t]", B), "v"));          // z1 = X v and z2 = z1 v are formed in the Wilke loop
   } else {
@@ -2273,9 +2312,15 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("  " + st(fmt("sZ1[k * %d + t]", B), "z1"));
     o("  " + st(fmt("sZ2[k * %d + t]", B), MUL("z1", "v")));
   }
-  o(fmt("  const %s ll = %s;", md.ty, horner("pl").c_str()));
-  o("  sl = " + FMA("X", EXP("ll"), "sl") + ";");
-  o("  sil = " + FMA("X", EXP(NEG("ll")), "sil") + ";");
+  if (direct) {
+    o(fmt("  const %s lam = %s;", md.ty, horner("pl").c_str()));
+    o("  sl = " + FMA("X", "lam", "sl") + ";");
+    o("  sil = " + FMA("X", DIV(md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0", "lam"), "sil") + ";");
+  } else {
+    o(fmt("  const %s ll = %s;", md.ty, horner("pl").c_str()));
+    o("  sl = " + FMA("X", EXP("ll"), "sl") + ";");
+    o("  sil = " + FMA("X", EXP(NEG("ll")), "sil") + ";");
+  }
   o("}");
   count_fma(ns * 14.0); count_exp(ns * 3.0);
   c.fp64 += 2 * ns;
@@ -2284,7 +2329,12 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("#pragma unroll 1");
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
-  o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
+  if (direct) {   // u = sqrt(eta)/W^(1/4) = eta / sqrt(eta) / W^(1/4)
+    o(fmt("  const %s eta = %s;", md.ty, horner("pv").c_str()));
+    o(fmt("  const %s u = %s;", md.ty, MUL(MUL("eta", RSQRT("eta")), ld("kx_iw4[k]")).c_str()));
+  } else {
+    o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
+  }
   if (two_arrays) {
     // float64 accuracy: den_k = sum_j a_kj X_j (1 + u_k v_j)^2 with w = 1 + u_k v_j formed per pair
     // (three products and one accumulation per pair; even and odd j in two chains)
@@ -2357,6 +2407,14 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   std::string vec;
   // exponential of one pair's polynomial, coefficients in the float4/double2/float2 triple (x, y, z)
   auto pexp = [&](const char* e, const char* x, const char* y, const char* z) {
+    if (direct && md.kind == TrMode::DF)   // 1/D_kj itself
+      return fmt("const kx_df %s = kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
+                 "kx_mk(%s.x, %s.y)), L, kx_mk(%s.z, %s.w)), L, kx_mk(%s.x, %s.y));",
+                 e, z, z, y, y, y, y, x, x, x, x);
+    if (direct && md.kind == TrMode::F64)
+      return fmt("const double %s = fma(fma(fma(fma(%s.x, L, %s.y), L, %s.x), L, %s.y), L, %s.x);", e, z, y, y, x, x);
+    if (direct)
+      return fmt("const float %s = fmaf(fmaf(fmaf(fmaf(%s.x, L, %s.y), L, %s.x), L, %s.y), L, %s.x);", e, z, y, y, x, x);
     if (md.kind == TrMode::DF)
       return fmt("const kx_df %s = kx_df_exp(kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
                  "kx_mk(%s.x, %s.y)), L, kx_mk(%s.z, %s.w)), L, kx_mk(%s.x, %s.y)));",
@@ -2421,8 +2479,13 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o(fmt("  const double Sk = %s, Xk = %s;", TOD(ld(fmt("sS[k * %d + t]", B))).c_str(), TOD(ld(fmt("sX[k * %d + t]", B))).c_str()));
   o("  const double* ds = kx_dself + 5 * k;");
   // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
-  o("  out2_[(long long)k * ld + i] = Sk > 0.0 ? fma(-Xk, kx_w[k] * iWbar, 1.0) * pr / Sk"
-    " : exp(fma(fma(fma(fma(ds[4], lnT, ds[3]), lnT, ds[2]), lnT, ds[1]), lnT, ds[0])) * pr;");
+  if (direct)
+    o(fmt("  out2_[(long long)k * ld + i] = Sk > 0.0 ? fma(-Xk, kx_w[k] * iWbar, 1.0) * pr / Sk"
+          " : pr / fma(fma(fma(fma(ds[4], lnT - %s, ds[3]), lnT - %s, ds[2]), lnT - %s, ds[1]), lnT - %s, ds[0]);",
+          D(L0).c_str(), D(L0).c_str(), D(L0).c_str(), D(L0).c_str()));
+  else
+    o("  out2_[(long long)k * ld + i] = Sk > 0.0 ? fma(-Xk, kx_w[k] * iWbar, 1.0) * pr / Sk"
+      " : exp(fma(fma(fma(fma(ds[4], lnT, ds[3]), lnT, ds[2]), lnT, ds[1]), lnT, ds[0])) * pr;");
   o("}");
   c.fp64 += 5 * ns + 4; c.div64 += ns + 2;
 }

@@ -51,6 +51,7 @@ struct Mechanism {
   std::vector<double> a_lo, a_hi;        // [ns][7] NASA-7
   std::vector<double> eta, lam;          // [ns][5]: ln eta, ln lambda as polynomials in ln T
   std::vector<double> dif;               // [ns][ns][5]: ln D_jk at p_atm
+  bool fit_direct = false;               // eta, lam, dif hold fits of eta, lambda and 1/D_jk themselves
   std::vector<Reaction> rx;
   int nr() const { return (int)rx.size(); }
 };

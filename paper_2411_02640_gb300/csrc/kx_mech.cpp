@@ -115,6 +115,11 @@ kx_status parse_mechanism(const std::string& path, Mechanism& m, std::string& er
       for (int j = 0; j < 7; ++j) m.a_lo[7 * k + j] = r.real();
       for (int j = 0; j < 7; ++j) m.a_hi[7 * k + j] = r.real();
       if (r.ok && !(m.Tmid[k] > 0.0)) return bad("NASA mid temperature must be positive");
+    } else if (key == "transport_fit") {
+      const std::string v = r.word();
+      if (v == "ln") m.fit_direct = false;
+      else if (v == "direct") m.fit_direct = true;
+      else return bad("transport_fit must be ln or direct");
     } else if (key == "eta" || key == "lambda") {
       long k = r.integer();
       if (!in_range(k, m.ns)) return bad("species index out of range");

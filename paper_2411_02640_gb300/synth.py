@@ -84,6 +84,9 @@ class Mechanism:
     lam_fit: np.ndarray              # [Ns, 5]  ln lambda = ..., W/(m K)
     diff_fit: np.ndarray             # [Ns, Ns, 5] ln D_jk at p_atm, m^2/s (symmetric)
     reactions: List[Reaction]
+    # "ln": the three fits are of ln eta, ln lambda, ln D_jk; "direct": of eta, lambda and of the
+    # reciprocal 1/D_jk themselves (the paper's polynomial fits, evaluated without exponentials)
+    transport_fit: str = "ln"
 
     @property
     def n_species(self) -> int:
@@ -122,6 +125,8 @@ def write_mechanism(mech: Mechanism, path: str) -> None:
         lo = " ".join(_f(v) for v in mech.nasa_lo[k])
         hi = " ".join(_f(v) for v in mech.nasa_hi[k])
         lines.append(f"nasa {k} {t} {lo} {hi}")
+    if mech.transport_fit != "ln":
+        lines.append(f"transport_fit {mech.transport_fit}")
     for k in range(ns):
         lines.append(f"eta {k} " + " ".join(_f(v) for v in mech.eta_fit[k]))
     for k in range(ns):
@@ -171,8 +176,12 @@ def read_mechanism(path: str) -> Mechanism:
     nasa_T, lo, hi = np.zeros((ns, 3)), np.zeros((ns, 7)), np.zeros((ns, 7))
     eta, lam, dif = np.zeros((ns, 5)), np.zeros((ns, 5)), np.zeros((ns, ns, 5))
     reactions: List[Reaction] = []
+    fit_kind = "ln"
     for t in it:
         key = t[0]
+        if key == "transport_fit":
+            fit_kind = t[1]
+            continue
         if key == "species_data":
             k = int(t[1]); species[k] = t[2]; W[k] = float(t[3]); inert[k] = bool(int(t[4]))
             comp[k] = [int(v) for v in t[5:5 + ne]]
@@ -214,7 +223,7 @@ def read_mechanism(path: str) -> Mechanism:
             pass
         else:
             raise ValueError(f"unknown record {key}")
-    return Mechanism(name, elements, species, comp, W, inert, nasa_T, lo, hi, eta, lam, dif, reactions)
+    return Mechanism(name, elements, species, comp, W, inert, nasa_T, lo, hi, eta, lam, dif, reactions, transport_fit=fit_kind)
 
 
 # --------------------------------------------------------------------------
@@ -569,6 +578,10 @@ STATE_SPECS = {
 CHUNK = 1 << 16
 
 
+for _n in list(STATE_SPECS):
+    STATE_SPECS[_n + "_direct"] = STATE_SPECS[_n]
+
+
 def make_states(ns: int, spec: StateSpec, start: int, count: int, dtype=np.float64):
     """States ``start .. start+count-1`` of the seeded stream: SoA arrays
     T[count], p[count], Y[ns, count].  Point i is drawn in chunk i // 2^16
@@ -600,9 +613,34 @@ def make_states(ns: int, spec: StateSpec, start: int, count: int, dtype=np.float
 _CACHE: Dict[str, Mechanism] = {}
 
 
+def direct_fits(mech: Mechanism) -> Mechanism:
+    """The same mechanism with its transport given by direct polynomial fits in
+    ln T of eta_k, lambda_k and 1/D_jk (least squares on 64 log-spaced points of
+    300-3000 K of the curves its ln fits describe); name suffixed "_direct"."""
+    import dataclasses
+    L = np.linspace(math.log(300.0), math.log(3000.0), 64)
+
+    def refit(c, sign):
+        return np.polyfit(L, np.exp(sign * np.polyval(c[::-1], L)), 4)[::-1]
+
+    ns = mech.n_species
+    eta = np.array([refit(mech.eta_fit[k], 1.0) for k in range(ns)])
+    lam = np.array([refit(mech.lam_fit[k], 1.0) for k in range(ns)])
+    dif = np.zeros_like(mech.diff_fit)
+    for j in range(ns):
+        for k in range(j, ns):
+            dif[j, k] = dif[k, j] = refit(mech.diff_fit[j, k], -1.0)
+    return dataclasses.replace(mech, name=mech.name + "_direct", eta_fit=eta, lam_fit=lam, diff_fit=dif,
+                               transport_fit="direct")
+
+
 def mechanism(name: str) -> Mechanism:
+    """A synthetic mechanism by name; "<name>_direct" is <name> with direct transport fits."""
     if name not in _CACHE:
-        _CACHE[name] = make_mechanism(SPECS[name])
+        if name.endswith("_direct"):
+            _CACHE[name] = direct_fits(mechanism(name[: -len("_direct")]))
+        else:
+            _CACHE[name] = make_mechanism(SPECS[name])
     return _CACHE[name]
 
 

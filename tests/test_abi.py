@@ -89,3 +89,17 @@ def test_toy_mechanisms_compile(tmp_path):
     m = kx.Mechanism(path, compile_only=1, cache_dir=str(tmp_path / "cache"))
     for k in ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed"):
         assert m.kernel_info(k)["registers"] > 0
+
+
+def test_transport_fit_keyword(tmp_path):
+    """The file's transport_fit record: "direct" loads, anything but ln or
+    direct is refused with KX_ERR_PARSE."""
+    path = synth.mechanism_file("h2o2_9_21_direct", str(tmp_path))
+    assert "transport_fit direct" in open(path).read()
+    m = kx.Mechanism(path, compile_only=1, lazy=1, cache_dir=str(tmp_path / "c"))
+    assert m.n_species == 9
+    bad = tmp_path / "bad.kxmech"
+    bad.write_text(open(path).read().replace("transport_fit direct", "transport_fit cubic"))
+    with pytest.raises(kx.KxError) as e:
+        kx.Mechanism(str(bad), compile_only=1, lazy=1, cache_dir=str(tmp_path / "c"))
+    assert e.value.status == 2          # KX_ERR_PARSE

@@ -116,6 +116,25 @@ def test_transport_fp64(torch, name, tr_mode):
     np.testing.assert_allclose(D[:, :n], D_r, rtol=1e-12)
 
 
+@pytest.mark.parametrize("name", ["h2o2_9_21_direct", "gri_53_325_direct"])
+@pytest.mark.parametrize("tr_mode", [0, 1])
+def test_transport_direct_fits(torch, name, tr_mode):
+    """Direct fits (eta, lambda, 1/D_kj as polynomials in ln T, no
+    exponentials): float64-accurate kernels (float pairs, tr_mode 0; native
+    float64, tr_mode 1) within 1e-12 of the oracle, the mixed kernels within
+    their 5e-6 bound."""
+    n = CASES[name.replace("_direct", "")]
+    T, p, Y = _states(name, n, start=23)
+    mech = mechanism(name, **({"tr_mode": 1} if tr_mode else {}))
+    Td, pd, Yd = to_device(torch, T, p, Y, ld=n + LD_PAD)
+    mu_r, lam_r, D_r = oracle(name).transport(T, p, Y)
+    for prec, tol in (("fp64", 1e-12), ("mixed", 5e-6)):
+        mu, lam, D = (t.cpu().numpy() for t in mech.transport(Td, pd, Yd, precision=prec))
+        np.testing.assert_allclose(mu, mu_r, rtol=tol)
+        np.testing.assert_allclose(lam, lam_r, rtol=tol)
+        np.testing.assert_allclose(D[:, :n], D_r, rtol=tol)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision_error_bounds(torch, name):
     """Mixed path: production rates within 2e-4 of the per-point scale

@@ -12,6 +12,7 @@ plausible slip (a dropped term, a wrong sign, a swapped index, an inverted
 ratio) breaks at least one of them.
 """
 import math
+import tempfile
 
 import numpy as np
 import pytest
@@ -366,6 +367,57 @@ def test_power_law_fits_and_pressure_scaling(tmp_path):
     np.testing.assert_allclose(lam, np.array([0.03, 0.04, 0.05, 0.06]) * 1500.0 ** 0.8, rtol=1e-13)
     assert D[1, 2] == pytest.approx(2e-5 * 1.3 * 1500.0 ** 1.75 / 2, rel=1e-13)
     np.testing.assert_allclose(D, D.T, rtol=0)
+
+
+def test_direct_fits_closed_form(tmp_path):
+    """Direct fits (transport_fit direct): eta, lambda and 1/D_kj are the
+    polynomials in ln T themselves, no exponential: eta = a + b ln T + c ln^2 T,
+    lambda likewise, D_kj = (p_atm/p) / (e0 + e1 ln T); a pure species has
+    mu = eta_k, a trace species k in pure j has D_k = D_kj."""
+    import dataclasses
+    from paper_2411_02640_gb300.synth import write_mechanism
+    mech, _ = toys.toy("dir0", [], str(tmp_path))
+    ns = mech.n_species
+    eta = np.array([[1e-5 * (1 + k), 2e-6, 3e-7, 0, 0] for k in range(ns)])
+    lam = np.array([[0.01 * (1 + k), 4e-3, -1e-4, 0, 0] for k in range(ns)])
+    dif = np.zeros((ns, ns, 5))
+    for j in range(ns):
+        for k in range(ns):
+            dif[j, k] = [3e4 * (1 + 0.1 * (j + k)), -2e3, 0, 0, 0]
+    d = dataclasses.replace(mech, name="dir", eta_fit=eta, lam_fit=lam, diff_fit=dif, transport_fit="direct")
+    path = str(tmp_path / "dir.kxmech")
+    write_mechanism(d, path)
+    o = oracle.Oracle(path)
+    T, p = 1234.5, 2.5 * P_ATM
+    L = math.log(T)
+    e, la, D = o.species_transport(T, p)
+    for k in range(ns):
+        assert e[k] == pytest.approx(1e-5 * (1 + k) + 2e-6 * L + 3e-7 * L * L, rel=1e-14)
+        assert la[k] == pytest.approx(0.01 * (1 + k) + 4e-3 * L - 1e-4 * L * L, rel=1e-14)
+    assert D[1, 3] == pytest.approx((P_ATM / p) / (3e4 * 1.4 - 2e3 * L), rel=1e-14)
+    mu, lm, Dk = o.transport(np.full(ns, T), np.full(ns, p), np.eye(ns))
+    np.testing.assert_allclose(mu, e, rtol=1e-14)
+    np.testing.assert_allclose(lm, la, rtol=1e-14)
+    Y = np.zeros((ns, 1)); Y[2, 0] = 1.0
+    _, _, Dk = o.transport([T], [p], Y)
+    assert Dk[0, 0] == pytest.approx(D[0, 2], rel=1e-13)
+
+
+def test_direct_fits_describe_the_same_curves():
+    """The generator's direct fits are least-squares refits of the curves its
+    ln fits describe: eta and lambda agree to the refit residual (< 0.5 %)
+    between the two forms of the 53/325 mechanism, so reading direct
+    coefficients as logarithms (or the reverse) cannot pass."""
+    ln_m, dir_m = synth.mechanism("gri_53_325"), synth.mechanism("gri_53_325_direct")
+    d = tempfile.mkdtemp()
+    o_ln = oracle.Oracle(synth.mechanism_file("gri_53_325", d))
+    o_dir = oracle.Oracle(synth.mechanism_file("gri_53_325_direct", d))
+    for T in (400.0, 900.0, 1700.0, 2600.0):
+        e1, l1, D1 = o_ln.species_transport(T, P_ATM)
+        e2, l2, D2 = o_dir.species_transport(T, P_ATM)
+        np.testing.assert_allclose(e2, e1, rtol=5e-3)
+        np.testing.assert_allclose(l2, l1, rtol=5e-3)
+        assert np.all(D2 > 0) and np.all(np.abs(np.log(D2 / D1)) < np.log(2.5))
 
 
 @pytest.mark.parametrize("name", MECHS)
