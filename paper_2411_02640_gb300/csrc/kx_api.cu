@@ -550,9 +550,18 @@ kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* l
 
 kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts) {
   if (!counts) return fail(KX_ERR_ARG, "null counts");
-  kx_status s = kx_kernel_info(h, kernel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-  if (s != KX_OK) return s;
-  const kx::OpCounts& c = find_kernel(h, kernel)->ops;
+  if (!h || !kernel) return fail(KX_ERR_ARG, "null argument");
+  Kernel* k = find_kernel(h, kernel);
+  if (!k) return fail(KX_ERR_ARG, std::string("no kernel ") + kernel);
+  {
+    // the counts come from the emitter alone: emit the source if it is not there yet (no compile)
+    std::lock_guard<std::mutex> lock(k->mu);
+    if (k->source.empty()) {
+      k->source = kx::emit_kernel(h->m, k->kind, k->eopt, k->entry, &k->ops);
+      if (k->source.empty()) return fail(KX_ERR_UNSUPPORTED, "kernel " + k->name + " is not available");
+    }
+  }
+  const kx::OpCounts& c = k->ops;
   const double v[8] = {c.fp64, c.fp32, c.exp64, c.log64, c.div64, c.exp32, c.log32, c.div32};
   std::memcpy(counts, v, sizeof v);
   return KX_OK;

@@ -1349,6 +1349,7 @@ struct DfClass {
   bool rev;
   Blend blend;
   int nre, npr;
+  bool kconst;          // k = A (beta = E = 0; elementary and three-body reactions): ln k needs no arithmetic
   std::vector<int> rx;
 };
 
@@ -1366,7 +1367,7 @@ std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
 void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c) {
   const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
   const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
-  o("  float lk = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
+  o(d.kconst ? "  float lk = f0.x;   // k = A" : "  float lk = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
   if (tb) {
     o(fmt("  const int2 e = kx_e%d[r];", ci));
     o("  const float4 f2 = f[2];");
@@ -1444,10 +1445,11 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     const Reaction& r = m.rx[i];
     const int nre = (int)entries(r.reac).size(), npr = (int)entries(r.prod).size();
     const Blend bl = (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) ? r.blend : Blend::Lindemann;
+    const bool kc = (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && r.k.beta == 0.0 && r.k.E == 0.0;
     auto it = std::find_if(cls.begin(), cls.end(), [&](const DfClass& d) {
-      return d.kind == r.kind && d.rev == r.reversible && d.blend == bl && d.nre == nre && d.npr == npr;
+      return d.kind == r.kind && d.rev == r.reversible && d.blend == bl && d.nre == nre && d.npr == npr && d.kconst == kc;
     });
-    if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, {}}); it = cls.end() - 1; }
+    if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, kc, {}}); it = cls.end() - 1; }
     it->rx.push_back(i);
   }
   std::string eff, plog, plogp;
@@ -1652,7 +1654,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       prefetch(d);
       o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
       o("  const float4 f0 = f[0], f1 = f[1];");
-      o("  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
+      o(d.kconst ? "  float b = f0.x;" : "  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
       if (d.kind == Kind::ThreeBody) {
         o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
         o("  b += e.y < 0 ? sv[kx_effd[e.x].k].x : lncMf + f1.z;");
@@ -1721,7 +1723,8 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     if (mx) {
       emit_class_mixed_body(o, d, (int)ci, E, c);
     } else {
-      o("  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+      o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
+                 : "  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
       if (tb) {
         o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
         o("  const float4 f2 = f[2];");
@@ -1792,7 +1795,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       o("  int sf = " + sfx + ";");
       o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
       o("  bool rev = false;");
-      c.fp32 += d.rx.size() * (2 * kDfFma + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
+      c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
       if (d.rev) {
         const int dn = d.npr - d.nre;
         o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");

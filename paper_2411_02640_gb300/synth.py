@@ -580,6 +580,7 @@ CHUNK = 1 << 16
 
 for _n in list(STATE_SPECS):
     STATE_SPECS[_n + "_direct"] = STATE_SPECS[_n]
+    STATE_SPECS[_n + "_special"] = STATE_SPECS[_n]
 
 
 def make_states(ns: int, spec: StateSpec, start: int, count: int, dtype=np.float64):
@@ -634,11 +635,41 @@ def direct_fits(mech: Mechanism) -> Mechanism:
                                transport_fit="direct")
 
 
+def special_rates(mech: Mechanism, seed: int = 7) -> Mechanism:
+    """The same mechanism with the special-case mix of Arrhenius parameters that
+    the paper counts for its ethanol mechanism (Sec. 2.3.1): about 27 % of the
+    rate constants with beta = E = 0 (k = A), 0.6 % with E = 0 and a small integer
+    beta (k = A T^beta), and 21 % sharing (beta, E) with another rate constant;
+    A is kept.  Drawn from its own seeded stream; name suffixed "_special"."""
+    import dataclasses
+    rng = np.random.Generator(np.random.PCG64([seed, 2411]))
+    rx = [dataclasses.replace(r) for r in mech.reactions]
+    slots = [(i, "rate") for i in range(len(rx))] + [(i, "rate_low") for i, r in enumerate(rx) if r.rate_low is not None]
+    order = rng.permutation(len(slots))
+    n_const, n_int, n_share = round(0.27 * len(slots)), max(1, round(0.006 * len(slots))), round(0.21 * len(slots))
+    general = [slots[j] for j in order[n_const + n_int + n_share:]]
+    for j in order[:n_const]:
+        i, f = slots[j]
+        setattr(rx[i], f, (getattr(rx[i], f)[0], 0.0, 0.0))
+    for j in order[n_const:n_const + n_int]:
+        i, f = slots[j]
+        setattr(rx[i], f, (getattr(rx[i], f)[0], float(rng.choice([-1.0, 1.0, 2.0])), 0.0))
+    for j in order[n_const + n_int:n_const + n_int + n_share]:
+        i, f = slots[j]
+        src_i, src_f = general[int(rng.integers(len(general)))]
+        a = getattr(rx[src_i], src_f)
+        setattr(rx[i], f, (getattr(rx[i], f)[0], a[1], a[2]))
+    return dataclasses.replace(mech, name=mech.name + "_special", reactions=rx)
+
+
 def mechanism(name: str) -> Mechanism:
-    """A synthetic mechanism by name; "<name>_direct" is <name> with direct transport fits."""
+    """A synthetic mechanism by name; "<name>_direct" is <name> with direct
+    transport fits, "<name>_special" with the paper's special-case Arrhenius mix."""
     if name not in _CACHE:
         if name.endswith("_direct"):
             _CACHE[name] = direct_fits(mechanism(name[: -len("_direct")]))
+        elif name.endswith("_special"):
+            _CACHE[name] = special_rates(mechanism(name[: -len("_special")]))
         else:
             _CACHE[name] = make_mechanism(SPECS[name])
     return _CACHE[name]
