@@ -77,6 +77,10 @@ typedef struct {
                          log space on the float32 pipe, one table-driven loop per reaction class,
                          wdot accumulated in float pairs under a per-state power-of-two scale;
                          1 native float64 */
+  int tr_layout;      /* transport kernels' per-thread species vectors: 1 all in shared-memory
+                         columns; 2 the mole fractions in local memory (half the shared memory per
+                         thread, twice the resident warps); 0 (default) or 3 every vector in local
+                         memory (no shared memory; residency set by registers, 64 by default) */
   int maxrreg;        /* register cap per thread for the generated kernels; 0 = compiler choice */
   int block;          /* threads per block; 0 = 128 */
   int lazy;           /* 0: compile the production-rate, thermo and transport kernels at load

@@ -312,6 +312,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.tr_mode < 0 || h->opt.tr_mode > 1) return fail(KX_ERR_ARG, "tr_mode must be 0 or 1");
   if (h->opt.rates_mode < 0 || h->opt.rates_mode > 2) return fail(KX_ERR_ARG, "rates_mode must be 0, 1 or 2");
   if (h->opt.rates_arith < 0 || h->opt.rates_arith > 2) return fail(KX_ERR_ARG, "rates_arith must be 0, 1 or 2");
+  if (h->opt.tr_layout < 0 || h->opt.tr_layout > 3) return fail(KX_ERR_ARG, "tr_layout must be 0, 1, 2 or 3");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
   h->opt.cache_dir = nullptr;
@@ -345,8 +346,9 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.scratch = std::strcmp(sp.name, "wdot_fp64_noalloc") == 0;
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
-      const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part);
-      int b = std::min(std::max(h->opt.block, 256), (216 * 1024 / per) / 32 * 32);
+      k->eopt.tr_layout = h->opt.tr_layout == 0 ? 3 : h->opt.tr_layout;
+      const int per = kx::transport_smem_per_thread(h->m, sp.mixed, sp.part, k->eopt.tr_layout);
+      int b = per == 0 ? h->opt.block : std::min(std::max(h->opt.block, 256), std::min(1024, (216 * 1024 / per) / 32 * 32));
       if (b >= 128) b = b / 128 * 128;   // whole warps on every SM sub-partition
       if (b < 32) return fail(KX_ERR_UNSUPPORTED, "mechanism too large for the transport kernel");
       k->eopt.block = b;

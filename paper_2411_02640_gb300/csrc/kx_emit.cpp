@@ -2165,6 +2165,17 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   // float64-accurate viscosity keeps two vectors per species (X, v = 1/u) in shared memory
   // and forms z1, z2 in the loop: two multiplies per pair buy twice the resident warps
   const bool two_arrays = md.kind != TrMode::F32 && opt.part != 2;
+  // X_k of this thread: a column of shared memory, or a per-thread local array (tr_layout 2: halves
+  // the shared memory per thread, so twice the warps are resident)
+  const bool xlocal = opt.tr_layout >= 2;
+  auto XS = [&](const std::string& idx) { return xlocal ? fmt("xl[%s]", idx.c_str()) : fmt("sX[%s * %d + t]", idx.c_str(), B); };
+  // the other vectors (z1 = v or X v, z2, and the diffusion sums S in the z1 slot): shared-memory
+  // columns, or per-thread local arrays (tr_layout 3: no shared memory at all)
+  const bool vlocal = opt.tr_layout == 3;
+  auto VS = [&](const char* arr, const std::string& idx) {
+    const std::string a = std::string(arr) == "sS" ? "sZ1" : arr;
+    return vlocal ? fmt("l%s[%s]", a.c_str() + 1, idx.c_str()) : fmt("%s[%s * %d + t]", a.c_str(), idx.c_str(), B);
+  };
   // ---- element literal, load, store and arithmetic spelled per mode
   auto lit = [&](double v) -> std::string {
     if (md.kind == TrMode::F64) return D(v);
@@ -2278,9 +2289,17 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   c.log64 += 1;
   if (L0 == 0.0) o("const double L = lnT;");
   else o(fmt("const %s L = %s;", md.ty, FROMD(fmt("lnT - %s", D(L0).c_str())).c_str()));
-  o(fmt("%s* const sX = (%s*)kx_dyn;", md.st, md.st));
-  o(fmt("%s* const sZ1 = sX + %d;", md.st, ns * B));
-  o(fmt("%s* const sZ2 = sZ1 + %d;", md.st, ns * B));
+  if (vlocal) {   // every species vector in per-thread local arrays
+    o(fmt("%s xl[%d], lZ1[%d], lZ2[%d];", md.st, ns, ns, ns));
+  } else if (xlocal) {   // X in a per-thread local array, the other vectors in shared memory
+    o(fmt("%s xl[%d];", md.st, ns));
+    o(fmt("%s* const sZ1 = (%s*)kx_dyn;", md.st, md.st));
+    o(fmt("%s* const sZ2 = sZ1 + %d;", md.st, ns * B));
+  } else {
+    o(fmt("%s* const sX = (%s*)kx_dyn;", md.st, md.st));
+    o(fmt("%s* const sZ1 = sX + %d;", md.st, ns * B));
+    o(fmt("%s* const sZ2 = sZ1 + %d;", md.st, ns * B));
+  }
   o("const int t = threadIdx.x;");
   o("double sy = 0.0, sY = 0.0;");
   o(fmt("for (int k = 0; k < %d; ++k) { const double Yk = Y_[(long long)k * ld + i]; sY += Yk; sy = fma(Yk, kx_iw[k], sy); }", ns));
@@ -2290,7 +2309,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   c.fp64 += 2 * ns + 1; c.div64 += 2;
   const bool p1 = opt.part != 2, p2 = opt.part != 1;
   if (!p1) {
-    o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(fmt("sX[k * %d + t]", B),
+    o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(XS("k"),
                                                     FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig")).c_str()));
     c.fp64 += ns;
   }
@@ -2300,7 +2319,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("#pragma unroll 1");
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const %s X = %s;", md.ty, FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig").c_str()));
-  o("  " + st(fmt("sX[k * %d + t]", B), "X"));
+  o("  " + st(XS("k"), "X"));
   o(fmt("  const %s* pv = kx_pv + 5 * k; const %s* pl = kx_pl + 5 * k;", md.st, md.st));
   if (direct) {   // v = W^(1/4)/sqrt(eta)
     o(fmt("  const %s eta = %s;", md.ty, horner("pv").c_str()));
@@ -2309,11 +2328,11 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o(fmt("  const %s v = %s;", md.ty, EXP(horner("pv")).c_str()));
   }
   if (two_arrays) {
-    o("  " + st(fmt("sZ1[k * %d + t]", B), "v"));          // z1 = X v and z2 = z1 v are formed in the Wilke loop
+    o("  " + st(VS("sZ1", "k"), "v"));          // z1 = X v and z2 = z1 v are formed in the Wilke loop
   } else {
     o(fmt("  const %s z1 = %s;", md.ty, MUL("X", "v").c_str()));
-    o("  " + st(fmt("sZ1[k * %d + t]", B), "z1"));
-    o("  " + st(fmt("sZ2[k * %d + t]", B), MUL("z1", "v")));
+    o("  " + st(VS("sZ1", "k"), "z1"));
+    o("  " + st(VS("sZ2", "k"), MUL("z1", "v")));
   }
   if (direct) {
     o(fmt("  const %s lam = %s;", md.ty, horner("pl").c_str()));
@@ -2347,15 +2366,15 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("  #pragma unroll 2");
     o(fmt("  for (int j = 0; j + 1 < %d; j += 2) {", ns));
     o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
-    o(fmt("    const %s xa = %s, va = %s, xb = %s, vb = %s;", md.ty, ld(fmt("sX[j * %d + t]", B)).c_str(),
-          ld(fmt("sZ1[j * %d + t]", B)).c_str(), ld(fmt("sX[(j + 1) * %d + t]", B)).c_str(), ld(fmt("sZ1[(j + 1) * %d + t]", B)).c_str()));
+    o(fmt("    const %s xa = %s, va = %s, xb = %s, vb = %s;", md.ty, ld(XS("j")).c_str(),
+          ld(VS("sZ1", "j")).c_str(), ld(XS("(j + 1)")).c_str(), ld(VS("sZ1", "(j + 1)")).c_str()));
     o(fmt("    const %s wa = %s, wb = %s;", md.ty, FMA("u", "va", ONE1).c_str(), FMA("u", "vb", ONE1).c_str()));
     o(fmt("    s0 = %s;", FMA(MUL("A", "xa"), MUL("wa", "wa"), "s0").c_str()));
     o(fmt("    t0 = %s;", FMA(MUL("Ab", "xb"), MUL("wb", "wb"), "t0").c_str()));
     o("  }");
     if (ns % 2) {
-      o(fmt("  { const %s A = %s, xa = %s, va = %s;", md.ty, ld(fmt("a[%d]", ns - 1)).c_str(), ld(fmt("sX[%d * %d + t]", ns - 1, B)).c_str(),
-            ld(fmt("sZ1[%d * %d + t]", ns - 1, B)).c_str()));
+      o(fmt("  { const %s A = %s, xa = %s, va = %s;", md.ty, ld(fmt("a[%d]", ns - 1)).c_str(), ld(XS(std::to_string(ns - 1))).c_str(),
+            ld(VS("sZ1", std::to_string(ns - 1))).c_str()));
       o(fmt("    const %s wa = %s;", md.ty, FMA("u", "va", ONE1).c_str()));
       o(fmt("    s0 = %s; }", FMA(MUL("A", "xa"), MUL("wa", "wa"), "s0").c_str()));
     }
@@ -2371,10 +2390,10 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   // the three vectors of species j: X_j, z1_j = X_j v_j, z2_j = z1_j v_j
   auto vecs = [&](const std::string& jj, const char* sfx) {
     if (!two_arrays)
-      return fmt("const %s x%s = %s, y%s = %s, z%s = %s;", md.ty, sfx, ld(fmt("sX[%s * %d + t]", jj.c_str(), B)).c_str(), sfx,
-                 ld(fmt("sZ1[%s * %d + t]", jj.c_str(), B)).c_str(), sfx, ld(fmt("sZ2[%s * %d + t]", jj.c_str(), B)).c_str());
+      return fmt("const %s x%s = %s, y%s = %s, z%s = %s;", md.ty, sfx, ld(XS(jj)).c_str(), sfx,
+                 ld(VS("sZ1", jj)).c_str(), sfx, ld(VS("sZ2", jj)).c_str());
     return fmt("const %s x%s = %s, v%s = %s; const %s y%s = %s; const %s z%s = %s;", md.ty, sfx,
-               ld(fmt("sX[%s * %d + t]", jj.c_str(), B)).c_str(), sfx, ld(fmt("sZ1[%s * %d + t]", jj.c_str(), B)).c_str(), md.ty,
+               ld(XS(jj)).c_str(), sfx, ld(VS("sZ1", jj)).c_str(), md.ty,
                sfx, MUL(fmt("x%s", sfx), fmt("v%s", sfx)).c_str(), md.ty, sfx, MUL(fmt("y%s", sfx), fmt("v%s", sfx)).c_str());
   };
   o("    " + vecs("j", "a") + " " + vecs("(j + 1)", "b"));
@@ -2390,7 +2409,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   const std::string two_s1 = md.kind == TrMode::DF ? "kx_mk(2.f * s1.hi, 2.f * s1.lo)" : md.kind == TrMode::F32 ? "2.0f * s1" : "2.0 * s1";
   o(fmt("  const %s den = %s;", md.ty, FMA("u", FMA("u", "s2", two_s1), "s0").c_str()));
   }
-  o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD(ld(fmt("sX[k * %d + t]", B))).c_str(), TOD(MUL("u", "u")).c_str(),
+  o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD(ld(XS("k"))).c_str(), TOD(MUL("u", "u")).c_str(),
         TOD("den").c_str()));
   o("}");
   count_fma(ns * (3.0 * ns + 8)); count_exp(ns);
@@ -2401,8 +2420,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   }  // part 1
   if (!p2) return;
   // mixture-averaged diffusion, S in the sZ1 columns
-  o(fmt("%s* const sS = sZ1;", md.st));
-  o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(fmt("sS[k * %d + t]", B), ZERO).c_str()));
+  if (!vlocal) o(fmt("%s* const sS = sZ1;", md.st));
+  o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(VS("sS", "k"), ZERO).c_str()));
   o(fmt("const %s* cf = kx_dc;", md.st));
   // the next pair's coefficients are loaded one iteration ahead (the table
   // carries one zero pair of padding), so their latency hides behind the
@@ -2439,9 +2458,9 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("    if (j == k) continue;");
     o("    " + take);
     o("    " + pexp("e", "c0", "c1", "c2"));
-    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
+    o("    Sk = " + FMA(ld(XS("j")), "e", "Sk") + ";");
     o("  }");
-    o("  " + st(fmt("sS[k * %d + t]", B), "Sk"));
+    o("  " + st(VS("sS", "k"), "Sk"));
     o("}");
     count_fma(ns * (ns - 1) * 5.0); count_exp(ns * (ns - 1.0));
   } else {
@@ -2449,8 +2468,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     // unroll); the coefficient stream is read one pair ahead
     o("#pragma unroll 1");
     o(fmt("for (int k = 0; k < %d; ++k) {", ns - 1));
-    o(fmt("  %s Sk = %s, Sk1 = %s;", md.ty, ld(fmt("sS[k * %d + t]", B)).c_str(), ZERO.c_str()));
-    o(fmt("  const %s Xk = %s;", md.ty, ld(fmt("sX[k * %d + t]", B)).c_str()));
+    o(fmt("  %s Sk = %s, Sk1 = %s;", md.ty, ld(VS("sS", "k")).c_str(), ZERO.c_str()));
+    o(fmt("  const %s Xk = %s;", md.ty, ld(XS("k")).c_str()));
     o("  int j = k + 1;");
     o("  #pragma unroll 2");
     o(fmt("  for (; j + 1 < %d; j += 2) {", ns));
@@ -2458,28 +2477,28 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("    cq += 6; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];");
     o("    " + pexp("ea", "a0", "a1", "a2"));
     o("    " + pexp("eb", "b0", "b1", "b2"));
-    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "ea", "Sk") + ";");
-    o("    Sk1 = " + FMA(ld(fmt("sX[(j + 1) * %d + t]", B)), "eb", "Sk1") + ";");
-    o(fmt("    const %s Sa = %s;", md.ty, FMA("Xk", "ea", ld(fmt("sS[j * %d + t]", B))).c_str()));
-    o(fmt("    const %s Sb = %s;", md.ty, FMA("Xk", "eb", ld(fmt("sS[(j + 1) * %d + t]", B))).c_str()));
-    o("    " + st(fmt("sS[j * %d + t]", B), "Sa"));
-    o("    " + st(fmt("sS[(j + 1) * %d + t]", B), "Sb"));
+    o("    Sk = " + FMA(ld(XS("j")), "ea", "Sk") + ";");
+    o("    Sk1 = " + FMA(ld(XS("(j + 1)")), "eb", "Sk1") + ";");
+    o(fmt("    const %s Sa = %s;", md.ty, FMA("Xk", "ea", ld(VS("sS", "j"))).c_str()));
+    o(fmt("    const %s Sb = %s;", md.ty, FMA("Xk", "eb", ld(VS("sS", "(j + 1)"))).c_str()));
+    o("    " + st(VS("sS", "j"), "Sa"));
+    o("    " + st(VS("sS", "(j + 1)"), "Sb"));
     o("  }");
     o(fmt("  if (j < %d) {", ns));
     o("    " + take);
     o("    " + pexp("e", "c0", "c1", "c2"));
-    o("    Sk = " + FMA(ld(fmt("sX[j * %d + t]", B)), "e", "Sk") + ";");
-    o(fmt("    const %s Sj = %s;", md.ty, FMA("Xk", "e", ld(fmt("sS[j * %d + t]", B))).c_str()));
-    o("    " + st(fmt("sS[j * %d + t]", B), "Sj"));
+    o("    Sk = " + FMA(ld(XS("j")), "e", "Sk") + ";");
+    o(fmt("    const %s Sj = %s;", md.ty, FMA("Xk", "e", ld(VS("sS", "j"))).c_str()));
+    o("    " + st(VS("sS", "j"), "Sj"));
     o("  }");
     const std::string ONE2 = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0";
-    o("  " + st(fmt("sS[k * %d + t]", B), FMA("Sk1", ONE2, "Sk")));
+    o("  " + st(VS("sS", "k"), FMA("Sk1", ONE2, "Sk")));
     o("}");
     count_fma(ns * (ns - 1) / 2.0 * 6); count_exp(ns * (ns - 1) / 2.0);
   }
   o(fmt("const double pr = %s / P;", D(P_ATM).c_str()));
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
-  o(fmt("  const double Sk = %s, Xk = %s;", TOD(ld(fmt("sS[k * %d + t]", B))).c_str(), TOD(ld(fmt("sX[k * %d + t]", B))).c_str()));
+  o(fmt("  const double Sk = %s, Xk = %s;", TOD(ld(VS("sS", "k"))).c_str(), TOD(ld(XS("k"))).c_str()));
   o("  const double* ds = kx_dself + 5 * k;");
   // D_k = (Wbar - X_k W_k)/Wbar / (S_k p/p_atm); a species with no partner present gets D_kk
   if (direct)
@@ -2496,9 +2515,11 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
 }  // namespace
 
 // Shared memory per thread of the transport kernels, in bytes.
-int transport_smem_per_thread(const Mechanism& m, bool mixed, int part) {
-  // diffusion: X and S; viscosity: X, X/u, X/u^2 (float32) or X and 1/u (float64 accuracy)
-  return ((part == 2 || !mixed) ? 2 : 3) * m.ns * (mixed ? 4 : 8);
+int transport_smem_per_thread(const Mechanism& m, bool mixed, int part, int layout) {
+  // diffusion: X and S; viscosity: X, X/u, X/u^2 (float32) or X and 1/u (float64 accuracy);
+  // layout 2 keeps X in local memory
+  if (layout == 3) return 0;
+  return (((part == 2 || !mixed) ? 2 : 3) - (layout == 2 ? 1 : 0)) * m.ns * (mixed ? 4 : 8);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -2569,18 +2590,20 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   // a register cap is expressed as a minimum number of resident blocks (ptxas
   // ignores --maxrregcount for kernels that carry launch bounds).  Defaults,
   // measured on the 53/325 mechanism (2^20 states): the unrolled native
-  // float64 rate kernel runs best at 128 registers and the unrolled mixed one
-  // at 96 (more resident warps hide instruction fetch, table and dependence
+  // float64 rate kernel runs best at 128 registers and the mixed ones at 96
+  // (more resident warps hide instruction fetch, table and dependence
   // latency better than the spills they cost); the float-pair rate kernel at
   // 128 (four blocks: its pipelined loops keep two reactions' operands live);
-  // the transport kernels, whose residency is set by shared memory, with the
-  // compiler allowed 128 registers (more independent chains in flight).
+  // the transport kernels with their vectors in local memory at 64 (eight
+  // blocks of 128: residency is what hides the local-memory latency), with
+  // shared-memory columns at 128; thermo at 48.
   int rreg = opt.maxrreg;
   const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
   if (rreg == 0 && unrolled_rates) rreg = opt.mixed ? 96 : 128;
-  if (rreg == 0 && df_rates) rreg = 128;
-  if (rreg == 0 && kind == KernelKind::Transport) rreg = 128;
+  if (rreg == 0 && df_rates) rreg = opt.mixed ? 96 : 128;
+  if (rreg == 0 && kind == KernelKind::Transport) rreg = opt.tr_layout == 3 ? 64 : 128;
+  if (rreg == 0 && kind == KernelKind::Thermo) rreg = 48;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;

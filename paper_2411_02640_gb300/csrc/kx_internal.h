@@ -66,6 +66,7 @@ struct EmitOptions {
   int diff_mode = 1;        // 1 symmetric pairs, 2 full matrix
   int kc_mode = 0;          // 0 log space, 1 per-species exponential products
   int tr_mode = 0;          // float64 transport: 0 double-float on the float32 pipe, 1 native float64
+  int tr_layout = 3;        // transport species vectors: 1 all in shared memory, 2 X in local memory, 3 all local
   int block = 128;
   int part = 0;             // transport: 0 all outputs, 1 viscosity and conductivity, 2 diffusion
   int maxrreg = 0;          // register cap per thread (0: compiler choice)
@@ -90,7 +91,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
 inline int rates_scratch_per_thread(const Mechanism& m) { return 24 * m.ns; }
 
 // Dynamic shared memory per thread that a kernel of this kind needs.
-int transport_smem_per_thread(const Mechanism& m, bool mixed, int part);
+int transport_smem_per_thread(const Mechanism& m, bool mixed, int part, int layout);
 
 // Device-side helper functions prepended to every generated kernel.
 extern const char* kDevicePrelude;

@@ -31,7 +31,7 @@ class KxError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("diff_mode", ctypes.c_int), ("kc_mode", ctypes.c_int), ("tr_mode", ctypes.c_int), ("rates_mode", ctypes.c_int),
-                ("rates_arith", ctypes.c_int), ("maxrreg", ctypes.c_int),
+                ("rates_arith", ctypes.c_int), ("tr_layout", ctypes.c_int), ("maxrreg", ctypes.c_int),
                 ("block", ctypes.c_int), ("lazy", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("libmath", ctypes.c_int), ("compile_only", ctypes.c_int), ("cache_dir", ctypes.c_char_p)]
 
