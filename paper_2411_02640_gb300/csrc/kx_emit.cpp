@@ -426,6 +426,13 @@ template <typename V> struct kx_strided {
   long long s;
   __device__ __forceinline__ V& operator[](int k) const { return p[(long long)k * s]; }
 };
+// nu q for a small integer nu: an exact scaling of both parts for |nu| <= 2,
+// a float-pair product otherwise (nu is the same for every thread of a warp)
+__device__ __forceinline__ kx_df kx_df_nu(kx_df q, int nu) {
+  const float f = kx_i2f(nu);
+  if (nu >= -2 && nu <= 2) return kx_mk(__fmul_rn(q.hi, f), __fmul_rn(q.lo, f));
+  return kx_df_mulf(q, f);
+}
 // S ln2 as a float pair (exact product terms for |S| < 2^11)
 __device__ __forceinline__ kx_df kx_df_ln2_mul(int S) {
   const float sf = __fsub_rn(__int_as_float(0x4b400000 + S), KX_RND_F);
@@ -1425,7 +1432,8 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
     std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
     o("  kx_df dl = " + first + ";");
     for (int j = 1; j < E; ++j) o(fmt("  dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
-    if (dn != 0) o(fmt("  dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+    if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
+    else if (dn != 0) o(fmt("  dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
     o("  const double q = kx_net_rate_s(lnRf, dl.hi, sf, " + srx + ");");
     c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + 10); c.exp32 += d.rx.size() * 2;
   } else {
@@ -1803,7 +1811,8 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         o("    kx_df dl = " + first + ";");
         for (int j = 1; j < E; ++j)
           o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
-        if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+        if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
+      else if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
         o("    const int sr = " + srx + ";");
         o("    rev = dl.hi > 0.0f;");
         o("    if (rev) L = kx_df_add(lf, dl);");
@@ -1838,7 +1847,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     } else {
       // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
       for (int j = 0; j < E; ++j)
-        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add(wl%d, kx_df_mulf(qp, kx_i2f(cj))); }", j, j, j));
+        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
       o("  qp = q;");
       for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
       c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
@@ -1851,7 +1860,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
               j, j));
     else if (!rop)
       for (int j = 0; j < E; ++j)
-        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add(w[kk], kx_df_mulf(qp, kx_i2f(cj))); } }",
+        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add(w[kk], kx_df_nu(qp, cj)); } }",
               j, j));
     --o.ind;
     o("}");
