@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 MECH = "gri_53_325"
 POINTS = 1 << 20
-E2E_CHUNK = 1 << 17     # states per chunk of the end-to-end host pipeline
+E2E_CHUNK = 1 << 18     # states per chunk of the end-to-end host pipeline
 METRIC = "Mpoints/s wdot+thermo+transport (53sp/325rxn)"
 CACHE = os.environ.get("KX_CACHE_DIR", os.path.join(ROOT, ".kxcache"))
 
@@ -307,7 +307,7 @@ def run_kx(args):
             "Dk": torch.empty((ns, n), dtype=torch.float64).pin_memory()}
     for k in ("cp", "h", "mu", "lam"):
         hout[k] = torch.empty(n, dtype=torch.float64).pin_memory()
-    chunk = min(n, E2E_CHUNK)
+    chunk = min(n, args.e2e_chunk)
     ws = torch.empty(2 * chunk * mech.evaluate_host_bytes_per_state(7), dtype=torch.uint8, device=dev)
     ss = (torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev))
 
@@ -575,6 +575,7 @@ def main():
     ap.add_argument("--points", type=int, default=POINTS, help="states per GPU (profiling of smaller cases)")
     ap.add_argument("--maxrreg", type=int, default=0, help="register cap for the generated kernels (0: compiler)")
     ap.add_argument("--rates-mode", type=int, default=0, help="0 automatic, 1 unrolled, 2 table-driven rate kernels")
+    ap.add_argument("--e2e-chunk", type=int, default=E2E_CHUNK, help="states per chunk of the end-to-end pipeline")
     ap.add_argument("--tr-layout", type=int, default=0, help="transport species vectors: 1 shared, 2 X local, 3 (default) all local")
     ap.add_argument("--rates-arith", type=int, default=0,
                     help="float64-accurate rates: 0 double-float (default), 1 native float64")

@@ -197,9 +197,10 @@ int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
 
 /* Production rates, thermo and/or transport for states held in HOST memory
  * (pinned for asynchronous copies), pipelined in chunks over two streams:
- * while one chunk's kernels run on one stream, the next chunk's inputs are
- * copied in and the previous chunk's outputs copied out on the other, so the
- * host<->device copies overlap the arithmetic.  T, p [n], Y [N_s][ld] are
+ * the kernels run chunk after chunk on stream_a while stream_b copies the
+ * next chunk's inputs in and the previous chunk's outputs out (events order
+ * the two), so the host<->device copies overlap the arithmetic and no two
+ * chunks' kernels compete for the device.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
  * are host outputs, those not selected by `outputs` may be NULL.
  * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk

@@ -598,35 +598,75 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   if (max_chunk > 0) c = std::min(c, std::max<int64_t>(256, max_chunk / 256 * 256));
   if (c < 256) return fail(KX_ERR_ARG, "workspace smaller than two chunks of 256 states");
   c = std::min(c, (n + 255) / 256 * 256);
-  cudaStream_t st[2] = {(cudaStream_t)stream_a, (cudaStream_t)stream_b};
-  for (int64_t c0 = 0, i = 0; c0 < n; c0 += c, ++i) {
-    const int64_t m = std::min(c, n - c0);
-    cudaStream_t q = st[i % 2];
+  // kernels in order on stream_a (one chunk's kernels at a time), every copy on stream_b, the next
+  // chunk's inputs copied in one chunk ahead; per-slot events order the two streams
+  cudaStream_t qa = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b;
+  cudaEvent_t ev[6] = {};
+  struct Events {
+    cudaEvent_t* e;
+    ~Events() { for (int j = 0; j < 6; ++j) if (e[j]) cudaEventDestroy(e[j]); }
+  } guard{ev};
+  for (int j = 0; j < 6; ++j) {
+    cudaError_t e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+  }
+  cudaEvent_t* in_done = ev;          // inputs of the slot copied in
+  cudaEvent_t* comp_done = ev + 2;    // kernels of the slot finished
+  cudaEvent_t* out_done = ev + 4;     // outputs of the slot copied out
+  const int64_t nchunks = (n + c - 1) / c;
+  auto slot = [&](int64_t i, double** dT, double** dp, double** dY, double** dw, double** dcp, double** dh, double** dmu,
+                  double** dl, double** dD) {
     double* b = (double*)((char*)workspace + (size_t)(i % 2) * (size_t)c * (size_t)per);
-    double *dT = b, *dp = dT + c, *dY = dp + c, *nx = dY + ns * c;
-    double *dw = nullptr, *dcp = nullptr, *dh = nullptr, *dmu = nullptr, *dl = nullptr, *dD = nullptr;
-    if (outputs & KX_OUT_WDOT) { dw = nx; nx += ns * c; }
-    if (outputs & KX_OUT_THERMO) { dcp = nx; dh = nx + c; nx += 2 * c; }
-    if (outputs & KX_OUT_TRANSPORT) { dmu = nx; dl = nx + c; dD = nx + 2 * c; nx += (2 + ns) * c; }
-    cudaError_t e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, q);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p + c0, m * 8, cudaMemcpyHostToDevice, q);
+    *dT = b; *dp = b + c; *dY = b + 2 * c;
+    double* nx = *dY + ns * c;
+    *dw = *dcp = *dh = *dmu = *dl = *dD = nullptr;
+    if (outputs & KX_OUT_WDOT) { *dw = nx; nx += ns * c; }
+    if (outputs & KX_OUT_THERMO) { *dcp = nx; *dh = nx + c; nx += 2 * c; }
+    if (outputs & KX_OUT_TRANSPORT) { *dmu = nx; *dl = nx + c; *dD = nx + 2 * c; }
+  };
+  auto copy_in = [&](int64_t i) -> kx_status {
+    double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
+    slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
+    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    cudaError_t e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, qb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p + c0, m * 8, cudaMemcpyHostToDevice, qb);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-    if ((s = kx_copy_rows_async(dY, c, Y + c0, ld, ns, m, q)) != KX_OK) return s;
-    if ((outputs & KX_OUT_WDOT) && (s = kx_production_rates(h, dT, dp, dY, c, dw, m, precision, q)) != KX_OK) return s;
-    if ((outputs & KX_OUT_THERMO) && (s = kx_thermo(h, dT, dp, dY, c, dcp, dh, m, q)) != KX_OK) return s;
-    if ((outputs & KX_OUT_TRANSPORT) && (s = kx_transport(h, dT, dp, dY, c, dmu, dl, dD, m, precision, q)) != KX_OK) return s;
-    if ((outputs & KX_OUT_WDOT) && (s = kx_copy_rows_async(wdot + c0, ldo, dw, c, ns, m, q)) != KX_OK) return s;
+    kx_status s2 = kx_copy_rows_async(dY, c, Y + c0, ld, ns, m, qb);
+    if (s2 != KX_OK) return s2;
+    e = cudaEventRecord(in_done[i % 2], qb);
+    return e == cudaSuccess ? KX_OK : cuda_fail(e, "cudaEventRecord");
+  };
+  if ((s = copy_in(0)) != KX_OK) return s;
+  for (int64_t i = 0; i < nchunks; ++i) {
+    // the next chunk's inputs (its slot's previous kernels finished: stream_b waited for them
+    // before copying that chunk's outputs out)
+    if (i + 1 < nchunks && (s = copy_in(i + 1)) != KX_OK) return s;
+    double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
+    slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
+    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    cudaError_t e = cudaStreamWaitEvent(qa, in_done[i % 2], 0);
+    if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(qa, out_done[i % 2], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((outputs & KX_OUT_WDOT) && (s = kx_production_rates(h, dT, dp, dY, c, dw, m, precision, qa)) != KX_OK) return s;
+    if ((outputs & KX_OUT_THERMO) && (s = kx_thermo(h, dT, dp, dY, c, dcp, dh, m, qa)) != KX_OK) return s;
+    if ((outputs & KX_OUT_TRANSPORT) && (s = kx_transport(h, dT, dp, dY, c, dmu, dl, dD, m, precision, qa)) != KX_OK) return s;
+    e = cudaEventRecord(comp_done[i % 2], qa);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(qb, comp_done[i % 2], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "event ordering");
+    if ((outputs & KX_OUT_WDOT) && (s = kx_copy_rows_async(wdot + c0, ldo, dw, c, ns, m, qb)) != KX_OK) return s;
     if (outputs & KX_OUT_THERMO) {
-      e = cudaMemcpyAsync(cp + c0, dcp, m * 8, cudaMemcpyDeviceToHost, q);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(hmass + c0, dh, m * 8, cudaMemcpyDeviceToHost, q);
+      e = cudaMemcpyAsync(cp + c0, dcp, m * 8, cudaMemcpyDeviceToHost, qb);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hmass + c0, dh, m * 8, cudaMemcpyDeviceToHost, qb);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
     if (outputs & KX_OUT_TRANSPORT) {
-      e = cudaMemcpyAsync(mu + c0, dmu, m * 8, cudaMemcpyDeviceToHost, q);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(lambda + c0, dl, m * 8, cudaMemcpyDeviceToHost, q);
+      e = cudaMemcpyAsync(mu + c0, dmu, m * 8, cudaMemcpyDeviceToHost, qb);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(lambda + c0, dl, m * 8, cudaMemcpyDeviceToHost, qb);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-      if ((s = kx_copy_rows_async(Dk + c0, ldo, dD, c, ns, m, q)) != KX_OK) return s;
+      if ((s = kx_copy_rows_async(Dk + c0, ldo, dD, c, ns, m, qb)) != KX_OK) return s;
     }
+    e = cudaEventRecord(out_done[i % 2], qb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   }
   return KX_OK;
 }
