@@ -45,6 +45,7 @@ class Request:
     future: cf.Future
     t_submit: float = 0.0
     t_done: float = 0.0
+    out: Optional[Dict[str, object]] = None   # caller-owned host outputs (pinned): wdot, mu, lam, Dk
 
     @property
     def n(self) -> int:
@@ -104,7 +105,13 @@ class Server:
         ns = self.mechs[name].n_species
         return 8 * ((2 + ns) + ns + ((2 + ns) if transport else 0))
 
-    def submit(self, name: str, T, p, Y, precision: str = "mixed", transport: bool = False) -> cf.Future:
+    def submit(self, name: str, T, p, Y, precision: str = "mixed", transport: bool = False,
+               out: Optional[Dict[str, object]] = None) -> cf.Future:
+        """Queue one request; ``out`` optionally holds the caller's host
+        output tensors (float64, pinned for asynchronous copies): ``wdot``
+        [N_s, n] and, with transport, ``mu``, ``lam`` [n] and ``Dk`` [N_s, n];
+        the results are copied straight into them and the Result holds views
+        of them (a CFD rank reuses its buffers from step to step)."""
         if name not in self.mechs:
             raise KeyError(name)
         if self.error is not None:
@@ -120,9 +127,19 @@ class Server:
             if t.dim() == 2 and t.stride(1) != 1:
                 t = t.contiguous()
             return t
-        req = Request(name, host(T), host(p), host(Y), precision, bool(transport), fut, time.perf_counter())
+        req = Request(name, host(T), host(p), host(Y), precision, bool(transport), fut, time.perf_counter(), out=out)
         if req.Y.dim() != 2 or req.Y.shape[0] != self.mechs[name].n_species or req.Y.shape[1] != req.n:
             raise ValueError("Y must be [N_s, n]")
+        if out is not None:
+            ns = self.mechs[name].n_species
+            want = {"wdot": (ns, req.n)}
+            if transport:
+                want.update(mu=(req.n,), lam=(req.n,), Dk=(ns, req.n))
+            for k, shp in want.items():
+                t = out.get(k)
+                if not (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and not t.is_cuda and tuple(t.shape) == shp
+                        and t.stride(-1) == 1):
+                    raise ValueError(f"out[{k!r}] must be a host float64 tensor of shape {shp} with unit column stride")
         if req.n * self.bytes_per_point(name, transport) > self.budget:
             fut.set_exception(MemoryError(f"request of {req.n} states exceeds the device-memory budget"))
             return fut
@@ -249,10 +266,20 @@ class Server:
                 h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
                 h.copy_(t, non_blocking=True)
                 return h
-            outs = {"wdot": down(w)}
+            dev = {"wdot": w}
             if transport:
-                mu, lam, D = mech.transport(T, p, Y, precision=prec, stream=stream)
-                outs.update(mu=down(mu), lam=down(lam), Dk=down(D))
+                dev["mu"], dev["lam"], dev["Dk"] = mech.transport(T, p, Y, precision=prec, stream=stream)
+            # requests that brought their own host buffers get their outputs copied straight into
+            # them (one copy per request and output); the others share pinned staging buffers
+            outs = {k: down(t) for k, t in dev.items()} if any(r.out is None for r in reqs) else {}
+            for r, o in zip(reqs, offs):
+                if r.out is None:
+                    continue
+                for k, t in dev.items():
+                    if t.dim() == 2:
+                        copy_rows(r.out[k], t[:, o:o + r.n], stream=stream)
+                    else:
+                        r.out[k].copy_(t[o:o + r.n], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.launches += 1
@@ -275,12 +302,16 @@ class Server:
         now = time.perf_counter()
         for b in done:
             for r, o in zip(b.reqs, b.offsets):
-                w = b.outs["wdot"][:, o:o + r.n].numpy()
-                res = Result(wdot=w)
-                if r.transport:
-                    res.mu = b.outs["mu"][o:o + r.n].numpy()
-                    res.lam = b.outs["lam"][o:o + r.n].numpy()
-                    res.Dk = b.outs["Dk"][:, o:o + r.n].numpy()
+                if r.out is not None:
+                    res = Result(wdot=r.out["wdot"].numpy())
+                    if r.transport:
+                        res.mu, res.lam, res.Dk = (r.out[k].numpy() for k in ("mu", "lam", "Dk"))
+                else:
+                    res = Result(wdot=b.outs["wdot"][:, o:o + r.n].numpy())
+                    if r.transport:
+                        res.mu = b.outs["mu"][o:o + r.n].numpy()
+                        res.lam = b.outs["lam"][o:o + r.n].numpy()
+                        res.Dk = b.outs["Dk"][:, o:o + r.n].numpy()
                 r.t_done = now
                 res.latency_s = now - r.t_submit
                 self.latencies.append(res.latency_s)

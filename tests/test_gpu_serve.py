@@ -106,3 +106,36 @@ def test_failure_in_the_loop_fails_the_waiting_requests(server_parts, monkeypatc
     with pytest.raises(RuntimeError):
         srv.submit("h2o2_9_21", T, p, Y)
     srv.stop()
+
+
+def test_caller_owned_outputs(server_parts):
+    """Requests that bring their own pinned host buffers get bit-identical
+    results written into them, alone and coalesced with requests that do
+    not; the Result's arrays are views of the caller's buffers."""
+    import torch
+    from paper_2411_02640_gb300.serve import Server
+    name = "gri_53_325"
+    ns = server_parts[name].n_species
+    reqs = [_req(name, n, 1000 + 7 * n, 0) for n in (3000, 5000, 7000)]
+    outs = []
+    for T, p, Y in reqs:
+        n = T.shape[0]
+        outs.append({"wdot": torch.empty((ns, n), dtype=torch.float64).pin_memory(),
+                     "mu": torch.empty(n, dtype=torch.float64).pin_memory(),
+                     "lam": torch.empty(n, dtype=torch.float64).pin_memory(),
+                     "Dk": torch.empty((ns, n), dtype=torch.float64).pin_memory()})
+    with Server(server_parts, hbm_budget=2 << 30, streams=2) as srv:
+        # the middle request keeps the server's staging buffers: one coalesced batch mixes both kinds
+        futs = [srv.submit(name, T, p, Y, precision="fp64", transport=True, out=(o if i != 1 else None))
+                for i, ((T, p, Y), o) in enumerate(zip(reqs, outs))]
+        res = [f.result(timeout=300) for f in futs]
+    with Server(server_parts, hbm_budget=2 << 30, streams=1, coalesce=False) as srv:
+        ref = [srv.submit(name, T, p, Y, precision="fp64", transport=True).result(timeout=300) for T, p, Y in reqs]
+    for i, (a, b) in enumerate(zip(res, ref)):
+        for k in ("wdot", "mu", "lam", "Dk"):
+            assert np.array_equal(getattr(a, k), getattr(b, k)), (i, k)
+    assert np.shares_memory(res[0].wdot, outs[0]["wdot"].numpy())
+    with Server(server_parts, hbm_budget=2 << 30) as srv:
+        T, p, Y = reqs[0]
+        with pytest.raises(ValueError):
+            srv.submit(name, T, p, Y, transport=True, out={"wdot": outs[0]["wdot"]})   # transport outputs missing
