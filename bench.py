@@ -586,7 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=POINTS, help="states per GPU (profiling of smaller cases)")
     ap.add_argument("--maxrreg", type=int, default=0, help="register cap for the generated kernels (0: compiler)")
-    ap.add_argument("--rates-mode", type=int, default=0, help="0 automatic, 1 unrolled, 2 table-driven, 3 reaction classes without pipelining")
+    ap.add_argument("--rates-mode", type=int, default=0, help="0 automatic, 1 unrolled, 2 table-driven rate kernels")
     ap.add_argument("--e2e-chunk", type=int, default=E2E_CHUNK, help="states per chunk of the end-to-end pipeline")
     ap.add_argument("--tr-layout", type=int, default=0, help="transport species vectors: 1 shared, 2 X local, 3 (default) all local")
     ap.add_argument("--rates-arith", type=int, default=0,

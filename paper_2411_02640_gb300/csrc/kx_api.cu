@@ -310,7 +310,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.diff_mode < 0 || h->opt.diff_mode > 2) return fail(KX_ERR_ARG, "diff_mode must be 0, 1 or 2");
   if (h->opt.kc_mode < 0 || h->opt.kc_mode > 1) return fail(KX_ERR_ARG, "kc_mode must be 0 or 1");
   if (h->opt.tr_mode < 0 || h->opt.tr_mode > 1) return fail(KX_ERR_ARG, "tr_mode must be 0 or 1");
-  if (h->opt.rates_mode < 0 || h->opt.rates_mode > 3) return fail(KX_ERR_ARG, "rates_mode must be 0, 1, 2 or 3");
+  if (h->opt.rates_mode < 0 || h->opt.rates_mode > 2) return fail(KX_ERR_ARG, "rates_mode must be 0, 1 or 2");
   if (h->opt.rates_arith < 0 || h->opt.rates_arith > 2) return fail(KX_ERR_ARG, "rates_arith must be 0, 1 or 2");
   if (h->opt.tr_layout < 0 || h->opt.tr_layout > 3) return fail(KX_ERR_ARG, "tr_layout must be 0, 1, 2 or 3");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
