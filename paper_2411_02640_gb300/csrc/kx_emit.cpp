@@ -2610,7 +2610,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
   if (rreg == 0 && unrolled_rates) rreg = opt.mixed ? 96 : 128;
-  if (rreg == 0 && df_rates) rreg = opt.mixed ? 96 : 128;
+  if (rreg == 0 && df_rates) rreg = opt.mixed ? 72 : 128;
   if (rreg == 0 && kind == KernelKind::Transport) rreg = opt.tr_layout == 3 ? 64 : 128;
   if (rreg == 0 && kind == KernelKind::Thermo) rreg = 48;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
