@@ -1424,7 +1424,7 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
   std::string sfx = "0", srx = "0";
   for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
   for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
-  o("  const int sf = " + sfx + ";");
+  o("  const int sf = anyneg ? (" + sfx + ") : 0;");
   c.fp32 += d.rx.size() * (2 + d.nre);
   if (d.rev) {
     const int dn = d.npr - d.nre;
@@ -1434,7 +1434,7 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
     for (int j = 1; j < E; ++j) o(fmt("  dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
     if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
     else if (dn != 0) o(fmt("  dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-    o("  const double q = kx_net_rate_s(lnRf, dl.hi, sf, " + srx + ");");
+    o("  const double q = kx_net_rate_s(lnRf, dl.hi, sf, anyneg ? (" + srx + ") : 0);");
     c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + 10); c.exp32 += d.rx.size() * 2;
   } else {
     o("  const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
@@ -1614,6 +1614,11 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
   }
   o("}");
+  {   // no negative mass fraction in this state (the usual case): the sign parities are all 0
+    std::string any = "nm0";
+    for (int q = 1; q < nw; ++q) any += fmt(" | nm%d", q);
+    o("const bool anyneg = (" + any + ") != 0ull;");
+  }
   c.fp32 += 40 + 45 + kDfDiv + 2 * kDfMul + kDfAdd + kDfDiv + kDfLog;
   c.fp32 += ns * (12 + kDfFma) + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
 
@@ -1800,7 +1805,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       std::string sfx = "0", srx = "0";
       for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
       for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
-      o("  int sf = " + sfx + ";");
+      o("  int sf = anyneg ? (" + sfx + ") : 0;");
       o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
       o("  bool rev = false;");
       c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
@@ -1813,7 +1818,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
         if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
       else if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-        o("    const int sr = " + srx + ";");
+        o("    const int sr = anyneg ? (" + srx + ") : 0;");
         o("    rev = dl.hi > 0.0f;");
         o("    if (rev) L = kx_df_add(lf, dl);");
         o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
