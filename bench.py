@@ -247,7 +247,8 @@ def run_kx(args):
     n = args.points
     path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
     mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg, rates_mode=args.rates_mode,
-                        rates_arith=args.rates_arith, tr_layout=args.tr_layout, block=args.block)
+                        rates_arith=args.rates_arith, tr_layout=args.tr_layout, block=args.block,
+                        diff_mode=args.diff_mode)
     ns = mech.n_species
     T, p, Y = make_inputs(rank, n)
     dev = torch.device("cuda", local)
@@ -589,6 +590,7 @@ def main():
     ap.add_argument("--rates-mode", type=int, default=0, help="0 automatic, 1 unrolled, 2 table-driven rate kernels")
     ap.add_argument("--e2e-chunk", type=int, default=E2E_CHUNK, help="states per chunk of the end-to-end pipeline")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the generated kernels (0: 128)")
+    ap.add_argument("--diff-mode", type=int, default=0, help="transport pairs: 0/1 symmetric (default), 2 full matrices")
     ap.add_argument("--tr-layout", type=int, default=0, help="transport species vectors: 1 shared, 2 X local, 3 (default) all local")
     ap.add_argument("--rates-arith", type=int, default=0,
                     help="float64-accurate rates: 0 double-float (default), 1 native float64")

@@ -64,7 +64,8 @@ typedef enum {
 
 /* Load options; a zero-initialised struct (or NULL) selects the defaults. */
 typedef struct {
-  int diff_mode;      /* 0 default (symmetric), 1 symmetric D_kj pairs, 2 full matrix */
+  int diff_mode;      /* 0 default (symmetric), 1 symmetric pairs (D_kj once per pair; float64-accurate
+                        Wilke phi_kj once per pair, phi_jk from phi_kj), 2 full matrices */
   int kc_mode;        /* 0 default (log space: k_r = exp(ln k_f - ln K_c)),
                          1 per-species exp(-G_k/RT) products, one division per reaction */
   int tr_mode;        /* float64 transport: 0 (default) double-float arithmetic on the float32
@@ -196,11 +197,12 @@ kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash)
 int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
 
 /* Production rates, thermo and/or transport for states held in HOST memory
- * (pinned for asynchronous copies), pipelined in chunks over two streams:
- * the kernels run chunk after chunk on stream_a while stream_b copies the
- * next chunk's inputs in and the previous chunk's outputs out (events order
- * the two), so the host<->device copies overlap the arithmetic and no two
- * chunks' kernels compete for the device.  T, p [n], Y [N_s][ld] are
+ * (pinned for asynchronous copies), pipelined in chunks: the kernels run
+ * chunk after chunk on stream_a while stream_b copies the next chunk's
+ * inputs in and a stream created for the call copies the previous chunk's
+ * outputs out (events order the three; stream_b waits for the last copy out
+ * before the call returns), so both copy directions overlap the arithmetic
+ * and no two chunks' kernels compete for the device.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
  * are host outputs, those not selected by `outputs` may be NULL.
  * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk

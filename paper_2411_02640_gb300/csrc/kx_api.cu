@@ -598,22 +598,57 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   if (max_chunk > 0) c = std::min(c, std::max<int64_t>(256, max_chunk / 256 * 256));
   if (c < 256) return fail(KX_ERR_ARG, "workspace smaller than two chunks of 256 states");
   c = std::min(c, (n + 255) / 256 * 256);
-  // kernels in order on stream_a (one chunk's kernels at a time), every copy on stream_b, the next
-  // chunk's inputs copied in one chunk ahead; per-slot events order the two streams
-  cudaStream_t qa = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b;
-  cudaEvent_t ev[6] = {};
-  struct Events {
+  // kernels in order on stream_a (one chunk's kernels at a time), the inputs copied in on stream_b one
+  // chunk ahead, the outputs copied out on a third stream of this call (so that the two copy
+  // directions run at once); per-slot events order the three, and stream_b waits for everything
+  // the third stream holds before the call returns
+  cudaStream_t qa = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b, qc = nullptr;
+  cudaEvent_t ev[7] = {};
+  struct Guard {   // on every return: stream_b waits for all the copy-out stream holds, then both go
     cudaEvent_t* e;
-    ~Events() { for (int j = 0; j < 6; ++j) if (e[j]) cudaEventDestroy(e[j]); }
-  } guard{ev};
-  for (int j = 0; j < 6; ++j) {
+    cudaStream_t* q;
+    cudaStream_t qb;
+    ~Guard() {
+      if (*q) {
+        if (e[6] && cudaEventRecord(e[6], *q) == cudaSuccess) cudaStreamWaitEvent(qb, e[6], 0);
+        cudaStreamDestroy(*q);   // released once its queued copies finish
+      }
+      for (int j = 0; j < 7; ++j) if (e[j]) cudaEventDestroy(e[j]);
+    }
+  } guard{ev, &qc, qb};
+  for (int j = 0; j < 7; ++j) {
     cudaError_t e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&qc, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { qc = nullptr; return cuda_fail(e, "cudaStreamCreateWithFlags"); }
+    // the copy-out stream starts after whatever the caller queued on stream_b
+    if ((e = cudaEventRecord(ev[6], qb)) == cudaSuccess) e = cudaStreamWaitEvent(qc, ev[6], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "event ordering");
   }
   cudaEvent_t* in_done = ev;          // inputs of the slot copied in
   cudaEvent_t* comp_done = ev + 2;    // kernels of the slot finished
   cudaEvent_t* out_done = ev + 4;     // outputs of the slot copied out
-  const int64_t nchunks = (n + c - 1) / c;
+  // chunk starts: full chunks of c states, except that a long run ramps up (c/4, c/2) and down
+  // (c/2, c/4) so that the first copy in and the last copy out, which nothing overlaps, are short
+  std::vector<int64_t> start{0};
+  {
+    const int64_t q4 = std::max<int64_t>(256, c / 4 / 256 * 256), q2 = std::max<int64_t>(256, c / 2 / 256 * 256);
+    std::vector<int64_t> sz;
+    if (n >= 2 * (q4 + q2) + c) {
+      const int64_t rem = n - 2 * (q4 + q2), k = (rem + c - 1) / c;
+      const int64_t each = ((rem + k - 1) / k + 255) / 256 * 256;
+      sz = {q4, q2};
+      for (int64_t j = 0, left = rem; j < k && left > 0; ++j, left -= each) sz.push_back(std::min(each, left));
+      sz.push_back(q2);
+      sz.push_back(q4);
+    } else {
+      for (int64_t left = n; left > 0; left -= c) sz.push_back(std::min(c, left));
+    }
+    for (int64_t z : sz) start.push_back(start.back() + z);
+  }
+  const int64_t nchunks = (int64_t)start.size() - 1;
   auto slot = [&](int64_t i, double** dT, double** dp, double** dY, double** dw, double** dcp, double** dh, double** dmu,
                   double** dl, double** dD) {
     double* b = (double*)((char*)workspace + (size_t)(i % 2) * (size_t)c * (size_t)per);
@@ -627,8 +662,10 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   auto copy_in = [&](int64_t i) -> kx_status {
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = i * c, m = std::min(c, n - c0);
-    cudaError_t e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, qb);
+    const int64_t c0 = start[i], m = start[i + 1] - c0;
+    // the slot's inputs are free once the kernels of chunk i - 2 finished
+    cudaError_t e = i >= 2 ? cudaStreamWaitEvent(qb, comp_done[i % 2], 0) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, qb);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p + c0, m * 8, cudaMemcpyHostToDevice, qb);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     kx_status s2 = kx_copy_rows_async(dY, c, Y + c0, ld, ns, m, qb);
@@ -638,12 +675,11 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   };
   if ((s = copy_in(0)) != KX_OK) return s;
   for (int64_t i = 0; i < nchunks; ++i) {
-    // the next chunk's inputs (its slot's previous kernels finished: stream_b waited for them
-    // before copying that chunk's outputs out)
+    // the next chunk's inputs, into the other slot
     if (i + 1 < nchunks && (s = copy_in(i + 1)) != KX_OK) return s;
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    const int64_t c0 = start[i], m = start[i + 1] - c0;
     cudaError_t e = cudaStreamWaitEvent(qa, in_done[i % 2], 0);
     if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(qa, out_done[i % 2], 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
@@ -651,21 +687,21 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
     if ((outputs & KX_OUT_THERMO) && (s = kx_thermo(h, dT, dp, dY, c, dcp, dh, m, qa)) != KX_OK) return s;
     if ((outputs & KX_OUT_TRANSPORT) && (s = kx_transport(h, dT, dp, dY, c, dmu, dl, dD, m, precision, qa)) != KX_OK) return s;
     e = cudaEventRecord(comp_done[i % 2], qa);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(qb, comp_done[i % 2], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(qc, comp_done[i % 2], 0);
     if (e != cudaSuccess) return cuda_fail(e, "event ordering");
-    if ((outputs & KX_OUT_WDOT) && (s = kx_copy_rows_async(wdot + c0, ldo, dw, c, ns, m, qb)) != KX_OK) return s;
+    if ((outputs & KX_OUT_WDOT) && (s = kx_copy_rows_async(wdot + c0, ldo, dw, c, ns, m, qc)) != KX_OK) return s;
     if (outputs & KX_OUT_THERMO) {
-      e = cudaMemcpyAsync(cp + c0, dcp, m * 8, cudaMemcpyDeviceToHost, qb);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(hmass + c0, dh, m * 8, cudaMemcpyDeviceToHost, qb);
+      e = cudaMemcpyAsync(cp + c0, dcp, m * 8, cudaMemcpyDeviceToHost, qc);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hmass + c0, dh, m * 8, cudaMemcpyDeviceToHost, qc);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
     if (outputs & KX_OUT_TRANSPORT) {
-      e = cudaMemcpyAsync(mu + c0, dmu, m * 8, cudaMemcpyDeviceToHost, qb);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(lambda + c0, dl, m * 8, cudaMemcpyDeviceToHost, qb);
+      e = cudaMemcpyAsync(mu + c0, dmu, m * 8, cudaMemcpyDeviceToHost, qc);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(lambda + c0, dl, m * 8, cudaMemcpyDeviceToHost, qc);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-      if ((s = kx_copy_rows_async(Dk + c0, ldo, dD, c, ns, m, qb)) != KX_OK) return s;
+      if ((s = kx_copy_rows_async(Dk + c0, ldo, dD, c, ns, m, qc)) != KX_OK) return s;
     }
-    e = cudaEventRecord(out_done[i % 2], qb);
+    e = cudaEventRecord(out_done[i % 2], qc);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   }
   return KX_OK;

@@ -223,8 +223,8 @@ __device__ __forceinline__ kx_df kx_df_fma(kx_df a, kx_df b, kx_df c) {
   const kx_df s = kx_ts(p, c.hi);
   return kx_qts(s.hi, __fadd_rn(s.lo, __fadd_rn(pe, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, c.lo)))));
 }
-// a*b + c without the final renormalisation (inner Horner steps: the next
-// step only needs hi + lo, not |lo| <= ulp(hi)/2)
+// a*b + c without the final renormalisation (inner Horner steps and running
+// sums: the next step only needs hi + lo, not |lo| <= ulp(hi)/2)
 __device__ __forceinline__ kx_df kx_df_fma_u(kx_df a, kx_df b, kx_df c) {
   const float p = __fmul_rn(a.hi, b.hi);
   const float pe = __fmaf_rn(a.hi, b.hi, -p);
@@ -328,6 +328,14 @@ __device__ __forceinline__ kx_df kx_df_add(kx_df a, kx_df b) {
   const kx_df s = kx_ts(a.hi, b.hi);
   return kx_qts(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
+// a + b without the final renormalisation: the high parts summed exactly
+// (two-sum), the low parts and the rounding error added once.  For running
+// sums that are renormalised (kx_ts) or converted (hi + lo) once at the end.
+__device__ __forceinline__ kx_df kx_df_add_u(kx_df a, kx_df b) {
+  const kx_df s = kx_ts(a.hi, b.hi);
+  return kx_mk(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ kx_df kx_df_norm(kx_df a) { return kx_ts(a.hi, a.lo); }
 __device__ __forceinline__ kx_df kx_df_neg(kx_df a) { return kx_mk(-a.hi, -a.lo); }
 __device__ __forceinline__ kx_df kx_df_sub(kx_df a, kx_df b) { return kx_df_add(a, kx_df_neg(b)); }
 // a b with b a float
@@ -420,6 +428,31 @@ __device__ __forceinline__ kx_df kx_df_exp_s(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+// e^x 2^-S of a float pair as a float pair, S an integer with |S| <= 1100 and
+// Sl = S ln2 in float32 (for the range test only): 0 where x - S ln2 <= -87,
+// inf where it is >= 88.7.  The reduction x = k ln2/256 + r takes x itself
+// (|x| < 830 there, so |k| < 2^19 and the 5-bit first part of ln2/256 keeps
+// k E1 exact); S is subtracted from the power of two.
+__device__ __forceinline__ kx_df kx_df_exp_sc(kx_df x, int S, float Sl) {
+  const float xs = __fsub_rn(x.hi, Sl);
+  if (!(xs > -87.0f)) return kx_mk(0.0f, 0.0f);
+  if (!(xs < 88.7f)) return kx_mk(KX_INF_F, 0.0f);
+  const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_E1F, x.hi);
+  const float p = __fmul_rn(kf, KX_E2F);
+  const float pe = __fmaf_rn(kf, KX_E2F, -p);
+  kx_df r = kx_ts(t1, -p);
+  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_E3F))));
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const float sc = __int_as_float(((k >> 8) - S + 127) << 23);
+  return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
+}
 // Element k of a per-thread vector kept in global scratch at stride s.
 template <typename V> struct kx_strided {
   V* p;
@@ -433,20 +466,14 @@ __device__ __forceinline__ kx_df kx_df_nu(kx_df q, int nu) {
   if (nu >= -2 && nu <= 2) return kx_mk(__fmul_rn(q.hi, f), __fmul_rn(q.lo, f));
   return kx_df_mulf(q, f);
 }
-// S ln2 as a float pair (exact product terms for |S| < 2^11)
-__device__ __forceinline__ kx_df kx_df_ln2_mul(int S) {
-  const float sf = __fsub_rn(__int_as_float(0x4b400000 + S), KX_RND_F);
-  const float p2 = __fmul_rn(sf, KX_LN2_2F);
-  const kx_df s = kx_qts(__fmul_rn(sf, KX_LN2_1F), p2);
-  return kx_qts(s.hi, __fadd_rn(s.lo, __fmaf_rn(sf, KX_LN2_3F, __fmaf_rn(sf, KX_LN2_2F, -p2))));
-}
 // (a.hi + a.lo) 2^S as a double: one float64 addition, the power of two
 // added to the exponent field (ldexp only when the result leaves the normal
 // range)
 __device__ __forceinline__ double kx_df2d_s(kx_df a, int S) {
-  if (a.hi == 0.0f) return 0.0;
+  if (a.hi == 0.0f && a.lo == 0.0f) return 0.0;   // (an unnormalised sum may hold its value in lo alone)
   if (!(fabsf(a.hi) < KX_INF_F)) return (double)a.hi;
   const double d = kx_f2d(a.hi) + kx_f2d(a.lo);
+  if (d == 0.0) return 0.0;
   const int hi = __double2hiint(d);
   const int E = ((hi >> 20) & 0x7ff) + S;
   if (E > 0 && E < 0x7ff) return __hiloint2double(hi + (int)((unsigned)S << 20), __double2loint(d));
@@ -1705,7 +1732,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     }
     o("// largest scaled rate near 2^63.5; |S| < 2^11 keeps S ln2 exact to the float-pair precision");
     o("const int S = kx_rint(fminf(fmaxf(U * KX_LOG2E_F, -1000.0f), 1000.0f)) - 63;");
-    o("const kx_df lnS = kx_df_ln2_mul(S);");
+    o("const float lnSf = __fmul_rn(kx_i2f(S), 0.693147182f);   // S ln2 for the range tests of the scaled exponential");
   }
 
   // ---- main pass, one loop per class
@@ -1800,24 +1827,26 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
       }
       // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
-      o(rop ? "  kx_df lf = lk;" : "  kx_df lf = kx_df_sub(lk, lnS);");
-      for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add(lf, kx_mk(v%d.x, v%d.y));", j, j));
+      o("  kx_df lf = lk;");
+      for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
+      if (d.nre > 0) o("  lf = kx_df_norm(lf);");
       std::string sfx = "0", srx = "0";
       for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
       for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
       o("  int sf = anyneg ? (" + sfx + ") : 0;");
       o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
       o("  bool rev = false;");
-      c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + (rop ? 0 : kDfAdd) + d.nre * kDfAdd + kDfExp + kDfMul);
+      c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + d.nre * kDfAdd + kDfExp + kDfMul);
       if (d.rev) {
         const int dn = d.npr - d.nre;
         o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
         std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
         o("    kx_df dl = " + first + ";");
         for (int j = 1; j < E; ++j)
-          o(fmt("    dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
-        if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
-      else if (dn != 0) o(fmt("    dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+          o(fmt("    dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+        if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+        else if (dn != 0) o(fmt("    dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+        o("    dl = kx_df_norm(dl);");
         o("    const int sr = anyneg ? (" + srx + ") : 0;");
         o("    rev = dl.hi > 0.0f;");
         o("    if (rev) L = kx_df_add(lf, dl);");
@@ -1832,10 +1861,10 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       }
       if (rop) {
         o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
-        o("  kx_df q = kx_df_mul(kx_df_exp_s(kx_df_sub(L, kx_df_ln2_mul(Sr))), fac);");
-        c.fp32 += d.rx.size() * (kDfAdd + 10);
+        o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
+        c.fp32 += d.rx.size() * 4;
       } else {
-        o("  kx_df q = kx_df_mul(kx_df_exp_s(L), fac);");
+        o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S");
       }
       o("  if (sf) q = kx_df_neg(q);");
       if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
@@ -1852,7 +1881,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     } else {
       // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
       for (int j = 0; j < E; ++j)
-        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
+        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add_u(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
       o("  qp = q;");
       for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
       c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
@@ -1865,7 +1894,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
               j, j));
     else if (!rop)
       for (int j = 0; j < E; ++j)
-        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add(w[kk], kx_df_nu(qp, cj)); } }",
+        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add_u(w[kk], kx_df_nu(qp, cj)); } }",
               j, j));
     --o.ind;
     o("}");
@@ -2206,6 +2235,10 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     return fmt("%s(%s, %s, %s)", md.kind == TrMode::DF ? "kx_df_fma" : md.kind == TrMode::F32 ? "fmaf" : "fma", a.c_str(), b.c_str(),
                cc.c_str());
   };
+  // a*b + c into a running sum that is renormalised once at the end (float pairs: no final renormalisation)
+  auto ACC = [&](const std::string& a, const std::string& b, const std::string& cc) {
+    return md.kind == TrMode::DF ? fmt("kx_df_fma_u(%s, %s, %s)", a.c_str(), b.c_str(), cc.c_str()) : FMA(a, b, cc);
+  };
   auto MUL = [&](const std::string& a, const std::string& b) {
     return md.kind == TrMode::DF ? fmt("kx_df_mul(%s, %s)", a.c_str(), b.c_str()) : fmt("(%s) * (%s)", a.c_str(), b.c_str());
   };
@@ -2252,7 +2285,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   };
   // ---- module-scope tables
   {
-    std::string pv, pl, wa, dself, w, iw, sqw, w4, iw4;
+    std::string pv, pl, wa, dself, w, iw, sqw, w4, iw4, sqwp, isqwp;
     for (int k = 0; k < ns; ++k) {
       double d[5];
       if (direct) coefs(&m.eta[5 * k], 1.0, 0.0, d);                  // eta_k
@@ -2267,6 +2300,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
       } else {
         for (int n = 0; n < 5; ++n) dself += D(m.dif[5 * ((size_t)k * ns + k) + n]) + ",";
       }
+      sqwp += lit(std::sqrt(m.W[k])) + ",";
+      isqwp += lit(1.0 / std::sqrt(m.W[k])) + ",";
       w4 += lit(std::pow(m.W[k], 0.25)) + ",";
       iw4 += lit(std::pow(m.W[k], -0.25)) + ",";
       w += D(m.W[k]) + ",";
@@ -2297,6 +2332,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     g(fmt("__device__ const double kx_iw[%d] = {%s};", ns, iw.c_str()));
     g(fmt("__device__ const double kx_sqw[%d] = {%s};", ns, sqw.c_str()));
     g(fmt("__device__ const %s kx_w4[%d] = {%s};", T, ns, w4.c_str()));
+    g(fmt("__device__ const %s kx_sqwp[%d] = {%s};", T, ns, sqwp.c_str()));
+    g(fmt("__device__ const %s kx_isqwp[%d] = {%s};", T, ns, isqwp.c_str()));
     g(fmt("__device__ const %s kx_iw4[%d] = {%s};", T, ns, iw4.c_str()));
   }
   o("const double lnT = log(T);");
@@ -2322,6 +2359,10 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("const double iWbar = 1.0 / (sY * isig);");
   c.fp64 += 2 * ns + 1; c.div64 += 2;
   const bool p1 = opt.part != 2, p2 = opt.part != 1;
+  // float64 accuracy, all vectors local: Wilke's phi_kj evaluated once per unordered pair (j > k),
+  // the other direction from phi_jk = phi_kj rho_j/rho_k with rho = eta/W (exact identity), added to
+  // a column accumulator C_j (the z2 slot)
+  const bool wsym = two_arrays && vlocal && opt.diff_mode != 2;
   if (!p1) {
     o(fmt("for (int k = 0; k < %d; ++k) %s", ns, st(XS("k"),
                                                     FROMD("Y_[(long long)k * ld + i] * kx_iw[k] * isig")).c_str()));
@@ -2343,6 +2384,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   }
   if (two_arrays) {
     o("  " + st(VS("sZ1", "k"), "v"));          // z1 = X v and z2 = z1 v are formed in the Wilke loop
+    if (wsym) o("  " + st(VS("sZ2", "k"), ZERO));
   } else {
     o(fmt("  const %s z1 = %s;", md.ty, MUL("X", "v").c_str()));
     o("  " + st(VS("sZ1", "k"), "z1"));
@@ -2362,6 +2404,54 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   c.fp64 += 2 * ns;
   // Wilke rows
   o("double mu = 0.0;");
+  if (wsym) {
+    // den_k = sum_j X_j phi_kj = X_k + sum_{j>k} X_j phi_kj + rho_k sum_{j<k} (X_j/rho_j) phi_jk, with
+    // phi_kk = 1, phi_kj = a_kj (1 + u_k v_j)^2, rho_k = eta_k/W_k = u_k^2/sqrt(W_k).  Row k adds its
+    // pairs to its own sum and X_k/rho_k phi_kj to C_j; C_k is complete when row k starts.
+    const std::string ONE1 = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : "1.0";
+    o("#pragma unroll 1");
+    o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+    o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
+    if (direct) {
+      o(fmt("  const %s eta = %s;", md.ty, horner("pv").c_str()));
+      o(fmt("  const %s u = %s;", md.ty, MUL(MUL("eta", RSQRT("eta")), ld("kx_iw4[k]")).c_str()));
+    } else {
+      o(fmt("  const %s u = %s;", md.ty, EXP(NEG(horner("pv"))).c_str()));
+    }
+    o(fmt("  const %s Xk = %s, vk = %s;", md.ty, ld(XS("k")).c_str(), ld(VS("sZ1", "k")).c_str()));
+    o(fmt("  const %s xr = %s;   // X_k / rho_k = X_k v_k^2 sqrt(W_k)", md.ty,
+          MUL(MUL("Xk", MUL("vk", "vk")), ld("kx_sqwp[k]")).c_str()));
+    o(fmt("  %s r0 = %s, r1 = %s;", md.ty, ZERO.c_str(), ZERO.c_str()));
+    o(fmt("  const %s* a = kx_wa + %d * k;", md.st, ns));
+    o("  int j = k + 1;");
+    o("  #pragma unroll 2");
+    o(fmt("  for (; j + 1 < %d; j += 2) {", ns));
+    o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
+    o(fmt("    const %s xa = %s, va = %s, xb = %s, vb = %s;", md.ty, ld(XS("j")).c_str(), ld(VS("sZ1", "j")).c_str(),
+          ld(XS("(j + 1)")).c_str(), ld(VS("sZ1", "(j + 1)")).c_str()));
+    o(fmt("    const %s wa = %s, wb = %s;", md.ty, FMA("u", "va", ONE1).c_str(), FMA("u", "vb", ONE1).c_str()));
+    o(fmt("    const %s pa = %s, pb = %s;", md.ty, MUL("A", MUL("wa", "wa")).c_str(), MUL("Ab", MUL("wb", "wb")).c_str()));
+    o(fmt("    r0 = %s; r1 = %s;", ACC("xa", "pa", "r0").c_str(), ACC("xb", "pb", "r1").c_str()));
+    o(fmt("    const %s ca = %s, cb = %s;", md.ty, ACC("xr", "pa", ld(VS("sZ2", "j"))).c_str(),
+          ACC("xr", "pb", ld(VS("sZ2", "(j + 1)"))).c_str()));
+    o("    " + st(VS("sZ2", "j"), "ca"));
+    o("    " + st(VS("sZ2", "(j + 1)"), "cb"));
+    o("  }");
+    o(fmt("  if (j < %d) {", ns));
+    o(fmt("    const %s A = %s, xa = %s, va = %s;", md.ty, ld("a[j]").c_str(), ld(XS("j")).c_str(), ld(VS("sZ1", "j")).c_str()));
+    o(fmt("    const %s wa = %s;", md.ty, FMA("u", "va", ONE1).c_str()));
+    o(fmt("    const %s pa = %s;", md.ty, MUL("A", MUL("wa", "wa")).c_str()));
+    o(fmt("    r0 = %s;", ACC("xa", "pa", "r0").c_str()));
+    o(fmt("    const %s ca = %s;", md.ty, ACC("xr", "pa", ld(VS("sZ2", "j"))).c_str()));
+    o("    " + st(VS("sZ2", "j"), "ca"));
+    o("  }");
+    o(fmt("  const %s rho = %s;", md.ty, MUL(MUL("u", "u"), ld("kx_isqwp[k]")).c_str()));
+    o(fmt("  const %s den = %s;", md.ty, FMA("rho", ld(VS("sZ2", "k")), FMA("r1", ONE1, FMA("r0", ONE1, "Xk"))).c_str()));
+    o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD("Xk").c_str(), TOD(MUL("u", "u")).c_str(), TOD("den").c_str()));
+    o("}");
+    count_fma(ns * (ns - 1) / 2.0 * 5 + ns * 10); count_exp(ns);
+    c.fp64 += 4 * ns; c.div64 += ns;
+  } else {
   o("#pragma unroll 1");
   o(fmt("for (int k = 0; k < %d; ++k) {", ns));
   o(fmt("  const %s* pv = kx_pv + 5 * k;", md.st));
@@ -2428,6 +2518,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   o("}");
   count_fma(ns * (3.0 * ns + 8)); count_exp(ns);
   c.fp64 += 4 * ns; c.div64 += ns;
+  }
   o("out0_[i] = mu;");
   o(fmt("out1_[i] = 0.5 * (%s + 1.0 / %s);", TOD("sl").c_str(), TOD("sil").c_str()));
   c.fp64 += 4; c.div64 += 1;
@@ -2491,18 +2582,18 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("    cq += 6; n0 = cq[0]; n1 = cq[1]; n2 = cq[2];");
     o("    " + pexp("ea", "a0", "a1", "a2"));
     o("    " + pexp("eb", "b0", "b1", "b2"));
-    o("    Sk = " + FMA(ld(XS("j")), "ea", "Sk") + ";");
-    o("    Sk1 = " + FMA(ld(XS("(j + 1)")), "eb", "Sk1") + ";");
-    o(fmt("    const %s Sa = %s;", md.ty, FMA("Xk", "ea", ld(VS("sS", "j"))).c_str()));
-    o(fmt("    const %s Sb = %s;", md.ty, FMA("Xk", "eb", ld(VS("sS", "(j + 1)"))).c_str()));
+    o("    Sk = " + ACC(ld(XS("j")), "ea", "Sk") + ";");
+    o("    Sk1 = " + ACC(ld(XS("(j + 1)")), "eb", "Sk1") + ";");
+    o(fmt("    const %s Sa = %s;", md.ty, ACC("Xk", "ea", ld(VS("sS", "j"))).c_str()));
+    o(fmt("    const %s Sb = %s;", md.ty, ACC("Xk", "eb", ld(VS("sS", "(j + 1)"))).c_str()));
     o("    " + st(VS("sS", "j"), "Sa"));
     o("    " + st(VS("sS", "(j + 1)"), "Sb"));
     o("  }");
     o(fmt("  if (j < %d) {", ns));
     o("    " + take);
     o("    " + pexp("e", "c0", "c1", "c2"));
-    o("    Sk = " + FMA(ld(XS("j")), "e", "Sk") + ";");
-    o(fmt("    const %s Sj = %s;", md.ty, FMA("Xk", "e", ld(VS("sS", "j"))).c_str()));
+    o("    Sk = " + ACC(ld(XS("j")), "e", "Sk") + ";");
+    o(fmt("    const %s Sj = %s;", md.ty, ACC("Xk", "e", ld(VS("sS", "j"))).c_str()));
     o("    " + st(VS("sS", "j"), "Sj"));
     o("  }");
     const std::string ONE2 = md.kind == TrMode::DF ? "kx_mk(1.f, 0.f)" : md.kind == TrMode::F32 ? "1.0f" : "1.0";
