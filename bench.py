@@ -332,6 +332,19 @@ def run_kx(args):
     if world > 1:
         e2e_total = max_over_ranks(e2e_total, dist, dev)
     e2e_ms = e2e_total / args.steps
+    # the link's plain copy rates, for reading the end-to-end number: one large copy each way
+    # between the same pinned outputs / inputs and device memory
+    big_h, big_d = hout["wdot"], torch.empty(hout["wdot"].shape, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        big_d.copy_(big_h, non_blocking=True)
+        big_h.copy_(big_d, non_blocking=True)
+    e0.record(stream); big_d.copy_(big_h, non_blocking=True); e1.record(stream)
+    e1.synchronize()
+    h2d_gbs = big_h.numel() * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    e0.record(stream); big_h.copy_(big_d, non_blocking=True); e1.record(stream)
+    e1.synchronize()
+    d2h_gbs = big_h.numel() * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del big_d
 
     if rank == 0:
         pk = peaks()
@@ -399,7 +412,9 @@ def run_kx(args):
                                                         "summed over the step"})(step_bound(names, per)),
             "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "api": "kx_evaluate_host",
                     "chunk": chunk,
-                    "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n},
+                    "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n,
+                    "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs,
+                                 "note": "one pinned copy of the production-rate array each way"}},
             "gpu_launches": NK * args.steps,
             "clocks": clocks,
         }

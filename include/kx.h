@@ -197,12 +197,16 @@ kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash)
 int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
 
 /* Production rates, thermo and/or transport for states held in HOST memory
- * (pinned for asynchronous copies), pipelined in chunks: the kernels run
- * chunk after chunk on stream_a while stream_b copies the next chunk's
- * inputs in and a stream created for the call copies the previous chunk's
- * outputs out (events order the three; stream_b waits for the last copy out
- * before the call returns), so both copy directions overlap the arithmetic
- * and no two chunks' kernels compete for the device.  T, p [n], Y [N_s][ld] are
+ * (pinned for asynchronous copies), pipelined in chunks: the kernels of
+ * even chunks run on stream_a and those of odd chunks on a stream created
+ * for the call (one chunk's last blocks overlap the next chunk's first),
+ * while stream_b copies the next chunk's inputs in and another stream of
+ * the call copies finished chunks' outputs out, so both copy directions
+ * overlap the arithmetic.  Events order the streams; before the call
+ * returns, stream_a and stream_b are made to wait for everything queued on
+ * the call's own streams.  Chunks hold a whole number of waves of the
+ * launched kernels (states that fill every SM's resident blocks once) where
+ * the chunk bound allows one.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
  * are host outputs, those not selected by `outputs` may be NULL.
  * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk

@@ -597,58 +597,65 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   int64_t c = (int64_t)(workspace_bytes / (2 * (size_t)per)) / 256 * 256;
   if (max_chunk > 0) c = std::min(c, std::max<int64_t>(256, max_chunk / 256 * 256));
   if (c < 256) return fail(KX_ERR_ARG, "workspace smaller than two chunks of 256 states");
-  c = std::min(c, (n + 255) / 256 * 256);
-  // kernels in order on stream_a (one chunk's kernels at a time), the inputs copied in on stream_b one
-  // chunk ahead, the outputs copied out on a third stream of this call (so that the two copy
-  // directions run at once); per-slot events order the three, and stream_b waits for everything
-  // the third stream holds before the call returns
-  cudaStream_t qa = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b, qc = nullptr;
-  cudaEvent_t ev[7] = {};
-  struct Guard {   // on every return: stream_b waits for all the copy-out stream holds, then both go
-    cudaEvent_t* e;
-    cudaStream_t* q;
-    cudaStream_t qb;
-    ~Guard() {
-      if (*q) {
-        if (e[6] && cudaEventRecord(e[6], *q) == cudaSuccess) cudaStreamWaitEvent(qb, e[6], 0);
-        cudaStreamDestroy(*q);   // released once its queued copies finish
-      }
-      for (int j = 0; j < 7; ++j) if (e[j]) cudaEventDestroy(e[j]);
+  // ... and, where it holds one, a whole number of waves of the launched kernels (states that fill
+  // every SM's resident blocks once): a partial last wave in every chunk would idle SMs per chunk
+  {
+    const bool fp = precision == KX_FP64;
+    std::vector<const char*> used;
+    if (outputs & KX_OUT_WDOT) used.push_back(fp ? "wdot_fp64" : "wdot_mixed");
+    if (outputs & KX_OUT_THERMO) used.push_back("thermo");
+    if (outputs & KX_OUT_TRANSPORT) { used.push_back(fp ? "visc_fp64" : "visc_mixed"); used.push_back(fp ? "diff_fp64" : "diff_mixed"); }
+    int64_t wave = 0;
+    for (const char* name : used) {
+      Kernel* k = find_kernel(h, name);
+      if (!k) return fail(KX_ERR_UNSUPPORTED, std::string("no kernel ") + name);
+      if ((s = ensure_ready(h, *k)) != KX_OK) return s;
+      wave = std::max<int64_t>(wave, (int64_t)k->max_blocks * k->eopt.block);
     }
-  } guard{ev, &qc, qb};
-  for (int j = 0; j < 7; ++j) {
+    if (wave > 0 && c >= wave) c = c / wave * wave;
+  }
+  c = std::min(c, (n + 255) / 256 * 256);
+  // the kernels of even chunks on stream_a and of odd chunks on a second compute stream of this call
+  // (so that one chunk's last blocks overlap the next chunk's first: no SM idles at a kernel's
+  // tail), the inputs copied in on stream_b one chunk ahead, the outputs copied out on a copy-out
+  // stream of this call (so that the two copy directions run at once); per-slot events order them,
+  // and on return stream_a and stream_b wait for everything the call's own streams hold
+  cudaStream_t qa0 = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b, qc = nullptr, qd = nullptr;
+  cudaEvent_t ev[8] = {};
+  struct Guard {
+    cudaEvent_t* e;
+    cudaStream_t *qc, *qd;
+    cudaStream_t qa, qb;
+    ~Guard() {
+      if (*qc) {
+        if (e[6] && cudaEventRecord(e[6], *qc) == cudaSuccess) cudaStreamWaitEvent(qb, e[6], 0);
+        cudaStreamDestroy(*qc);   // released once its queued work finishes
+      }
+      if (*qd) {
+        if (e[7] && cudaEventRecord(e[7], *qd) == cudaSuccess) cudaStreamWaitEvent(qa, e[7], 0);
+        cudaStreamDestroy(*qd);
+      }
+      for (int j = 0; j < 8; ++j) if (e[j]) cudaEventDestroy(e[j]);
+    }
+  } guard{ev, &qc, &qd, qa0, qb};
+  for (int j = 0; j < 8; ++j) {
     cudaError_t e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
   }
   {
     cudaError_t e = cudaStreamCreateWithFlags(&qc, cudaStreamNonBlocking);
     if (e != cudaSuccess) { qc = nullptr; return cuda_fail(e, "cudaStreamCreateWithFlags"); }
-    // the copy-out stream starts after whatever the caller queued on stream_b
+    e = cudaStreamCreateWithFlags(&qd, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { qd = nullptr; return cuda_fail(e, "cudaStreamCreateWithFlags"); }
+    // the call's streams start after whatever the caller queued on stream_a and stream_b
     if ((e = cudaEventRecord(ev[6], qb)) == cudaSuccess) e = cudaStreamWaitEvent(qc, ev[6], 0);
+    if (e == cudaSuccess && (e = cudaEventRecord(ev[7], qa0)) == cudaSuccess) e = cudaStreamWaitEvent(qd, ev[7], 0);
     if (e != cudaSuccess) return cuda_fail(e, "event ordering");
   }
   cudaEvent_t* in_done = ev;          // inputs of the slot copied in
   cudaEvent_t* comp_done = ev + 2;    // kernels of the slot finished
   cudaEvent_t* out_done = ev + 4;     // outputs of the slot copied out
-  // chunk starts: full chunks of c states, except that a long run ramps up (c/4, c/2) and down
-  // (c/2, c/4) so that the first copy in and the last copy out, which nothing overlaps, are short
-  std::vector<int64_t> start{0};
-  {
-    const int64_t q4 = std::max<int64_t>(256, c / 4 / 256 * 256), q2 = std::max<int64_t>(256, c / 2 / 256 * 256);
-    std::vector<int64_t> sz;
-    if (n >= 2 * (q4 + q2) + c) {
-      const int64_t rem = n - 2 * (q4 + q2), k = (rem + c - 1) / c;
-      const int64_t each = ((rem + k - 1) / k + 255) / 256 * 256;
-      sz = {q4, q2};
-      for (int64_t j = 0, left = rem; j < k && left > 0; ++j, left -= each) sz.push_back(std::min(each, left));
-      sz.push_back(q2);
-      sz.push_back(q4);
-    } else {
-      for (int64_t left = n; left > 0; left -= c) sz.push_back(std::min(c, left));
-    }
-    for (int64_t z : sz) start.push_back(start.back() + z);
-  }
-  const int64_t nchunks = (int64_t)start.size() - 1;
+  const int64_t nchunks = (n + c - 1) / c;
   auto slot = [&](int64_t i, double** dT, double** dp, double** dY, double** dw, double** dcp, double** dh, double** dmu,
                   double** dl, double** dD) {
     double* b = (double*)((char*)workspace + (size_t)(i % 2) * (size_t)c * (size_t)per);
@@ -662,7 +669,7 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   auto copy_in = [&](int64_t i) -> kx_status {
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = start[i], m = start[i + 1] - c0;
+    const int64_t c0 = i * c, m = std::min(c, n - c0);
     // the slot's inputs are free once the kernels of chunk i - 2 finished
     cudaError_t e = i >= 2 ? cudaStreamWaitEvent(qb, comp_done[i % 2], 0) : cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, qb);
@@ -679,7 +686,8 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
     if (i + 1 < nchunks && (s = copy_in(i + 1)) != KX_OK) return s;
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = start[i], m = start[i + 1] - c0;
+    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    cudaStream_t qa = i % 2 ? qd : qa0;
     cudaError_t e = cudaStreamWaitEvent(qa, in_done[i % 2], 0);
     if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(qa, out_done[i % 2], 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");

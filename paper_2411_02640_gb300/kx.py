@@ -178,7 +178,7 @@ class Mechanism:
     def evaluate_host(self, T, p, Y, out: dict, outputs: int = 7, precision="fp64", workspace=None,
                       max_chunk: int = 0, streams=None):
         """kx_evaluate_host: host (pinned) states in, host outputs out, the
-        copies overlapped with the kernels in chunks over two streams.  ``out``
+        copies overlapped with the kernels in chunks.  ``out``
         holds host tensors under the keys wdot, cp, h, mu, lam, Dk (those of
         the selected outputs); ``workspace`` a device uint8 tensor; ``streams``
         two torch streams.  Returns after enqueueing; synchronise both streams."""
