@@ -2700,14 +2700,18 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   // latency better than the spills they cost); the float-pair rate kernel at
   // 128 (four blocks: its pipelined loops keep two reactions' operands live);
   // the transport kernels with their vectors in local memory at 64 (eight
-  // blocks of 128: residency is what hides the local-memory latency), with
-  // shared-memory columns at 128; thermo at 48.
+  // blocks of 128: residency is what hides the local-memory latency), except
+  // the float-pair viscosity kernel with Wilke's pairs evaluated once per
+  // unordered pair at 80 (six blocks: its row and column sums hold more live
+  // values; 4.49 against 5.10 ms at 64 on 2^20 states); with shared-memory
+  // columns at 128; thermo at 48.
   int rreg = opt.maxrreg;
   const bool unrolled_rates = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !df_rates &&
                               !(opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400)));
   if (rreg == 0 && unrolled_rates) rreg = opt.mixed ? 96 : 128;
   if (rreg == 0 && df_rates) rreg = opt.mixed ? 72 : 128;
-  if (rreg == 0 && kind == KernelKind::Transport) rreg = opt.tr_layout == 3 ? 64 : 128;
+  if (rreg == 0 && kind == KernelKind::Transport)
+    rreg = opt.tr_layout != 3 ? 128 : (!opt.mixed && opt.tr_mode == 0 && opt.part == 1 && opt.diff_mode != 2) ? 80 : 64;
   if (rreg == 0 && kind == KernelKind::Thermo) rreg = 48;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
