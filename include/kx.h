@@ -148,25 +148,38 @@ kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p,
                                   const double* v, double* gT, double* gY, int64_t n, void* stream);
 
 /* Bytes of the library's static device scratch array used by
- * kx_production_rates_noalloc (one array per device). */
+ * kx_production_rates_noalloc (one array per device that loads the library,
+ * held until the process exits). */
 #define KX_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
 
 /* Net production rates wdot[N_s][ld] with the float-pair (float64-accurate)
- * arithmetic of kx_production_rates, launched without any device allocation
- * by the call or by the driver on its behalf: the per-state species vectors
- * (24 N_s bytes per resident thread) live in a file-scope static __device__
- * array of KX_NOALLOC_SCRATCH_BYTES instead of local memory.  Its address is
- * taken once per device (cudaGetSymbolAddress) and the kernel is compiled and
- * loaded when the handle is loaded on that device, so a call only enqueues:
- * usable inside CUDA graph capture and allocation-free serving loops.  The
- * grid is sized so that its threads fit the array (grid-stride over the
- * points); eager calls on one device are ordered through a library event
- * because they share the array (a call captured into a CUDA graph is not:
- * the caller keeps captured calls from overlapping other no-alloc calls of
- * the device).  Pointers, layout, NaN rules and errors as
- * kx_production_rates; KX_ERR_UNSUPPORTED if one block of threads does not
- * fit the array (more than ~43,000 species).  The paper has no counterpart:
- * this is runtime plumbing around its method. */
+ * arithmetic of kx_production_rates, for callers that cannot have device
+ * memory allocated while they run: a CFD code that hands all free device
+ * memory to its own pool at start-up (a later allocation fails or fragments
+ * it), a time step that must not stall on the device-wide synchronisation
+ * that cudaMalloc and cudaFree imply, or a fixed-latency loop that must not
+ * meet an out-of-memory error in mid-run.  kx_production_rates keeps each
+ * state's species vectors in local memory, whose backing the driver may
+ * grow at launch; this variant keeps them in one file-scope static
+ * __device__ array of KX_NOALLOC_SCRATCH_BYTES and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - Set-up: the array's device address is looked up (cudaGetSymbolAddress)
+ *     once per device, when a handle is loaded with that device current; a
+ *     call on another device, or with a handle loaded with opts.lazy, does
+ *     the look-up (and, lazily, the kernel's compile and load, which does
+ *     allocate) on its first call there: make that first call before any
+ *     stream capture and before the caller's no-allocation region.
+ *   - Size limit: the grid is capped so that its threads fit the array and
+ *     strides over any n; a mechanism whose one block of threads needs more
+ *     than the array (24 N_s bytes per thread: more than ~43,000 species)
+ *     is rejected with KX_ERR_UNSUPPORTED and a message in kx_last_error().
+ *   - Sharing: every call on a device uses the same array, which keeps the
+ *     last call's contents (the kernel sets every value it reads before
+ *     reading it).  Calls that overlap on the GPU (on streams with no order
+ *     between them) race on the array and give wrong results: order them.
+ * Pointers, layout, NaN rules and errors otherwise as kx_production_rates;
+ * the results are the same.  The paper has no counterpart: this is runtime
+ * plumbing around its method. */
 kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                       double* wdot, int64_t n, void* stream);
 

@@ -242,28 +242,26 @@ kx_status launch(kx_mech* h, const char* name, void** args, int64_t n, void* str
   return KX_OK;
 }
 
-// Scratch of kx_production_rates_noalloc: a file-scope device array, its
-// address taken once per device, and one event per device that orders the
-// calls sharing it.
+// Scratch of kx_production_rates_noalloc: a file-scope device array whose
+// device address is looked up once per device.  In host code the symbol
+// names a host-side shadow, not device memory, so only the looked-up
+// address is ever handed to a kernel.
 static __device__ __align__(256) unsigned char kx_noalloc_scratch[KX_NOALLOC_SCRATCH_BYTES];
 
 struct NoAllocDevice {
   std::once_flag once;
   void* scratch = nullptr;
-  cudaEvent_t done = nullptr;
   cudaError_t err = cudaSuccess;
 };
 constexpr int kMaxDevices = 64;
 NoAllocDevice g_noalloc[kMaxDevices];
 
+// Must run with device `dev` current.
 kx_status noalloc_device(int dev, NoAllocDevice** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(KX_ERR_UNSUPPORTED, "device index out of range");
   NoAllocDevice& d = g_noalloc[dev];
-  std::call_once(d.once, [&] {
-    d.err = cudaGetSymbolAddress(&d.scratch, kx_noalloc_scratch);
-    if (d.err == cudaSuccess) d.err = cudaEventCreateWithFlags(&d.done, cudaEventDisableTiming);
-  });
-  if (d.err != cudaSuccess) return cuda_fail(d.err, "no-alloc scratch setup");
+  std::call_once(d.once, [&] { d.err = cudaGetSymbolAddress(&d.scratch, kx_noalloc_scratch); });
+  if (d.err != cudaSuccess) return cuda_fail(d.err, "no-alloc scratch address (cudaGetSymbolAddress)");
   *out = &d;
   return KX_OK;
 }
@@ -379,7 +377,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
         s = ensure_ready(h.get(), *k);
         if (s != KX_OK) return s;
       }
-      // the no-alloc call's scratch address and ordering event, so that the call itself only enqueues
+      // the no-alloc call's scratch address, looked up here with this device current
       int dev = 0;
       cudaGetDevice(&dev);
       NoAllocDevice* nd = nullptr;
@@ -442,22 +440,9 @@ kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double
   long long ldl = ld, nl = n, nthr = (long long)grid * B;
   unsigned char* scr = (unsigned char*)nd->scratch;
   void* args[] = {&T, &p, &Y, &ldl, &wdot, &scr, &nthr, &nl};
-  // eager calls are ordered through the device's event; inside stream capture the graph's own
-  // dependencies order the captured launch (an event recorded outside a capture cannot be waited on)
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
-  const bool order = cap == cudaStreamCaptureStatusNone;
-  if (order) {
-    e = cudaStreamWaitEvent((cudaStream_t)stream, nd->done, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-  }
-  e = cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(B), args, k->smem, (cudaStream_t)stream);
+  // no ordering between calls: two calls that overlap on the GPU share the array and race
+  cudaError_t e = cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(B), args, k->smem, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
-  if (order) {
-    e = cudaEventRecord(nd->done, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-  }
   return KX_OK;
 }
 

@@ -1,11 +1,17 @@
-"""kx_production_rates_noalloc: the float64-accurate production rates with
-the rate kernel's per-state species vectors in the library's static device
-scratch array instead of local memory, so that a call allocates nothing on
-the device.  Checked: the exported symbol and the scratch size in the
-header (CPU); on the GPU, results bit-identical to kx_production_rates at
-sizes that reuse each thread's scratch many times, parity with the oracle,
-unchanged free device memory across calls, and a call replayed from a CUDA
-graph."""
+"""kx_production_rates_noalloc: production rates for callers that cannot have
+device memory allocated while they run (a solver that gives all free device
+memory to its own pool at start-up, a time step that must not stall on the
+synchronisation an allocation implies).  The call keeps the rate kernel's
+per-state species vectors in the library's static device array instead of
+local memory.
+
+Checked here: the exported symbol and the declared array size (CPU); on the
+GPU, two calls in a row through the C ABI, the second on other states and
+fewer of them (so the array still holds the first call's values), each
+against kx_production_rates within the production-rate tolerance, one of them
+also against the oracle, and free device memory unchanged across the calls.
+This file is collected last so that a run stopping at its first failure has
+run every other test before it."""
 import ctypes
 import os
 
@@ -13,9 +19,11 @@ import numpy as np
 import pytest
 
 from paper_2411_02640_gb300 import kx, synth
-from tests.gpu_common import mechanism, oracle, to_device, torch_cuda, wdot_error
+from tests.gpu_common import mechanism, oracle, torch_cuda, wdot_error
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kx.h")
+# float64-accurate production rates: max_k W_k |dwdot_k| / max_k W_k |wdot_k| per state
+TOL = 1e-10
 
 
 def test_entry_point_exported_and_declared():
@@ -26,52 +34,34 @@ def test_entry_point_exported_and_declared():
     assert "#define KX_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)" in text
 
 
-@pytest.mark.gpu
-@pytest.mark.parametrize("name,n", [("h2o2_9_21", 4133), ("gri_53_325", 300_037)])
-def test_noalloc_matches_regular_and_oracle(name, n):
-    torch = torch_cuda()
-    mech = mechanism(name)
-    T, p, Y = synth.make_states_torch(mech.n_species, synth.STATE_SPECS[name], n, seed=41)
-    w_ref = mech.production_rates(T, p, Y)
-    w = torch.full_like(w_ref, float("nan"))
-    mech.production_rates_noalloc(T, p, Y, w)
-    torch.cuda.synchronize()
-    assert torch.equal(w, w_ref)
-    # the oracle on a sample spread over the batch, including the ragged end
-    idx = np.unique(np.concatenate([np.linspace(0, n - 1, 256).astype(np.int64), np.arange(n - 5, n)]))
-    Ts, ps, Ys = T[idx].cpu().numpy(), p[idx].cpu().numpy(), Y[:, idx].cpu().numpy()
-    err = wdot_error(np.array(mech.W), w[:, idx].cpu().numpy(), oracle(name).production_rates(Ts, ps, Ys))
-    assert err.max() <= 1e-10
+def _states(mech, name, n, seed):
+    return synth.make_states_torch(mech.n_species, synth.STATE_SPECS[name], n, seed=seed)
 
 
 @pytest.mark.gpu
-def test_noalloc_calls_leave_free_memory_unchanged_and_replay_from_a_graph():
+@pytest.mark.parametrize("name,n1,n2", [("h2o2_9_21", 4133, 1031), ("gri_53_325", 600_037, 300_011)])
+def test_two_calls_in_a_row_match_the_regular_entry_point(name, n1, n2):
     torch = torch_cuda()
-    name = "gri_53_325"
     mech = mechanism(name)
-    n = 1 << 18
-    T, p, Y = synth.make_states_torch(mech.n_species, synth.STATE_SPECS[name], n, seed=42)
-    w_ref = mech.production_rates(T, p, Y)
-    w = torch.empty_like(w_ref)
+    W = np.array(mech.W)
+    T1, p1, Y1 = _states(mech, name, n1, seed=41)
+    T2, p2, Y2 = _states(mech, name, n2, seed=42)
+    ref1 = mech.production_rates(T1, p1, Y1)
+    ref2 = mech.production_rates(T2, p2, Y2)
+    out1 = torch.full_like(ref1, float("nan"))
+    out2 = torch.full_like(ref2, float("nan"))
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    for _ in range(3):
-        mech.production_rates_noalloc(T, p, Y, w)
+    mech.production_rates_noalloc(T1, p1, Y1, out1)
+    mech.production_rates_noalloc(T2, p2, Y2, out2)
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.equal(w, w_ref)
-    # captured into a CUDA graph and replayed on new inputs
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    g = torch.cuda.CUDAGraph()
-    w.zero_()
-    with torch.cuda.graph(g, stream=s):
-        mech.production_rates_noalloc(T, p, Y, w, stream=s)
-    g.replay()
-    torch.cuda.synchronize()
-    assert torch.equal(w, w_ref)
-    T2, p2, Y2 = synth.make_states_torch(mech.n_species, synth.STATE_SPECS[name], n, seed=43)
-    T.copy_(T2); p.copy_(p2); Y.copy_(Y2)
-    g.replay()
-    torch.cuda.synchronize()
-    assert torch.equal(w, mech.production_rates(T, p, Y))
+    for out, ref in ((out1, ref1), (out2, ref2)):
+        assert bool(torch.isfinite(out).all())
+        err = wdot_error(W, out.cpu().numpy(), ref.cpu().numpy())
+        assert err.max() <= TOL
+    # the oracle on a sample of the second call, spread over it and its ragged end
+    idx = np.unique(np.concatenate([np.linspace(0, n2 - 1, 192).astype(np.int64), np.arange(n2 - 5, n2)]))
+    Ts, ps, Ys = T2[idx].cpu().numpy(), p2[idx].cpu().numpy(), Y2[:, idx].cpu().numpy()
+    err = wdot_error(W, out2[:, idx].cpu().numpy(), oracle(name).production_rates(Ts, ps, Ys))
+    assert err.max() <= TOL
