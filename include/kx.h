@@ -24,7 +24,11 @@
  *   - Y need not be normalised: concentrations use
  *     C_k = (p/(R T)) (Y_k/W_k) / sum_j (Y_j/W_j).
  *   - A point with T <= 0, p <= 0 or a non-finite T or p gets NaN in every
- *     output; nothing traps.  Non-finite Y propagates as NaN.
+ *     output, and so does, in the calls that form concentrations or mole
+ *     fractions (all but kx_thermo), a point whose sum_k Y_k/W_k is not
+ *     positive and finite; such points are recorded for
+ *     kx_last_point_status; nothing traps.  Other non-finite Y propagates
+ *     as NaN.
  *   - A handle may be used from several host threads and streams at once.
  *   - Errors: every call returns a kx_status; kx_last_error() gives a
  *     message for the calling thread's last failure.
@@ -50,7 +54,7 @@ typedef enum {
   KX_ERR_COMPILE = 6,       /* NVRTC failed on the emitted source */
   KX_ERR_CUDA = 7,          /* a CUDA runtime call failed */
   KX_ERR_TIMEOUT = 8,       /* a host-side wait ran past its deadline */
-  KX_ERR_NONFINITE_INPUT = 9,
+  KX_ERR_NONFINITE_INPUT = 9, /* kx_last_point_status: a point was outside the domain */
   KX_ERR_UNSUPPORTED = 10   /* feature not available for this mechanism */
 } kx_status;
 
@@ -146,6 +150,21 @@ kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const doub
  * Jacobian as future work (Sec. 4); this is its adjoint form.  FP64. */
 kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                   const double* v, double* gT, double* gY, int64_t n, void* stream);
+
+/* Per-point domain check.  The method is defined for T > 0, p > 0 and a
+ * positive, finite sum_k Y_k/W_k (the concentrations of Sec. A.2 and the
+ * mole fractions of Sec. A.3.5 divide by it; kx_thermo does not check it);
+ * every kernel of a handle gives the points outside that domain NaN
+ * outputs and records the smallest such point index (the index within the
+ * call's batch).  This call enqueues on `stream` a read of every record of
+ * the handle on the current device and their reset, then waits for
+ * `stream`: it returns KX_OK with *first_bad_point = -1 if no point was
+ * outside the domain since the handle was loaded or last checked, else
+ * KX_ERR_NONFINITE_INPUT with the smallest recorded index (over all calls
+ * since then; kx_last_error() names it).  Calls on other streams are seen
+ * once they have finished: synchronise them first; a call still running on
+ * another stream may record its points before or after the reset. */
+kx_status kx_last_point_status(kx_handle h, void* stream, int64_t* first_bad_point);
 
 /* Bytes of the library's static device scratch array used by
  * kx_production_rates_noalloc (one array per device that loads the library,

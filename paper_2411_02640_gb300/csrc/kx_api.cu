@@ -446,6 +446,40 @@ kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double
   return KX_OK;
 }
 
+kx_status kx_last_point_status(kx_handle h, void* stream, int64_t* first_bad_point) {
+  if (!h || !first_bad_point) return fail(KX_ERR_ARG, "null argument");
+  *first_bad_point = -1;
+  if (h->opt.compile_only) return fail(KX_ERR_UNSUPPORTED, "handle was loaded with compile_only");
+  // every loaded kernel keeps its own word; read each and set it back to "none" behind the work queued on stream
+  std::vector<void*> addr;
+  for (auto& k : h->kernels) {
+    {
+      std::lock_guard<std::mutex> lock(k->mu);
+      if (!k->ready) continue;
+    }
+    void* d = nullptr;
+    size_t bytes = 0;
+    cudaError_t e = cudaLibraryGetGlobal(&d, &bytes, k->lib, "kx_bad_first");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetGlobal");
+    if (bytes != sizeof(unsigned long long)) return fail(KX_ERR_CUDA, "unexpected size of the point status word");
+    addr.push_back(d);
+  }
+  std::vector<unsigned long long> word(addr.size(), ~0ull);
+  for (size_t j = 0; j < addr.size(); ++j) {
+    cudaError_t e = cudaMemcpyAsync(&word[j], addr[j], sizeof(unsigned long long), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(addr[j], 0xff, sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "point status word");
+  }
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned long long first = ~0ull;
+  for (unsigned long long w : word) first = std::min(first, w);
+  if (first == ~0ull) return KX_OK;
+  *first_bad_point = (int64_t)first;
+  return fail(KX_ERR_NONFINITE_INPUT, "point " + std::to_string(first) +
+                                          " is outside the domain (T or p not positive and finite, or sum Y/W not positive and finite)");
+}
+
 kx_status kx_rates_of_progress(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld, double* q,
                                int64_t n, kx_precision precision, void* stream) {
   kx_status s = check_state(h, T, p, Y, ld, n);

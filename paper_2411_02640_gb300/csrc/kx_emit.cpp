@@ -2691,6 +2691,9 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
+  // the smallest index of a point outside the domain since the host last read and reset it
+  s << "__device__ unsigned long long kx_bad_first = 0xffffffffffffffffull;\n";
+  nan_fill = "atomicMin(&kx_bad_first, (unsigned long long)i); " + nan_fill;
   s << "#define KX_BAD_POINT { " << nan_fill << " continue; }\n";
   // a register cap is expressed as a minimum number of resident blocks (ptxas
   // ignores --maxrregcount for kernels that carry launch bounds).  Defaults,

@@ -17,6 +17,7 @@ from . import build as _build
 _lib: Optional[ctypes.CDLL] = None
 
 FP64, MIXED = 0, 1
+KX_ERR_NONFINITE_INPUT = 9   # kx_last_point_status: a point outside the domain was recorded
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 KERNELS = ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "visc_fp64", "visc_mixed", "diff_fp64",
@@ -55,6 +56,7 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_double)]
         L.kx_production_rates.argtypes = [vp, dp, dp, dp, i64, dp, i64, ctypes.c_int, vp]
         L.kx_production_rates_noalloc.argtypes = [vp, dp, dp, dp, i64, dp, i64, vp]
+        L.kx_last_point_status.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.kx_evaluate_host_bytes_per_state.argtypes = [vp, ctypes.c_int]
         L.kx_evaluate_host_bytes_per_state.restype = i64
         L.kx_evaluate_host.argtypes = [vp, dp, dp, dp, i64, dp, dp, dp, dp, dp, dp, i64, i64, ctypes.c_int, ctypes.c_int,
@@ -245,6 +247,16 @@ class Mechanism:
         _check(lib().kx_production_rates_vjp(self.h, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(v), _ptr(gT), _ptr(gY), n,
                                              _stream(stream)))
         return gT, gY
+
+    def last_point_status(self, stream=None) -> int:
+        """kx_last_point_status: the smallest index of a point outside the
+        domain seen by this handle's calls since the last check (-1 if none);
+        waits for ``stream`` and resets the record."""
+        first = ctypes.c_int64()
+        st = lib().kx_last_point_status(self.h, _stream(stream), ctypes.byref(first))
+        if st != KX_ERR_NONFINITE_INPUT:
+            _check(st)
+        return first.value
 
     def source_hash(self, name: str) -> str:
         h = ctypes.c_uint64()

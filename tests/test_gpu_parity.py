@@ -195,6 +195,41 @@ def test_domain_edges(torch, precision):
     assert out.shape == (mech.n_species, 0)
 
 
+def test_point_status(torch):
+    """kx_last_point_status: the smallest index of a point outside the domain
+    over the calls since the last check, -1 once it has been read; a state
+    whose sum Y/W is zero is outside the domain of the concentrations and
+    mole fractions (rates, transport, adjoint) but not of the thermo call."""
+    name = "h2o2_9_21"
+    mech = mechanism(name)
+    mech.last_point_status()   # clears what earlier tests on this shared handle recorded
+    T, p, Y = _states(name, 300)
+    Td, pd, Yd = to_device(torch, T, p, Y)
+    mech.production_rates(Td, pd, Yd)
+    mech.transport(Td, pd, Yd)
+    assert mech.last_point_status() == -1
+    T2, p2, Y2 = T.copy(), p.copy(), Y.copy()
+    T2[211], p2[97] = -1.0, np.nan
+    Td, pd, Yd = to_device(torch, T2, p2, Y2)
+    mech.thermo(Td, pd, Yd)
+    assert mech.last_point_status() == 97
+    assert mech.last_point_status() == -1
+    mech.production_rates(Td, pd, Yd, precision="mixed")
+    mech.diffusion(Td, pd, Yd)
+    assert mech.last_point_status() == 97
+    Y3 = Y.copy()
+    Y3[:, 150] = 0.0
+    Td, pd, Yd = to_device(torch, T, p, Y3)
+    mech.thermo(Td, pd, Yd)
+    assert mech.last_point_status() == -1
+    for call in (lambda: mech.production_rates(Td, pd, Yd), lambda: mech.viscosity_conductivity(Td, pd, Yd),
+                 lambda: mech.diffusion(Td, pd, Yd, precision="mixed"),
+                 lambda: mech.production_rates_vjp(Td, pd, Yd, torch.ones_like(Yd))):
+        call()
+        assert mech.last_point_status() == 150
+    assert mech.last_point_status() == -1
+
+
 def test_libmath_variant_agrees(torch):
     """The library's own float64 exp/log against CUDA's exp/log: the same
     kernels built both ways agree to 1e-13 relative (transport) and within
