@@ -323,12 +323,17 @@ def run_kx(args):
         e2e_step()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)]
     e0.record(stream)
-    for _ in range(args.steps):
+    for j in range(args.steps):
         e2e_step()
+        if j < args.steps - 1:
+            marks[j].record(stream)
     e1.record(stream)
     barrier()
     e2e_total = e0.elapsed_time(e1)
+    edges = [e0] + marks + [e1]
+    e2e_steps = sorted(a.elapsed_time(b) for a, b in zip(edges[:-1], edges[1:]))
     if world > 1:
         e2e_total = max_over_ranks(e2e_total, dist, dev)
     e2e_ms = e2e_total / args.steps
@@ -412,6 +417,7 @@ def run_kx(args):
                                                         "summed over the step"})(step_bound(names, per)),
             "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "api": "kx_evaluate_host",
                     "chunk": chunk,
+                    "step_ms": {"min": e2e_steps[0], "median": e2e_steps[len(e2e_steps) // 2], "max": e2e_steps[-1]},
                     "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n,
                     "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs,
                                  "note": "one pinned copy of the production-rate array each way"}},
