@@ -230,13 +230,16 @@ int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
 
 /* Production rates, thermo and/or transport for states held in HOST memory
  * (pinned for asynchronous copies), pipelined in chunks: the kernels of
- * even chunks run on stream_a and those of odd chunks on a stream created
- * for the call (one chunk's last blocks overlap the next chunk's first),
- * while stream_b copies the next chunk's inputs in and another stream of
- * the call copies finished chunks' outputs out, so both copy directions
- * overlap the arithmetic.  Events order the streams; before the call
- * returns, stream_a and stream_b are made to wait for everything queued on
- * the call's own streams.  Chunks hold a whole number of waves of the
+ * even chunks run on stream_a and those of odd chunks on a stream of the
+ * library (one chunk's last blocks overlap the next chunk's first), while
+ * stream_b copies the next chunk's inputs in and another library stream
+ * copies finished chunks' outputs out, so both copy directions overlap the
+ * arithmetic.  Events order the streams; before the call returns, stream_a
+ * and stream_b are made to wait for everything queued on the library's
+ * streams.  The library's two streams and eight events are made on a
+ * handle's first call on a device and reused by its later calls there (a
+ * call running on another host thread at the same time gets a set of its
+ * own); kx_free_mechanism releases them.  Chunks hold a whole number of waves of the
  * launched kernels (states that fill every SM's resident blocks once) where
  * the chunk bound allows one.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]

@@ -66,11 +66,24 @@ struct Kernel {
 
 }  // namespace
 
+// The call's own streams and events of kx_evaluate_host, kept for reuse: a
+// call takes one set (of the current device) from the handle's free list and
+// puts it back on return, with its work possibly still in flight; the next
+// call on the same set queues behind it on the same streams.
+struct HostPipe {
+  int device = -1;
+  cudaStream_t qc = nullptr, qd = nullptr;   // copy-out stream, odd chunks' kernels
+  cudaEvent_t ev[8] = {};
+};
+
 struct kx_mech {
   kx::Mechanism m;
   kx_options opt{};
   std::string cache_dir;
   std::vector<std::unique_ptr<Kernel>> kernels;
+  std::mutex pipe_mu;
+  std::vector<std::unique_ptr<HostPipe>> pipes;   // every set this handle made
+  std::vector<HostPipe*> free_pipes;
 };
 
 namespace {
@@ -391,6 +404,11 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
 
 kx_status kx_free_mechanism(kx_handle h) {
   if (!h) return fail(KX_ERR_ARG, "null handle");
+  for (auto& hp : h->pipes) {
+    for (cudaEvent_t e : hp->ev) if (e) cudaEventDestroy(e);
+    if (hp->qc) cudaStreamDestroy(hp->qc);
+    if (hp->qd) cudaStreamDestroy(hp->qd);
+  }
   for (auto& k : h->kernels)
     if (k->lib) cudaLibraryUnload(k->lib);
   delete h;
@@ -639,35 +657,54 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   // tail), the inputs copied in on stream_b one chunk ahead, the outputs copied out on a copy-out
   // stream of this call (so that the two copy directions run at once); per-slot events order them,
   // and on return stream_a and stream_b wait for everything the call's own streams hold
-  cudaStream_t qa0 = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b, qc = nullptr, qd = nullptr;
-  cudaEvent_t ev[8] = {};
+  cudaStream_t qa0 = (cudaStream_t)stream_a, qb = (cudaStream_t)stream_b;
+  HostPipe* hp = nullptr;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(h->pipe_mu);
+    for (size_t j = 0; j < h->free_pipes.size(); ++j)
+      if (h->free_pipes[j]->device == dev) {
+        hp = h->free_pipes[j];
+        h->free_pipes.erase(h->free_pipes.begin() + (long)j);
+        break;
+      }
+    if (!hp) {
+      std::unique_ptr<HostPipe> np(new HostPipe());
+      np->device = dev;
+      cudaError_t e = cudaSuccess;
+      for (int j = 0; j < 8 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&np->ev[j], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&np->qc, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&np->qd, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        for (cudaEvent_t x : np->ev) if (x) cudaEventDestroy(x);
+        if (np->qc) cudaStreamDestroy(np->qc);
+        if (np->qd) cudaStreamDestroy(np->qd);
+        return cuda_fail(e, "evaluate_host streams and events");
+      }
+      hp = np.get();
+      h->pipes.push_back(std::move(np));
+    }
+  }
+  cudaStream_t qc = hp->qc, qd = hp->qd;
+  cudaEvent_t* ev = hp->ev;
+  // on return (also on an error): stream_b waits for the copy-out stream and stream_a for the odd
+  // chunks' kernel stream, and the set goes back to the free list
   struct Guard {
-    cudaEvent_t* e;
-    cudaStream_t *qc, *qd;
+    kx_mech* h;
+    HostPipe* hp;
     cudaStream_t qa, qb;
     ~Guard() {
-      if (*qc) {
-        if (e[6] && cudaEventRecord(e[6], *qc) == cudaSuccess) cudaStreamWaitEvent(qb, e[6], 0);
-        cudaStreamDestroy(*qc);   // released once its queued work finishes
-      }
-      if (*qd) {
-        if (e[7] && cudaEventRecord(e[7], *qd) == cudaSuccess) cudaStreamWaitEvent(qa, e[7], 0);
-        cudaStreamDestroy(*qd);
-      }
-      for (int j = 0; j < 8; ++j) if (e[j]) cudaEventDestroy(e[j]);
+      if (cudaEventRecord(hp->ev[6], hp->qc) == cudaSuccess) cudaStreamWaitEvent(qb, hp->ev[6], 0);
+      if (cudaEventRecord(hp->ev[7], hp->qd) == cudaSuccess) cudaStreamWaitEvent(qa, hp->ev[7], 0);
+      std::lock_guard<std::mutex> lock(h->pipe_mu);
+      h->free_pipes.push_back(hp);
     }
-  } guard{ev, &qc, &qd, qa0, qb};
-  for (int j = 0; j < 8; ++j) {
-    cudaError_t e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
-  }
+  } guard{h, hp, qa0, qb};
   {
-    cudaError_t e = cudaStreamCreateWithFlags(&qc, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { qc = nullptr; return cuda_fail(e, "cudaStreamCreateWithFlags"); }
-    e = cudaStreamCreateWithFlags(&qd, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { qd = nullptr; return cuda_fail(e, "cudaStreamCreateWithFlags"); }
     // the call's streams start after whatever the caller queued on stream_a and stream_b
-    if ((e = cudaEventRecord(ev[6], qb)) == cudaSuccess) e = cudaStreamWaitEvent(qc, ev[6], 0);
+    cudaError_t e = cudaEventRecord(ev[6], qb);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(qc, ev[6], 0);
     if (e == cudaSuccess && (e = cudaEventRecord(ev[7], qa0)) == cudaSuccess) e = cudaStreamWaitEvent(qd, ev[7], 0);
     if (e != cudaSuccess) return cuda_fail(e, "event ordering");
   }
