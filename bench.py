@@ -333,7 +333,8 @@ def run_kx(args):
     barrier()
     e2e_total = e0.elapsed_time(e1)
     edges = [e0] + marks + [e1]
-    e2e_steps = sorted(a.elapsed_time(b) for a, b in zip(edges[:-1], edges[1:]))
+    e2e_times = [a.elapsed_time(b) for a, b in zip(edges[:-1], edges[1:])]
+    e2e_steps = sorted(e2e_times)
     if world > 1:
         e2e_total = max_over_ranks(e2e_total, dist, dev)
     e2e_ms = e2e_total / args.steps
@@ -417,7 +418,8 @@ def run_kx(args):
                                                         "summed over the step"})(step_bound(names, per)),
             "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "api": "kx_evaluate_host",
                     "chunk": chunk,
-                    "step_ms": {"min": e2e_steps[0], "median": e2e_steps[len(e2e_steps) // 2], "max": e2e_steps[-1]},
+                    "step_ms": {"min": e2e_steps[0], "median": e2e_steps[len(e2e_steps) // 2], "max": e2e_steps[-1],
+                                "slowest_step": e2e_times.index(e2e_steps[-1])},
                     "h2d_bytes_per_step": 8 * (2 + ns) * n, "d2h_bytes_per_step": 8 * (2 * ns + 4) * n,
                     "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs,
                                  "note": "one pinned copy of the production-rate array each way"}},

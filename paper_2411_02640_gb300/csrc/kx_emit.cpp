@@ -1735,170 +1735,187 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     o("const float lnSf = __fmul_rn(kx_i2f(S), 0.693147182f);   // S ln2 for the range tests of the scaled exponential");
   }
 
-  // ---- main pass, one loop per class
-  for (size_t ci = 0; ci < cls.size(); ++ci) {
-    const DfClass& d = cls[ci];
-    const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
-    const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
-    const int NF = fo ? 7 : tb ? 3 : 2;
-    const int E = d.nre + d.npr;
-    o(fmt("{   // class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
-    ++o.ind;
-    prologue(d, (int)ci);
-    if (!rop) {
-      std::string pdecl = "int";
-      for (int j = 0; j < E; ++j) pdecl += fmt("%s p%d = 0", j ? "," : "", j);
-      o(pdecl + ";   // entries of the previous reaction (coefficient 0: nothing to add)");
-      o(mx ? "double qp = 0.0;" : "kx_df qp = kx_mk(0.0f, 0.0f);");
-    }
-    o("#pragma unroll 1");
-    o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
-    if (!rop)
-      for (int j = 0; j < E; ++j) o(fmt("  const %s wl%d = w[p%d & 0xffff];", mx ? "double" : "kx_df", j, j));
-    prefetch(d);
-    for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
-    if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
-    o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
-    o("  const float4 f0 = f[0], f1 = f[1];");
-    if (mx) {
-      emit_class_mixed_body(o, d, (int)ci, E, c);
-    } else {
-      o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
-                 : "  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
-      if (tb) {
-        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-        o("  const float4 f2 = f[2];");
-        o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
-        o("  if (e.y < 0) {");
-        o("    const int kc = kx_effd[e.x].k;");
-        o("    X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + i]), KX_PF(kx_iwf + 2 * kc)), fC);");
-        o("  } else {");
-        o("    kx_df t = kx_mk(0.0f, 0.0f);");
-        o("    for (int j = 0; j < e.y; ++j) {");
-        o("      const kx_effd_t q = kx_effd[e.x + j];");
-        o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + i]), KX_PF(kx_iwf + 2 * q.k)), t);");
-        o("    }");
-        o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
-        o("  }");
-        c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
+  // ---- main pass, one loop per class.  Emitted twice: for warps in which some state has a
+  // negative mass fraction (signed concentration products), and for the usual warps without,
+  // where a shadowing constant anyneg = false folds every sign parity away.
+  auto main_pass = [&](OpCounts& c) {
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+      const DfClass& d = cls[ci];
+      const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const int NF = fo ? 7 : tb ? 3 : 2;
+      const int E = d.nre + d.npr;
+      o(fmt("{   // class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
+      ++o.ind;
+      prologue(d, (int)ci);
+      if (!rop) {
+        std::string pdecl = "int";
+        for (int j = 0; j < E; ++j) pdecl += fmt("%s p%d = 0", j ? "," : "", j);
+        o(pdecl + ";   // entries of the previous reaction (coefficient 0: nothing to add)");
+        o(mx ? "double qp = 0.0;" : "kx_df qp = kx_mk(0.0f, 0.0f);");
       }
-      if (fo) {
-        o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
-        o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
-        o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
-        o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
-        o("  kx_df lnF = kx_mk(0.0f, 0.0f);");
-        const std::string il10 = DFc(1.0 / std::log(10.0));
-        if (d.blend == Blend::Troe) {
-          o("  kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
-          o("  Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
-          o("  Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
-          o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
-          o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
-          o(fmt("  const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
-                DFc(0.75).c_str()));
-          o(fmt("  lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
-          c.fp32 += d.rx.size() * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
-        } else if (d.blend == Blend::Sri) {
-          o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
-          o("  const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
-          o("  lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
-          c.fp32 += d.rx.size() * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
+      o("#pragma unroll 1");
+      o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
+      if (!rop)
+        for (int j = 0; j < E; ++j) o(fmt("  const %s wl%d = w[p%d & 0xffff];", mx ? "double" : "kx_df", j, j));
+      prefetch(d);
+      for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
+      if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
+      o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+      o("  const float4 f0 = f[0], f1 = f[1];");
+      if (mx) {
+        emit_class_mixed_body(o, d, (int)ci, E, c);
+      } else {
+        o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
+                   : "  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+        if (tb) {
+          o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+          o("  const float4 f2 = f[2];");
+          o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
+          o("  if (e.y < 0) {");
+          o("    const int kc = kx_effd[e.x].k;");
+          o("    X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + i]), KX_PF(kx_iwf + 2 * kc)), fC);");
+          o("  } else {");
+          o("    kx_df t = kx_mk(0.0f, 0.0f);");
+          o("    for (int j = 0; j < e.y; ++j) {");
+          o("      const kx_effd_t q = kx_effd[e.x + j];");
+          o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + i]), KX_PF(kx_iwf + 2 * q.k)), t);");
+          o("    }");
+          o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+          o("  }");
+          c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
         }
-        o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
-        o("  const bool small = lnPr.hi < 0.0f;");
-        o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
-        if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
-        else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
-        c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
-      } else if (d.kind == Kind::Plog) {
-        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-        o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
-        o("  const long long Pb = __double_as_longlong(P);");
-        o("  if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
-        o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
-        o("  else {");
-        o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
-        o("    const float* u = t + 8 * j;");
-        o("    const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
-        o("    const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
-        o("    lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
-        o("  }");
-        c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
-      }
-      // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
-      o("  kx_df lf = lk;");
-      for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
-      if (d.nre > 0) o("  lf = kx_df_norm(lf);");
-      std::string sfx = "0", srx = "0";
-      for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
-      for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
-      o("  int sf = anyneg ? (" + sfx + ") : 0;");
-      o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
-      o("  bool rev = false;");
-      c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + d.nre * kDfAdd + kDfExp + kDfMul);
-      if (d.rev) {
-        const int dn = d.npr - d.nre;
-        o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
-        std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
-        o("    kx_df dl = " + first + ";");
-        for (int j = 1; j < E; ++j)
-          o(fmt("    dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
-        if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
-        else if (dn != 0) o(fmt("    dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-        o("    dl = kx_df_norm(dl);");
-        o("    const int sr = anyneg ? (" + srx + ") : 0;");
-        o("    rev = dl.hi > 0.0f;");
-        o("    if (rev) L = kx_df_add(lf, dl);");
-        o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
-        o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
-        o("    const float pm = sf == sr ? -1.0f : 1.0f;");
-        o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
-        o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
-        o("    if (sf == sr) sf ^= (int)rev;");
-        o("  }");
-        c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+        if (fo) {
+          o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+          o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
+          o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+          o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+          o("  kx_df lnF = kx_mk(0.0f, 0.0f);");
+          const std::string il10 = DFc(1.0 / std::log(10.0));
+          if (d.blend == Blend::Troe) {
+            o("  kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
+            o("  Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
+            o("  Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
+            o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+            o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+            o(fmt("  const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
+                  DFc(0.75).c_str()));
+            o(fmt("  lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
+            c.fp32 += d.rx.size() * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
+          } else if (d.blend == Blend::Sri) {
+            o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+            o("  const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
+            o("  lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
+            c.fp32 += d.rx.size() * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
+          }
+          o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
+          o("  const bool small = lnPr.hi < 0.0f;");
+          o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
+          if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
+          else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
+          c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
+        } else if (d.kind == Kind::Plog) {
+          o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+          o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+          o("  const long long Pb = __double_as_longlong(P);");
+          o("  if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
+          o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
+          o("  else {");
+          o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+          o("    const float* u = t + 8 * j;");
+          o("    const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
+          o("    const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
+          o("    lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
+          o("  }");
+          c.fp32 += d.rx.size() * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
+        }
+        // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
+        o("  kx_df lf = lk;");
+        for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
+        if (d.nre > 0) o("  lf = kx_df_norm(lf);");
+        std::string sfx = "0", srx = "0";
+        for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+        for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+        o("  int sf = anyneg ? (" + sfx + ") : 0;");
+        o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
+        o("  bool rev = false;");
+        c.fp32 += d.rx.size() * ((d.kconst ? 0 : 2 * kDfFma) + d.nre * kDfAdd + kDfExp + kDfMul);
+        if (d.rev) {
+          const int dn = d.npr - d.nre;
+          o("  {   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
+          std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+          o("    kx_df dl = " + first + ";");
+          for (int j = 1; j < E; ++j)
+            o(fmt("    dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+          if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+          else if (dn != 0) o(fmt("    dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+          o("    dl = kx_df_norm(dl);");
+          o("    const int sr = anyneg ? (" + srx + ") : 0;");
+          o("    rev = dl.hi > 0.0f;");
+          o("    if (rev) L = kx_df_add(lf, dl);");
+          o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
+          o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
+          o("    const float pm = sf == sr ? -1.0f : 1.0f;");
+          o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
+          o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
+          o("    if (sf == sr) sf ^= (int)rev;");
+          o("  }");
+          c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+        }
+        if (rop) {
+          o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
+          o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
+          c.fp32 += d.rx.size() * 4;
+        } else {
+          o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S");
+        }
+        o("  if (sf) q = kx_df_neg(q);");
+        if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
       }
       if (rop) {
-        o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
-        o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
-        c.fp32 += d.rx.size() * 4;
+        o(mx ? "  out_[(long long)ri * ld + i] = q;" : "  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
+        c.fp64 += d.rx.size();
+      } else if (mx) {
+        for (int j = 0; j < E; ++j)
+          o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = fma(kx_f2d(kx_i2f(cj)), qp, wl%d); }", j, j, j));
+        o("  qp = q;");
+        for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
+        c.fp64 += d.rx.size() * E;
       } else {
-        o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S");
+        // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
+        for (int j = 0; j < E; ++j)
+          o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add_u(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
+        o("  qp = q;");
+        for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
+        c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
       }
-      o("  if (sf) q = kx_df_neg(q);");
-      if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
+      advance(d);
+      o("}");
+      if (!rop && mx)
+        for (int j = 0; j < E; ++j)
+          o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(kx_i2f(cj)), qp, w[kk]); } }",
+                j, j));
+      else if (!rop)
+        for (int j = 0; j < E; ++j)
+          o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add_u(w[kk], kx_df_nu(qp, cj)); } }",
+                j, j));
+      --o.ind;
+      o("}");
     }
-    if (rop) {
-      o(mx ? "  out_[(long long)ri * ld + i] = q;" : "  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
-      c.fp64 += d.rx.size();
-    } else if (mx) {
-      for (int j = 0; j < E; ++j)
-        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = fma(kx_f2d(kx_i2f(cj)), qp, wl%d); }", j, j, j));
-      o("  qp = q;");
-      for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
-      c.fp64 += d.rx.size() * E;
-    } else {
-      // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
-      for (int j = 0; j < E; ++j)
-        o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add_u(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
-      o("  qp = q;");
-      for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
-      c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
-    }
-    advance(d);
-    o("}");
-    if (!rop && mx)
-      for (int j = 0; j < E; ++j)
-        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(kx_i2f(cj)), qp, w[kk]); } }",
-              j, j));
-    else if (!rop)
-      for (int j = 0; j < E; ++j)
-        o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add_u(w[kk], kx_df_nu(qp, cj)); } }",
-              j, j));
-    --o.ind;
-    o("}");
+  };
+  o("if (__any_sync(__activemask(), anyneg)) {");
+  ++o.ind;
+  main_pass(c);
+  --o.ind;
+  o("} else {");
+  ++o.ind;
+  o("const bool anyneg = false;   // no state of this warp has a negative mass fraction");
+  {
+    OpCounts once;   // the operations are counted for one of the two copies
+    main_pass(once);
   }
+  --o.ind;
+  o("}");
   if (!rop) {
     o(fmt(mx ? "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = w[k];"
              : "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));

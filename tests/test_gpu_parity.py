@@ -68,6 +68,29 @@ def test_negative_mass_fractions_fp64(torch, name, arith):
     assert rel.max() <= 1e-10, f"max {rel.max():.3e}"
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_negative_mass_fractions_in_some_warps(torch, precision):
+    """Negative mass fractions in a few scattered states only: most warps of
+    32 states have none (the rate kernels' sign-free copy of the reaction
+    loops) and the others mix signed and unsigned states (the signed copy);
+    both against the oracle."""
+    name = "gri_53_325"
+    n = CASES[name]
+    T, p, Y = _states(name, n, start=907)
+    rng = np.random.default_rng(23)
+    some = np.arange(0, n, 97)
+    for i in some:
+        k = rng.choice(Y.shape[0], 3, replace=False)
+        Y[k, i] = -1e-4 * rng.random(3)
+    mech = mechanism(name)
+    Td, pd, Yd = to_device(torch, T, p, Y, ld=n + LD_PAD)
+    w = mech.production_rates(Td, pd, Yd, precision=precision)[:, :n].cpu().numpy()
+    o = oracle(name)
+    err = wdot_error(np.array(mech.W), w, o.production_rates(T, p, Y))
+    assert err.max() <= (1e-10 if precision == "fp64" else 2e-4), f"max {err.max():.3e}"
+    assert err[some].max() <= (1e-10 if precision == "fp64" else 2e-4)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_rates_of_progress_fp64(torch, name):
     n = CASES[name]
