@@ -459,13 +459,9 @@ template <typename V> struct kx_strided {
   long long s;
   __device__ __forceinline__ V& operator[](int k) const { return p[(long long)k * s]; }
 };
-// nu q for a small integer nu: an exact scaling of both parts for |nu| <= 2,
-// a float-pair product otherwise (nu is the same for every thread of a warp)
-__device__ __forceinline__ kx_df kx_df_nu(kx_df q, int nu) {
-  const float f = kx_i2f(nu);
-  if (nu >= -2 && nu <= 2) return kx_mk(__fmul_rn(q.hi, f), __fmul_rn(q.lo, f));
-  return kx_df_mulf(q, f);
-}
+// nu q for a coefficient nu in {-2, -1, 1, 2}: an exact scaling of both parts
+// (larger coefficients take the float-pair product kx_df_mulf)
+__device__ __forceinline__ kx_df kx_df_scale2(kx_df q, float nu) { return kx_mk(__fmul_rn(q.hi, nu), __fmul_rn(q.lo, nu)); }
 // (a.hi + a.lo) 2^S as a double: one float64 addition, the power of two
 // added to the exponent field (ldexp only when the result leaves the normal
 // range)
@@ -1385,6 +1381,7 @@ struct DfClass {
   int nre, npr;
   bool kconst;          // k = A (beta = E = 0; elementary and three-body reactions): ln k needs no arithmetic
   std::vector<int> rx;
+  int maxnu = 0;        // largest |net coefficient| of an entry (set with the tables)
 };
 
 std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
@@ -1484,13 +1481,13 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     auto it = std::find_if(cls.begin(), cls.end(), [&](const DfClass& d) {
       return d.kind == r.kind && d.rev == r.reversible && d.blend == bl && d.nre == nre && d.npr == npr && d.kconst == kc;
     });
-    if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, kc, {}}); it = cls.end() - 1; }
+    if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, kc, {}, 0}); it = cls.end() - 1; }
     it->rx.push_back(i);
   }
   std::string eff, plog, plogp;
   int eo = 0, po = 0;
   for (size_t ci = 0; ci < cls.size(); ++ci) {
-    const DfClass& d = cls[ci];
+    DfClass& d = cls[ci];
     const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
     const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
     const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
@@ -1500,8 +1497,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       const Reaction& r = m.rx[i];
       auto er = entries(r.reac), ep = entries(r.prod);
       {
-        // entry j: species k | (c << 16), c = the species' net coefficient on its first entry, 0 on
-        // repeats (so that the accumulators are updated once per species)
+        // entry j: species k in the low 16 bits, and in the high 16 bits the upper half of the float32
+        // of c, the species' net coefficient on its first entry and 0 on repeats (so that the
+        // accumulators are updated once per species); integers up to 256 in magnitude are exact there
         std::vector<int> ek(er);
         ek.insert(ek.end(), ep.begin(), ep.end());
         std::map<int, int> net;
@@ -1511,7 +1509,11 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         for (int k : ek) {
           const int cc = seen.count(k) ? 0 : net[k];
           seen.insert(k);
-          si += std::to_string(k + 65536 * cc) + ",";
+          d.maxnu = std::max(d.maxnu, std::abs(cc));
+          const float fc = (float)cc;
+          uint32_t fb;
+          std::memcpy(&fb, &fc, 4);
+          si += std::to_string((int32_t)((fb & 0xffff0000u) | (uint32_t)k)) + ",";
         }
       }
       si += std::to_string(i) + ",";
@@ -1877,14 +1879,15 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         c.fp64 += d.rx.size();
       } else if (mx) {
         for (int j = 0; j < E; ++j)
-          o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = fma(kx_f2d(kx_i2f(cj)), qp, wl%d); }", j, j, j));
+          o(fmt("  { const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) w[p%d & 0xffff] = fma(kx_f2d(__uint_as_float(cj)), qp, wl%d); }", j, j, j));
         o("  qp = q;");
         for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
         c.fp64 += d.rx.size() * E;
       } else {
         // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
         for (int j = 0; j < E; ++j)
-          o(fmt("  { const int cj = p%d >> 16; if (cj != 0) w[p%d & 0xffff] = kx_df_add_u(wl%d, kx_df_nu(qp, cj)); }", j, j, j));
+          o(fmt("  { const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) w[p%d & 0xffff] = kx_df_add_u(wl%d, %s(qp, __uint_as_float(cj))); }",
+                j, j, j, d.maxnu <= 2 ? "kx_df_scale2" : "kx_df_mulf"));
         o("  qp = q;");
         for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
         c.fp32 += d.rx.size() * E * (kDfAdd + kDfMulf) / 2.0;
@@ -1893,12 +1896,12 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       o("}");
       if (!rop && mx)
         for (int j = 0; j < E; ++j)
-          o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(kx_i2f(cj)), qp, w[kk]); } }",
+          o(fmt("{ const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(__uint_as_float(cj)), qp, w[kk]); } }",
                 j, j));
       else if (!rop)
         for (int j = 0; j < E; ++j)
-          o(fmt("{ const int cj = p%d >> 16; if (cj != 0) { const int kk = p%d & 0xffff; w[kk] = kx_df_add_u(w[kk], kx_df_nu(qp, cj)); } }",
-                j, j));
+          o(fmt("{ const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) { const int kk = p%d & 0xffff; w[kk] = kx_df_add_u(w[kk], %s(qp, __uint_as_float(cj))); } }",
+                j, j, d.maxnu <= 2 ? "kx_df_scale2" : "kx_df_mulf"));
       --o.ind;
       o("}");
     }
