@@ -428,6 +428,25 @@ __device__ __forceinline__ kx_df kx_df_exp_s(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+// e^x of a non-positive float pair (the upper range test of kx_df_exp_s drops out)
+__device__ __forceinline__ kx_df kx_df_exp_n(kx_df x) {
+  if (!(x.hi > -87.0f)) return kx_mk(0.0f, 0.0f);
+  const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_C1F, x.hi);
+  const float p = __fmul_rn(kf, KX_C2F);
+  const float pe = __fmaf_rn(kf, KX_C2F, -p);
+  kx_df r = kx_ts(t1, -p);
+  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_C3F))));
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const float sc = __int_as_float(((k >> 8) + 127) << 23);
+  return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
+}
 // e^x 2^-S of a float pair as a float pair, S an integer with |S| <= 1100 and
 // Sl = S ln2 in float32 (for the range test only): 0 where x - S ln2 <= -87,
 // inf where it is >= 88.7.  The reduction x = k ln2/256 + r takes x itself
@@ -1549,7 +1568,8 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         }
       }
     }
-    g(fmt("__device__ const __align__(16) int kx_s%d[%d] = {%s};", (int)ci, P * (int)d.rx.size(), si.c_str()));
+    for (int j = 0; j < P; ++j) si += "0,";   // one record past the last: the loops prefetch it
+    g(fmt("__device__ const __align__(16) int kx_s%d[%d] = {%s};", (int)ci, P * ((int)d.rx.size() + 1), si.c_str()));
     g(fmt("__device__ const float4 kx_f%d[%d] = {%s};", (int)ci, NF * (int)d.rx.size(), sf.c_str()));
     if (tb || d.kind == Kind::Plog) g(fmt("__device__ const int2 kx_e%d[%d] = {%s};", (int)ci, (int)d.rx.size(), se.c_str()));
   }
@@ -1667,8 +1687,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   };
   auto prefetch = [&](const DfClass& d) {
     const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
-    o(fmt("  const int rn = r + 1 < %d ? r + 1 : r;", (int)d.rx.size()));
-    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 n%d = sp4[%d * rn + %d];", q, P / 4, q));
+    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 n%d = sp4[%d * (r + 1) + %d];", q, P / 4, q));
     for (int j = 0; j < E; ++j) o(fmt("  const float4 u%d = sv[%s];", j, spc("n", j).c_str()));
   };
   auto advance = [&](const DfClass& d) {
@@ -1812,7 +1831,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           }
           o("  // ln(Pr/(1+Pr)) (falloff) or ln(1/(1+Pr)) (chemically activated) from l1p = ln(1 + e^-|ln Pr|)");
           o("  const bool small = lnPr.hi < 0.0f;");
-          o("  const kx_df l1p = kx_df_log1p(kx_df_exp_s(small ? lnPr : kx_df_neg(lnPr)));");
+          o("  const kx_df l1p = kx_df_log1p(kx_df_exp_n(small ? lnPr : kx_df_neg(lnPr)));");
           if (d.kind == Kind::Falloff) o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
           else o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
           c.fp32 += d.rx.size() * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
@@ -1855,7 +1874,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("    const int sr = anyneg ? (" + srx + ") : 0;");
           o("    rev = dl.hi > 0.0f;");
           o("    if (rev) L = kx_df_add(lf, dl);");
-          o("    const kx_df e = kx_df_exp_s(rev ? kx_df_neg(dl) : dl);");
+          o("    const kx_df e = kx_df_exp_n(rev ? kx_df_neg(dl) : dl);");
           o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
           o("    const float pm = sf == sr ? -1.0f : 1.0f;");
           o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
