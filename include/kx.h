@@ -239,9 +239,11 @@ int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
  * streams.  The library's two streams and eight events are made on a
  * handle's first call on a device and reused by its later calls there (a
  * call running on another host thread at the same time gets a set of its
- * own); kx_free_mechanism releases them.  Chunks hold a whole number of waves of the
- * launched kernels (states that fill every SM's resident blocks once) where
- * the chunk bound allows one.  T, p [n], Y [N_s][ld] are
+ * own); kx_free_mechanism releases them.  Chunks hold a whole number of
+ * waves of the launched kernels (states that fill every SM's resident
+ * blocks once) where the chunk bound allows one; when there are more than
+ * two, the first is a quarter chunk, so that the copy-in nothing overlaps
+ * is short.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
  * are host outputs, those not selected by `outputs` may be NULL.
  * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk

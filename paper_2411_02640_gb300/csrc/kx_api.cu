@@ -711,7 +711,15 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   cudaEvent_t* in_done = ev;          // inputs of the slot copied in
   cudaEvent_t* comp_done = ev + 2;    // kernels of the slot finished
   cudaEvent_t* out_done = ev + 4;     // outputs of the slot copied out
-  const int64_t nchunks = (n + c - 1) / c;
+  // chunk bounds: a first chunk of a quarter slot (the copy-in that nothing hides is short; its
+  // kernels share the GPU with the next chunk's, which run on the other stream), then full slots
+  std::vector<int64_t> at{0};
+  {
+    int64_t pos = 0;
+    if (n > 2 * c && c >= 1024) at.push_back(pos = c / 4 / 256 * 256);
+    while (pos < n) at.push_back(pos = std::min(n, pos + c));
+  }
+  const int64_t nchunks = (int64_t)at.size() - 1;
   auto slot = [&](int64_t i, double** dT, double** dp, double** dY, double** dw, double** dcp, double** dh, double** dmu,
                   double** dl, double** dD) {
     double* b = (double*)((char*)workspace + (size_t)(i % 2) * (size_t)c * (size_t)per);
@@ -725,7 +733,7 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   auto copy_in = [&](int64_t i) -> kx_status {
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    const int64_t c0 = at[i], m = at[i + 1] - at[i];
     // the slot's inputs are free once the kernels of chunk i - 2 finished
     cudaError_t e = i >= 2 ? cudaStreamWaitEvent(qb, comp_done[i % 2], 0) : cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T + c0, m * 8, cudaMemcpyHostToDevice, qb);
@@ -742,7 +750,7 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
     if (i + 1 < nchunks && (s = copy_in(i + 1)) != KX_OK) return s;
     double *dT, *dp, *dY, *dw, *dcp, *dh, *dmu, *dl, *dD;
     slot(i, &dT, &dp, &dY, &dw, &dcp, &dh, &dmu, &dl, &dD);
-    const int64_t c0 = i * c, m = std::min(c, n - c0);
+    const int64_t c0 = at[i], m = at[i + 1] - at[i];
     cudaStream_t qa = i % 2 ? qd : qa0;
     cudaError_t e = cudaStreamWaitEvent(qa, in_done[i % 2], 0);
     if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(qa, out_done[i % 2], 0);
