@@ -235,6 +235,11 @@ __device__ __forceinline__ kx_df kx_df_mul(kx_df a, kx_df b) {
   const float p = __fmul_rn(a.hi, b.hi);
   return kx_qts(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))));
 }
+// a*b without the final renormalisation (an operand of a further product or running sum)
+__device__ __forceinline__ kx_df kx_df_mul_u(kx_df a, kx_df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return kx_mk(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))));
+}
 __device__ __forceinline__ double kx_df2d(kx_df a) { return kx_f2d(a.hi) + kx_f2d(a.lo); }
 // a / b: a reciprocal estimate refined by one Newton step, then one
 // correction of the quotient from the exact remainder a - q1 b
@@ -1788,7 +1793,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         emit_class_mixed_body(o, d, (int)ci, E, c);
       } else {
         o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
-                   : "  kx_df lk = kx_df_fma(kx_mk(f0.z, f0.w), lnT, kx_df_fma(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+                   : "  kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
         if (tb) {
           o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
           o("  const float4 f2 = f[2];");
@@ -1873,25 +1878,25 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("    dl = kx_df_norm(dl);");
           o("    const int sr = anyneg ? (" + srx + ") : 0;");
           o("    rev = dl.hi > 0.0f;");
-          o("    if (rev) L = kx_df_add(lf, dl);");
+          o("    if (rev) L = kx_df_add_u(lf, dl);");
           o("    const kx_df e = kx_df_exp_n(rev ? kx_df_neg(dl) : dl);");
           o("    // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|): minus for equal signs, plus for opposite signs");
           o("    const float pm = sf == sr ? -1.0f : 1.0f;");
           o("    const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
-          o("    fac = kx_qts(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
+          o("    fac = kx_mk(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
           o("    if (sf == sr) sf ^= (int)rev;");
           o("  }");
           c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
         }
         if (rop) {
           o("  const int Sr = kx_rint(fminf(fmaxf(L.hi * KX_LOG2E_F, -1000.0f), 1000.0f));");
-          o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
+          o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
           c.fp32 += d.rx.size() * 4;
         } else {
-          o("  kx_df q = kx_df_mul(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S");
+          o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S (the products and sums after it take hi + lo as is)");
         }
         o("  if (sf) q = kx_df_neg(q);");
-        if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
+        if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul_u(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
       }
       if (rop) {
         o(mx ? "  out_[(long long)ri * ld + i] = q;" : "  out_[(long long)ri * ld + i] = kx_df2d_s(q, Sr);");
@@ -2281,6 +2286,10 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   auto MUL = [&](const std::string& a, const std::string& b) {
     return md.kind == TrMode::DF ? fmt("kx_df_mul(%s, %s)", a.c_str(), b.c_str()) : fmt("(%s) * (%s)", a.c_str(), b.c_str());
   };
+  // a*b feeding a further product or running sum (float pairs: no final renormalisation)
+  auto MULU = [&](const std::string& a, const std::string& b) {
+    return md.kind == TrMode::DF ? fmt("kx_df_mul_u(%s, %s)", a.c_str(), b.c_str()) : MUL(a, b);
+  };
   auto EXP = [&](const std::string& a) {
     return fmt("%s(%s)", md.kind == TrMode::DF ? "kx_df_exp" : md.kind == TrMode::F32 ? "exp2f" : "kx_exp", a.c_str());
   };
@@ -2468,8 +2477,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o(fmt("    const %s A = %s, Ab = %s;", md.ty, ld("a[j]").c_str(), ld("a[j + 1]").c_str()));
     o(fmt("    const %s xa = %s, va = %s, xb = %s, vb = %s;", md.ty, ld(XS("j")).c_str(), ld(VS("sZ1", "j")).c_str(),
           ld(XS("(j + 1)")).c_str(), ld(VS("sZ1", "(j + 1)")).c_str()));
-    o(fmt("    const %s wa = %s, wb = %s;", md.ty, FMA("u", "va", ONE1).c_str(), FMA("u", "vb", ONE1).c_str()));
-    o(fmt("    const %s pa = %s, pb = %s;", md.ty, MUL("A", MUL("wa", "wa")).c_str(), MUL("Ab", MUL("wb", "wb")).c_str()));
+    o(fmt("    const %s wa = %s, wb = %s;", md.ty, ACC("u", "va", ONE1).c_str(), ACC("u", "vb", ONE1).c_str()));
+    o(fmt("    const %s pa = %s, pb = %s;", md.ty, MULU("A", MULU("wa", "wa")).c_str(), MULU("Ab", MULU("wb", "wb")).c_str()));
     o(fmt("    r0 = %s; r1 = %s;", ACC("xa", "pa", "r0").c_str(), ACC("xb", "pb", "r1").c_str()));
     o(fmt("    const %s ca = %s, cb = %s;", md.ty, ACC("xr", "pa", ld(VS("sZ2", "j"))).c_str(),
           ACC("xr", "pb", ld(VS("sZ2", "(j + 1)"))).c_str()));
@@ -2478,8 +2487,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o("  }");
     o(fmt("  if (j < %d) {", ns));
     o(fmt("    const %s A = %s, xa = %s, va = %s;", md.ty, ld("a[j]").c_str(), ld(XS("j")).c_str(), ld(VS("sZ1", "j")).c_str()));
-    o(fmt("    const %s wa = %s;", md.ty, FMA("u", "va", ONE1).c_str()));
-    o(fmt("    const %s pa = %s;", md.ty, MUL("A", MUL("wa", "wa")).c_str()));
+    o(fmt("    const %s wa = %s;", md.ty, ACC("u", "va", ONE1).c_str()));
+    o(fmt("    const %s pa = %s;", md.ty, MULU("A", MULU("wa", "wa")).c_str()));
     o(fmt("    r0 = %s;", ACC("xa", "pa", "r0").c_str()));
     o(fmt("    const %s ca = %s;", md.ty, ACC("xr", "pa", ld(VS("sZ2", "j"))).c_str()));
     o("    " + st(VS("sZ2", "j"), "ca"));
@@ -2571,10 +2580,11 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   // carries one zero pair of padding), so their latency hides behind the
   // current pair's arithmetic
   std::string vec;
-  // exponential of one pair's polynomial, coefficients in the float4/double2/float2 triple (x, y, z)
+  // exponential of one pair's polynomial, coefficients in the float4/double2/float2 triple (x, y, z);
+  // float pairs: no renormalisation inside (the exponential and the running sums take hi + lo as is)
   auto pexp = [&](const char* e, const char* x, const char* y, const char* z) {
     if (direct && md.kind == TrMode::DF)   // 1/D_kj itself
-      return fmt("const kx_df %s = kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
+      return fmt("const kx_df %s = kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
                  "kx_mk(%s.x, %s.y)), L, kx_mk(%s.z, %s.w)), L, kx_mk(%s.x, %s.y));",
                  e, z, z, y, y, y, y, x, x, x, x);
     if (direct && md.kind == TrMode::F64)
@@ -2582,7 +2592,7 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     if (direct)
       return fmt("const float %s = fmaf(fmaf(fmaf(fmaf(%s.x, L, %s.y), L, %s.x), L, %s.y), L, %s.x);", e, z, y, y, x, x);
     if (md.kind == TrMode::DF)
-      return fmt("const kx_df %s = kx_df_exp(kx_df_fma(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
+      return fmt("const kx_df %s = kx_df_exp(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_df_fma_u(kx_mk(%s.x, %s.y), L, kx_mk(%s.z, %s.w)), L, "
                  "kx_mk(%s.x, %s.y)), L, kx_mk(%s.z, %s.w)), L, kx_mk(%s.x, %s.y)));",
                  e, z, z, y, y, y, y, x, x, x, x);
     if (md.kind == TrMode::F64)
