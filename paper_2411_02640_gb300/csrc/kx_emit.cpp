@@ -433,7 +433,8 @@ __device__ __forceinline__ kx_df kx_df_exp_s(kx_df x) {
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
-// e^x of a non-positive float pair (the upper range test of kx_df_exp_s drops out)
+// e^x of a non-positive float pair (the upper range test of kx_df_exp_s drops out); x may be
+// unnormalised (|x.lo| a few ulp of x.hi)
 __device__ __forceinline__ kx_df kx_df_exp_n(kx_df x) {
   if (!(x.hi > -87.0f)) return kx_mk(0.0f, 0.0f);
   const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
@@ -443,7 +444,7 @@ __device__ __forceinline__ kx_df kx_df_exp_n(kx_df x) {
   const float p = __fmul_rn(kf, KX_C2F);
   const float pe = __fmaf_rn(kf, KX_C2F, -p);
   kx_df r = kx_ts(t1, -p);
-  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_C3F))));
+  r = kx_ts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_C3F))));   // x.lo may exceed r.hi: two-sum
   const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
   kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
   s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
@@ -468,7 +469,7 @@ __device__ __forceinline__ kx_df kx_df_exp_sc(kx_df x, int S, float Sl) {
   const float p = __fmul_rn(kf, KX_E2F);
   const float pe = __fmaf_rn(kf, KX_E2F, -p);
   kx_df r = kx_ts(t1, -p);
-  r = kx_qts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_E3F))));
+  r = kx_ts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_E3F))));   // x.lo may exceed r.hi: two-sum
   const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
   kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
   s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
@@ -1479,10 +1480,12 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
     o("  // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T)) in float pairs, rounded to float32 once");
     std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
     o("  kx_df dl = " + first + ";");
-    for (int j = 1; j < E; ++j) o(fmt("  dl = kx_df_%s(dl, kx_mk(v%d.z, v%d.w));", j < d.nre ? "sub" : "add", j, j));
-    if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_%s(dl, lnPRT);", dn == 1 ? "sub" : "add"));
-    else if (dn != 0) o(fmt("  dl = kx_df_add(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-    o("  const double q = kx_net_rate_s(lnRf, dl.hi, sf, anyneg ? (" + srx + ") : 0);");
+    // the high parts summed exactly (two-sum), the errors and low parts beside them, one rounding at the end
+    for (int j = 1; j < E; ++j)
+      o(fmt("  dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+    if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+    else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+    o("  const double q = kx_net_rate_s(lnRf, __fadd_rn(dl.hi, dl.lo), sf, anyneg ? (" + srx + ") : 0);");
     c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + 10); c.exp32 += d.rx.size() * 2;
   } else {
     o("  const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
@@ -1858,7 +1861,6 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         // ln |R_f| (scaled by 2^-S) and the sign of prod C^nu'
         o("  kx_df lf = lk;");
         for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
-        if (d.nre > 0) o("  lf = kx_df_norm(lf);");
         std::string sfx = "0", srx = "0";
         for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
         for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
@@ -1875,7 +1877,6 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
             o(fmt("    dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
           if (dn == 1 || dn == -1) o(fmt("    dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
           else if (dn != 0) o(fmt("    dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-          o("    dl = kx_df_norm(dl);");
           o("    const int sr = anyneg ? (" + srx + ") : 0;");
           o("    rev = dl.hi > 0.0f;");
           o("    if (rev) L = kx_df_add_u(lf, dl);");
