@@ -1,6 +1,6 @@
 """Every reaction form the file format carries -- three-body with
 efficiencies and with a single collider species, Lindemann, Troe and SRI
-falloff, chemically activated falloff, PLOG, irreversible -- through the
+falloff, chemically activated falloff, PLOG, irreversible, a coefficient of 3 -- through the
 GPU kernels against the oracle (rates of progress, production rates, the
 adjoint)."""
 import numpy as np
@@ -25,7 +25,10 @@ def _mechanism(tmp_path_factory):
           Reaction(kind="plog", reversible=True, reactants=[(0, 1), (1, 1)], products=[(2, 1)], rate=(0, 0, 0),
                    plog=[(0.1 * P_ATM, 1e9, 0.2, 300.0), (1.0 * P_ATM, 3e9, 0.0, 500.0), (10 * P_ATM, 1e11, -0.3, 900.0)]),
           Reaction(kind="elementary", reversible=False, reactants=[(2, 1)], products=[(0, 1), (1, 1)],
-                   rate=(1e13, 0.0, 2e4))]
+                   rate=(1e13, 0.0, 2e4)),
+          # net coefficients of 3 (the float-pair product path of the accumulation, not the exact scaling)
+          Reaction(kind="elementary", reversible=True, reactants=[(2, 3)], products=[(0, 3), (1, 3)],
+                   rate=(1e8, 0.5, 1000.0))]
     _, path = toys.toy("kinds", rx, d)
     return path
 

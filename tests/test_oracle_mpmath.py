@@ -225,7 +225,9 @@ def _kinds_mechanism(directory):
           Reaction(kind="elementary", reversible=False, reactants=[(2, 1)], products=[(0, 1), (1, 1)],
                    rate=(1e13, 0.0, 2e4)),
           Reaction(kind="elementary", reversible=True, reactants=[(2, 2)], products=[(0, 2), (1, 2)],
-                   rate=(1e8, 1.5, 5e3))]
+                   rate=(1e8, 1.5, 5e3)),
+          Reaction(kind="elementary", reversible=True, reactants=[(2, 3)], products=[(0, 3), (1, 3)],
+                   rate=(1e7, 0.5, 1000.0))]
     return toys.toy("kinds", rx, directory)
 
 
