@@ -285,7 +285,7 @@ __device__ __forceinline__ kx_df kx_df_exp(kx_df x) {
   kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
   s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
   const float2 tj = kx_s_dexp[k & 255];
-  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const kx_df v = kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
   const float sc = __int_as_float(((k >> 8) + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
@@ -474,7 +474,7 @@ __device__ __forceinline__ kx_df kx_df_exp_sc(kx_df x, int S, float Sl) {
   kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
   s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
   const float2 tj = kx_s_dexp[k & 255];
-  const kx_df v = kx_df_fma(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));
+  const kx_df v = kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
   const float sc = __int_as_float(((k >> 8) - S + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
