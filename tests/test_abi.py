@@ -103,3 +103,28 @@ def test_transport_fit_keyword(tmp_path):
     with pytest.raises(kx.KxError) as e:
         kx.Mechanism(str(bad), compile_only=1, lazy=1, cache_dir=str(tmp_path / "c"))
     assert e.value.status == 2          # KX_ERR_PARSE
+
+
+def test_host_side_argument_checks_of_the_status_and_no_alloc_calls(tmp_path):
+    """kx_last_point_status and kx_production_rates_noalloc refuse a null
+    handle or pointer and a handle that was only compiled (no device), before
+    any CUDA call."""
+    L = kx.lib()
+    first = ctypes.c_int64(7)
+    assert L.kx_last_point_status(None, None, ctypes.byref(first)) == 4            # KX_ERR_ARG
+    _, path = toys.toy("st", [toys.recomb("elementary")], str(tmp_path))
+    st, h = _load(path, compile_only=1, cache_dir=str(tmp_path / "c").encode())
+    assert st == 0
+    try:
+        assert L.kx_last_point_status(h, None, None) == 4                             # null output
+        assert L.kx_last_point_status(h, None, ctypes.byref(first)) == 10             # KX_ERR_UNSUPPORTED
+        assert first.value == -1
+        one = (ctypes.c_double * 8)()
+        args = [h, one, one, one, ctypes.c_int64(1), one, ctypes.c_int64(1), None]
+        assert L.kx_production_rates_noalloc(*args) == 10                             # compile-only handle
+        args[6] = ctypes.c_int64(-1)
+        assert L.kx_production_rates_noalloc(*args) == 4                              # negative count
+        args[6] = ctypes.c_int64(0)
+        assert L.kx_production_rates_noalloc(*args) == 0                              # n = 0: no-op
+    finally:
+        L.kx_free_mechanism(h)
