@@ -32,28 +32,43 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def configure(L: ctypes.CDLL) -> ctypes.CDLL:
+    """Declare the argument types of the oracle's C entry points on a loaded library."""
+    L.ora_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.ora_free.argtypes = [ctypes.c_void_p]
+    L.ora_free.restype = None
+    L.ora_sizes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.ora_species_thermo.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_D] * 5
+    L.ora_production_rates.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
+    L.ora_reaction_detail.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D]
+    L.ora_rates_of_progress.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long,
+                                        ctypes.c_int]
+    L.ora_reaction_gross.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
+    L.ora_gross_scale.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
+    L.ora_thermo.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, _D, ctypes.c_long, ctypes.c_int]
+    L.ora_species_transport.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D, _D]
+    L.ora_transport.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, _D, _D, ctypes.c_long,
+                                ctypes.c_int]
+    L.ora_wilke_phi.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
+    L.ora_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D]
+    return L
+
+
+def build_variant(source: str, out_so: str) -> ctypes.CDLL:
+    """Compile another oracle source text (the tests' planted mistakes, on the
+    CPU) with the oracle's own flags and load it."""
+    src = out_so + ".cpp"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC", "-pthread",
+                           "-o", out_so, src])
+    return configure(ctypes.CDLL(out_so))
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.ora_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
-        L.ora_free.argtypes = [ctypes.c_void_p]
-        L.ora_free.restype = None
-        L.ora_sizes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-        L.ora_species_thermo.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_D] * 5
-        L.ora_production_rates.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
-        L.ora_reaction_detail.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D]
-        L.ora_rates_of_progress.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long,
-                                            ctypes.c_int]
-        L.ora_reaction_gross.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
-        L.ora_gross_scale.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, ctypes.c_long, ctypes.c_int]
-        L.ora_thermo.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, _D, ctypes.c_long, ctypes.c_int]
-        L.ora_species_transport.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D, _D]
-        L.ora_transport.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_long, _D, _D, _D, ctypes.c_long,
-                                    ctypes.c_int]
-        L.ora_wilke_phi.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
-        L.ora_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D]
+        _lib = configure(ctypes.CDLL(build()))
     return _lib
 
 
@@ -69,8 +84,8 @@ class Oracle:
     """One mechanism loaded into the oracle.  Arrays are SoA float64:
     T[n], p[n], Y[ns, n] (species-major)."""
 
-    def __init__(self, path: str, nthreads: int = 1):
-        self.L = lib()
+    def __init__(self, path: str, nthreads: int = 1, library: Optional[ctypes.CDLL] = None):
+        self.L = library if library is not None else lib()
         h = ctypes.c_void_p()
         if self.L.ora_load(path.encode(), ctypes.byref(h)) != 0:
             raise RuntimeError(f"oracle cannot load {path}")

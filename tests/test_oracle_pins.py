@@ -294,6 +294,70 @@ def test_troe_center_and_limits(tmp_path):
         assert det["F"][0] == pytest.approx(F, rel=1e-11)
 
 
+def _sri_pin_errors(o, T, sri):
+    """Largest relative deviation of the oracle's SRI blending factor F from
+    the values the SRI form (App. A.2.2) fixes exactly.  With
+    X = 1/(1 + (log10 Pr)^2): at log10 Pr = 0, X = 1 and
+    F = d T^e (a e^(-b/T) + e^(-T/c)); at log10 Pr = +-1, X = 1/2 (the square
+    root of that base); at log10 Pr = +-3, X = 1/10; and as Pr grows without
+    bound X -> 0 and F -> d T^e (at log10 Pr = 100, X = 1/10001).
+    k_inf = 1e9 and k_0 = 1e12 with unit efficiencies give
+    Pr = 1e3 p/(R T), so each log10 Pr is set through p."""
+    a, b, c, d, e = sri
+    base = a * math.exp(-b / T) + math.exp(-T / c)
+    Y = np.array([0.25, 0.25, 0.25, 0.25])
+    worst = 0.0
+    for lp in (0.0, 1.0, -1.0, 3.0, -3.0, 100.0):
+        X = 1.0 / (1.0 + lp * lp)
+        want = d * T ** e * base ** X
+        det = o.reaction_detail(T, 10.0 ** lp / 1e3 * R_U * T, Y)
+        assert math.log10(det["Pr"][0]) == pytest.approx(lp, abs=1e-12)
+        dev = abs(det["F"][0] / want - 1.0)
+        worst = max(worst, dev if math.isfinite(dev) else math.inf)
+    return worst
+
+
+SRI_CASES = [(1000.0, (0.5, 200.0, 1000.0, 1.2, 0.1)),   # base 0.78
+             (1500.0, (3.0, 0.0, 800.0, 0.9, -0.4)),     # a = 3, b = 0: base = 3 + e^(-T/c)
+             (700.0, (1.0, 0.0, 300.0, 1.0, 0.0))]      # a = 1, b = 0, d = 1, e = 0: F = (1 + e^(-T/c))^X
+
+
+def _sri_toy(tmp_path, sri):
+    r = toys.recomb("falloff", rate=(1e9, 0.0, 0.0), rate_low=(1e12, 0.0, 0.0), sri=sri)
+    return toys.toy("sri", [r], str(tmp_path))[1]
+
+
+@pytest.mark.parametrize("T,sri", SRI_CASES)
+def test_sri_blend_exact_points(tmp_path, T, sri):
+    """The SRI factor at the points where X = 1, 1/2, 1/10 and X -> 0."""
+    o = oracle.Oracle(_sri_toy(tmp_path, sri))
+    assert _sri_pin_errors(o, T, sri) <= 1e-14
+
+
+SRI_MUTANTS = [
+    ("log10(Pr)", "log(Pr)"),   # natural log where the SRI form takes log10 of Pr
+    ("d * pow(T, e) * pow(a * exp(-b / T) + exp(-T / c), X)",   # the exponent X over d T^e as well
+     "pow(d * pow(T, e) * (a * exp(-b / T) + exp(-T / c)), X)"),
+    ("1.0 / (1.0 + lp * lp)", "1.0 / (1.0 + lp)"),   # X without the square
+]
+
+
+@pytest.mark.parametrize("old,new", SRI_MUTANTS)
+def test_sri_pins_catch_planted_mistakes(tmp_path, old, new):
+    """Planted mistakes in the oracle's SRI factor, compiled on the CPU from a
+    copy of its source: the exact points above must reject each."""
+    src = open(oracle._SRC).read()
+    at = src.index("R sri_F(")
+    end = src.index("\n}\n", at)
+    body = src[at:end]
+    assert body.count(old) == 1
+    mutant = src[:at] + body.replace(old, new) + src[end:]
+    L = oracle.build_variant(mutant, str(tmp_path / "liboracle_mutant.so"))
+    T, sri = SRI_CASES[0]
+    o = oracle.Oracle(_sri_toy(tmp_path, sri), library=L)
+    assert _sri_pin_errors(o, T, sri) > 1e-3
+
+
 def test_chemically_activated_and_plog_limits(tmp_path):
     """Chemically activated: k_f -> k_0 as Pr -> 0 (Lindemann F = 1).
     PLOG: at a tabulated pressure k_f is that pressure's Arrhenius rate; at
