@@ -6,9 +6,15 @@
  * (arXiv 2411.02640, Appendix A): net species production rates
  * (Sec. A.2), mixture heat capacity and enthalpy (Sec. A.1) and
  * mixture-averaged transport properties (Sec. A.3.5).  kx_load_mechanism
- * reads a mechanism file, emits CUDA C++ specialised to that mechanism
- * (constants as immediates, reaction loops fully unrolled) and compiles it
- * for sm_103a with NVRTC; the other calls launch the compiled kernels.
+ * reads a mechanism file, emits CUDA C++ specialised to that mechanism and
+ * compiles it for sm_103a with NVRTC; the other calls launch the compiled
+ * kernels.  By default the production-rate kernels group the reactions
+ * into classes of one code shape (kind, reversibility, blend, entry
+ * counts) and run one loop per class over per-class constant tables, and
+ * the transport kernels loop over per-pair coefficient tables; the
+ * alternative native float64 and mixed kernels (kx_options.rates_arith = 1,
+ * rates_mode = 1) are fully unrolled with the mechanism's constants as
+ * immediates.
  *
  * Conventions shared by every call below:
  *   - Every array argument is a DEVICE pointer to float64 data that the
@@ -59,11 +65,23 @@ typedef enum {
 } kx_status;
 
 typedef enum {
-  KX_FP64 = 0,   /* every operation in float64 */
-  KX_MIXED = 1   /* float32 bulk arithmetic; float64 for the Gibbs sums of
-                    ln K_c, the forward-minus-reverse difference and the
-                    production-rate accumulation (production rates); float32
-                    mixing rules (transport) */
+  KX_FP64 = 0,   /* float64 ACCURACY: results within 1e-10 of the per-point
+                    scale max_k |W_k wdot_k| (production rates) and 1e-12
+                    relative (thermo, transport) of a float64 evaluation.
+                    By default the arithmetic is double-float -- each value a
+                    pair of float32s, about 2^-47 relative per operation, with
+                    float32's exponent range, run on the float32 pipe -- and
+                    the production rates are formed in log space and
+                    accumulated in float pairs under a per-state power-of-two
+                    scale; kx_options.rates_arith = 1 selects native float64
+                    production rates and rates of progress, tr_mode = 1
+                    native float64 transport.  kx_thermo is always
+                    double-float. */
+  KX_MIXED = 1   /* float32 bulk arithmetic (ln k_f, third body, falloff
+                    blend, ln R_f); float pairs for the Gibbs sums of ln K_c;
+                    the forward-minus-reverse difference resolved from that
+                    ratio and the production-rate accumulation in float64
+                    (production rates); float32 mixing rules (transport) */
 } kx_precision;
 
 /* Load options; a zero-initialised struct (or NULL) selects the defaults. */
@@ -91,7 +109,7 @@ typedef struct {
   int lazy;           /* 0: compile the production-rate, thermo and transport kernels at load
                          (in parallel), the rates-of-progress and adjoint kernels on first
                          use; 1: every kernel on first use */
-  int verbose;        /* 1: print compile times and register/spill counts to stderr */
+  int verbose;        /* 1: print compile times, registers and local memory per thread to stderr */
   int libmath;        /* 1: CUDA's exp/log in the float64 kernels instead of the library's own */
   int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);
                          launch calls on such a handle return KX_ERR_UNSUPPORTED */
@@ -171,8 +189,9 @@ kx_status kx_last_point_status(kx_handle h, void* stream, int64_t* first_bad_poi
  * held until the process exits). */
 #define KX_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
 
-/* Net production rates wdot[N_s][ld] with the float-pair (float64-accurate)
- * arithmetic of kx_production_rates, for callers that cannot have device
+/* Net production rates wdot[N_s][ld] in the float-pair (double-float,
+ * float64-accurate) arithmetic of kx_production_rates' default kernel,
+ * whatever kx_options.rates_arith says, for callers that cannot have device
  * memory allocated while they run: a CFD code that hands all free device
  * memory to its own pool at start-up (a later allocation fails or fragments
  * it), a time step that must not stall on the device-wide synchronisation
@@ -197,15 +216,22 @@ kx_status kx_last_point_status(kx_handle h, void* stream, int64_t* first_bad_poi
  *     reading it).  Calls that overlap on the GPU (on streams with no order
  *     between them) race on the array and give wrong results: order them.
  * Pointers, layout, NaN rules and errors otherwise as kx_production_rates;
- * the results are the same.  The paper has no counterpart: this is runtime
+ * the results match its KX_FP64 results within the same 1e-10 bound of the
+ * per-point scale (bit for bit when both run the default float-pair
+ * kernel, not when the handle selects native float64 rates).  The paper has no counterpart: this is runtime
  * plumbing around its method. */
 kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                       double* wdot, int64_t n, void* stream);
 
 /* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
  * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
- * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp".  Any output pointer may be
- * NULL.  fp64_ops/fp32_ops/exps: the emitter's per-point operation counts. */
+ * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp" and
+ * "wdot_fp64_noalloc" (the kernel of kx_production_rates_noalloc).  Any
+ * output pointer may be NULL.  registers and local_bytes: per thread, from
+ * the compiler's report (local_bytes is the stack frame: local arrays and
+ * register spills, the local memory the driver backs for every resident
+ * thread).  fp64_ops/fp32_ops/exps: the emitter's per-point operation
+ * counts. */
 kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes,
                          double* compile_seconds, double* fp64_ops, double* fp32_ops, double* exps);
 

@@ -129,15 +129,17 @@ void write_file_atomic(const std::string& p, const std::vector<char>& data) {
   std::rename(tmp.c_str(), p.c_str());
 }
 
-void parse_ptxas_info(const std::string& log, int& regs, int& spill) {
-  // "ptxas info    : Used 255 registers, ..."  and "N bytes spill stores"
+// "ptxas info    : Used 255 registers, ...", "N bytes stack frame, M bytes spill stores": the
+// registers and the per-thread local memory (stack frame: local arrays and spills) of the kernel
+void parse_ptxas_info(const std::string& log, int& regs, int& local) {
   size_t p = log.rfind("Used ");
   if (p != std::string::npos) regs = std::atoi(log.c_str() + p + 5);
-  size_t q = log.find("bytes spill stores");
+  size_t q = log.find("bytes stack frame");
   if (q != std::string::npos) {
-    size_t b = log.rfind(',', q);
-    size_t s = (b == std::string::npos) ? log.rfind('\n', q) : b;
-    spill = std::atoi(log.c_str() + (s == std::string::npos ? 0 : s + 1));
+    size_t s = q;
+    while (s > 0 && log[s - 1] == ' ') --s;
+    while (s > 0 && log[s - 1] >= '0' && log[s - 1] <= '9') --s;
+    local = std::atoi(log.c_str() + s);
   }
 }
 
@@ -195,7 +197,7 @@ kx_status compile_kernel(kx_mech* h, Kernel& k) {
   }
   k.compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (h->opt.verbose)
-    std::fprintf(stderr, "kx: %s: %.1f s, %d registers, %d spill bytes, %zu source bytes\n", k.name.c_str(),
+    std::fprintf(stderr, "kx: %s: %.1f s, %d registers, %d bytes of local memory per thread, %zu source bytes\n", k.name.c_str(),
                  k.compile_seconds, k.registers, k.local_bytes, k.source.size());
   return KX_OK;
 }
@@ -206,8 +208,10 @@ kx_status load_kernel(Kernel& k) {
   e = cudaLibraryGetKernel(&k.fn, k.lib, k.entry.c_str());
   if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel");
   int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
   if (k.smem > 0) {
     e = cudaKernelSetAttributeForDevice(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaKernelSetAttributeForDevice");
@@ -392,7 +396,8 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
       }
       // the no-alloc call's scratch address, looked up here with this device current
       int dev = 0;
-      cudaGetDevice(&dev);
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
       NoAllocDevice* nd = nullptr;
       s = noalloc_device(dev, &nd);
       if (s != KX_OK) return s;
@@ -446,7 +451,8 @@ kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double
   s = ensure_ready(h, *k);
   if (s != KX_OK) return s;
   int dev = 0;
-  cudaGetDevice(&dev);
+  cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return cuda_fail(ge, "cudaGetDevice");
   NoAllocDevice* nd = nullptr;
   s = noalloc_device(dev, &nd);
   if (s != KX_OK) return s;
@@ -661,7 +667,8 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   HostPipe* hp = nullptr;
   {
     int dev = 0;
-    cudaGetDevice(&dev);
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return cuda_fail(ge, "cudaGetDevice");
     std::lock_guard<std::mutex> lock(h->pipe_mu);
     for (size_t j = 0; j < h->free_pipes.size(); ++j)
       if (h->free_pipes[j]->device == dev) {

@@ -1,30 +1,43 @@
-// CUDA source emitter: turns one mechanism into straight-line, fully
-// unrolled per-point kernels for sm_103a.
+// CUDA source emitter: turns one mechanism into per-point kernels for
+// sm_103a, specialised to that mechanism.
 //
-// Every constant of the mechanism (Arrhenius triples, stoichiometry,
-// efficiencies, Troe/SRI/PLOG parameters, NASA-7 and transport-fit
-// coefficients) is folded into the generated source, so a kernel is one
-// long dependence-light instruction stream per grid point (thread per
-// point, the paper's per-thread model, Sec. 2.4).  On GB300 the float64
-// pipe is the scarce unit (about 2 DFMA per clock per SM, against 128 FFMA),
-// so the emitter's job is to spend as few float64 operations as it can:
+// On GB300 the float64 pipe is the scarce unit (about 2 DFMA per clock per
+// SM, against 128 float32 lanes), so float64 ACCURACY is produced off the
+// float64 pipe wherever the error bars allow:
 //
-//  * one ln T and 1/T per point, shared by every Arrhenius term;
-//    k_f = exp(ln A + beta ln T - E/T) with the special cases of Eq. (k_f)
-//    (constant, integer power) and one shared exponential for reactions
-//    with equal (beta, E), emitted next to each other;
-//  * reverse rates in log space, k_r = exp(ln k_f - ln K_c), with
-//    ln K_c = -sum nu G/RT + (sum nu) ln(p_atm/(R T)) (Eq. K_p), or, as an
-//    option, the paper's per-species exp(-G/RT) products with one division;
-//  * float64 exp/log of our own (table-driven, Tang's method) whose
-//    polynomial tail runs on the float32 pipe;
-//  * the Wilke sum refactored into three products with a constant matrix,
-//    the Mathur and diffusion sums accumulated pairwise (symmetric D_kj).
+//  * Production rates, default (emit_rates_class_df): double-float (float32
+//    pair) arithmetic in log space.  Reactions are grouped into classes of
+//    one code shape (kind, reversibility, blend, reactant and product entry
+//    counts); each class is one loop over per-class constant tables
+//    (Arrhenius triples, packed species/coefficient entries, efficiencies,
+//    blend parameters) with a straight-line body.  Per state: one ln T and
+//    1/T, ln |C_k| and mu_k = G_k/RT + ln |C_k| (Eq. (Ck)); per reaction
+//    ln k_f (Eq. (k_f)), the falloff blend, ln |R_f| and the log ratio
+//    ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T)) (Eq. (K_p)); the net
+//    rate from the larger rate and that ratio; wdot accumulated in float
+//    pairs under a per-state power-of-two scale.  The tables make the
+//    compile time independent of the mechanism's size.
+//  * Production rates, native float64 (rates_arith = 1, emit_rates64): one
+//    thread per point, fully unrolled, constants as immediates (the paper's
+//    per-thread model, Sec. 2.4): one ln T and 1/T shared by every
+//    Arrhenius term, the special cases of Eq. (k_f) and one shared
+//    exponential for reactions with equal (beta, E) emitted next to each
+//    other; k_r = exp(ln k_f - ln K_c), or the paper's per-species
+//    exp(-G/RT) products with one division (kc_mode = 1); float64 exp/log
+//    of our own (table-driven, Tang's method).  Table-driven above 64
+//    species or 400 reactions.
+//  * Transport (emit_transport): loops over per-species and per-pair
+//    coefficient tables, double-float by default; Wilke's sum over
+//    unordered pairs (phi_jk from phi_kj), symmetric D_kj evaluated once per
+//    pair and added to both rows.
+//  * Thermo (emit_thermo): two float-pair Horner evaluations per species.
 //
-// The mixed-precision variant evaluates the Arrhenius, third-body and
-// falloff arithmetic in float32, keeps ln K_c (through species chemical
-// potentials G_k/RT + ln C_k), the forward/reverse cancellation and the
-// accumulation of wdot in float64 (see emit_rates_mixed).
+// The mixed-precision production rates (KX_MIXED) run the same class loops
+// with a float32 body for the Arrhenius, third-body and falloff arithmetic;
+// the Gibbs sums of ln K_c stay in float pairs (through the species
+// chemical potentials G_k/RT + ln C_k), the forward/reverse cancellation is
+// resolved from that ratio and wdot is accumulated in float64
+// (emit_class_mixed_body; the fully unrolled form is emit_rates_mixed).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

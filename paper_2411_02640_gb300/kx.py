@@ -274,7 +274,7 @@ class Mechanism:
         cs, f64, f32, ex = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().kx_kernel_info(self.h, name.encode(), ctypes.byref(r), ctypes.byref(lb), ctypes.byref(cs),
                                     ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(ex)))
-        return dict(registers=r.value, spill_bytes=lb.value, compile_seconds=cs.value, fp64_ops=f64.value,
+        return dict(registers=r.value, local_bytes=lb.value, compile_seconds=cs.value, fp64_ops=f64.value,
                     fp32_ops=f32.value, exps=ex.value)
 
 

@@ -5,7 +5,8 @@ synchronisation an allocation implies).  The call keeps the rate kernel's
 per-state species vectors in the library's static device array instead of
 local memory.
 
-Checked here: the exported symbol and the declared array size (CPU); on the
+Checked here: the exported symbol, the declared array size and the kernel's
+small per-thread local memory (CPU); on the
 GPU, two calls in a row through the C ABI, the second on other states and
 fewer of them (so the array still holds the first call's values), each
 against kx_production_rates within the production-rate tolerance, one of them
@@ -21,7 +22,8 @@ import pytest
 from paper_2411_02640_gb300 import kx, synth
 from tests.gpu_common import mechanism, oracle, torch_cuda, wdot_error
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kx.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kx.h")
 # float64-accurate production rates: max_k W_k |dwdot_k| / max_k W_k |wdot_k| per state
 TOL = 1e-10
 
@@ -32,6 +34,21 @@ def test_entry_point_exported_and_declared():
     text = open(HEADER).read()
     assert "kx_status kx_production_rates_noalloc(" in text
     assert "#define KX_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)" in text
+
+
+@pytest.mark.parametrize("name", ["h2o2_9_21", "gri_53_325"])
+def test_noalloc_kernel_local_memory_is_small(name):
+    """The no-alloc kernel's own per-thread local memory (stack frame: local
+    arrays and register spills, from the compiler's report; compiled without a
+    GPU) stays within the 1 KB per thread that a CUDA context reserves by
+    default (cudaLimitStackSize) and below the regular kernel's, so its launch
+    gives the driver no reason to grow the local-memory backing."""
+    m = kx.Mechanism(synth.mechanism_file(name, os.path.join(ROOT, ".kxcache", "mech")),
+                     cache_dir=os.path.join(ROOT, ".kxcache"), compile_only=1, lazy=1)
+    na = m.kernel_info("wdot_fp64_noalloc")["local_bytes"]
+    reg = m.kernel_info("wdot_fp64")["local_bytes"]
+    assert 0 <= na <= 1024
+    assert na <= reg
 
 
 def _states(mech, name, n, seed):
