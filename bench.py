@@ -44,22 +44,36 @@ def peaks():
         return {}
 
 
-# float64 pipe: 2 DFMA per clock per SM on GB300 (measured 5.99e11 DFMA/s at ~2.0 GHz);
-# the peak is taken at the maximum SM clock.
-FP64_DFMA_PER_CLK_SM = 2.0
 SMS = 152
+PEAKS_RECORD = os.path.join(ROOT, "profiles", "peaks_gb300.json")
+
+
+def pipe_rates():
+    """Per-clock, per-SM rates of the arithmetic pipes: measured by
+    `bench.py --peaks` (kx_probe_pipe) and committed as profiles/peaks_gb300.json;
+    the nominal unit counts (2 float64 FMA and 128 float32 lanes per clock per
+    SM) where no record exists."""
+    try:
+        with open(PEAKS_RECORD) as f:
+            rec = json.load(f)
+        return {"dfma": rec["per_clk_per_sm"]["dfma"], "ffma": rec["per_clk_per_sm"]["ffma"],
+                "source": f"measured (kx_probe_pipe, {rec.get('when', '?')}, median SM clock "
+                          f"{rec.get('sm_mhz_median', '?')} MHz)"}
+    except (OSError, KeyError, ValueError):
+        return {"dfma": 2.0, "ffma": 128.0, "source": "nominal unit counts"}
+
+
+PIPE = pipe_rates()
 
 
 def fp64_peak_gops(sm_max_mhz: float) -> float:
-    return FP64_DFMA_PER_CLK_SM * SMS * sm_max_mhz * 1e6 / 1e9
-
-
-# float32 pipe (and instruction issue): 128 lanes per clock per SM
-FP32_LANES_PER_CLK_SM = 128.0
+    """float64 pipe: measured FMA per clock per SM x SMs x the maximum SM clock."""
+    return PIPE["dfma"] * SMS * sm_max_mhz * 1e6 / 1e9
 
 
 def fp32_peak_gops(sm_max_mhz: float) -> float:
-    return FP32_LANES_PER_CLK_SM * SMS * sm_max_mhz * 1e6 / 1e9
+    """float32 pipe (and instruction issue): measured FMA lanes per clock per SM x SMs x max clock."""
+    return PIPE["ffma"] * SMS * sm_max_mhz * 1e6 / 1e9
 
 
 def kernel_roofline(mech, name, n, ms, sm_max):
@@ -75,12 +89,13 @@ def kernel_roofline(mech, name, n, ms, sm_max):
         ach = f32 * n / (ms * 1e-3) / 1e9
         return {"bound": "alu", "kernel": name, "achieved": ach, "peak": p32, "unit": "G fp32-pipe instr/s",
                 "frac": ach / p32, "per_point_instr": f32,
-                "peak_source": f"152 SMs x 128 lanes/clk x {sm_max:.0f} MHz (float32 pipe and issue; unit counts "
-                               "and max SM clock)"}
+                "peak_source": f"152 SMs x {PIPE['ffma']:.1f} float32 FMA lanes/clk x {sm_max:.0f} MHz (float32 "
+                               f"pipe and issue; per-clock rate {PIPE['source']}, max SM clock)"}
     ach = f64 * n / (ms * 1e-3) / 1e9
     return {"bound": "alu", "kernel": name, "achieved": ach, "peak": p64, "unit": "G fp64 instr/s",
             "frac": ach / p64, "per_point_instr": f64,
-            "peak_source": f"152 SMs x 2 DFMA/clk x {sm_max:.0f} MHz (float64 pipe; unit counts and max SM clock)"}
+            "peak_source": f"152 SMs x {PIPE['dfma']:.2f} DFMA/clk x {sm_max:.0f} MHz (float64 pipe; per-clock "
+                           f"rate {PIPE['source']}, max SM clock)"}
 
 
 # float64 instructions that one call of each library routine costs in the
@@ -246,6 +261,18 @@ def run_kx(args):
 
     n = args.points
     path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
+    # the handles of the extra blocks compile in background threads while the main step is timed
+    # (NVRTC is host work; each thread makes this rank's device current before loading)
+    import concurrent.futures as cf
+    extra = {}
+    pool = cf.ThreadPoolExecutor(max_workers=3)
+    if rank == 0 and not args.no_extra:
+        def load(mname, **o):
+            torch.cuda.set_device(local)
+            return kx.Mechanism(synth.mechanism_file(mname, os.path.join(CACHE, "mech")), cache_dir=CACHE, **o)
+        extra["native"] = pool.submit(load, MECH, rates_arith=1, tr_mode=1)
+        extra["c1"] = pool.submit(load, "h2o2_9_21")
+        extra["large"] = pool.submit(load, "large_160_900")
     mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg, rates_mode=args.rates_mode,
                         rates_arith=args.rates_arith, tr_layout=args.tr_layout, block=args.block,
                         diff_mode=args.diff_mode)
@@ -426,6 +453,24 @@ def run_kx(args):
             "gpu_launches": NK * args.steps,
             "clocks": clocks,
         }
+        if extra:
+            # the plain float64 GPU form of the same step: native float64 production rates
+            # (rates_arith 1, fully unrolled) and native float64 transport (tr_mode 1); thermo has
+            # only its double-float kernel
+            nat = extra["native"].result()
+            nb = step_block(nat, MECH, n, dev, stream, args.steps, args.warmup, "fp64", sm_max, Td, pd, Yd)
+            nb["dtype"] = "f64 (thermo f32x2)"
+            nb["roofline"] = kernel_roofline(nat, "wdot_fp64", n, nb["kernel_ms"]["wdot_fp64"], sm_max)
+            nb["speedup_of_float_pair_step"] = nb["ms_per_step"] / ms
+            nb["speedup_of_mixed_step"] = nb["ms_per_step"] / mms
+            line["fp64_native"] = nb
+            c1 = extra["c1"].result()
+            cb = {"workload": "h2o2_9_21: synthetic 9 species / 21 reactions (4 three-body, 2 Troe), 4096 states, "
+                              "T U[300,2500] K, p = 1 atm, Y Dirichlet(0.5); all outputs"}
+            for prec in ("fp64", "mixed"):
+                cb[prec] = step_block(c1, "h2o2_9_21", 4096, dev, stream, max(args.steps, 50), args.warmup, prec, sm_max)
+            line["c1_h2o2_9_21_4096"] = cb
+            line["large_160_900"] = large_block(extra["large"].result(), dev, stream, args.steps, args.warmup, sm_max)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         if world == 1 and not args.no_serve:
@@ -437,6 +482,7 @@ def run_kx(args):
                                "workload": "Poisson arrivals, 1e3-2e6 states per request, mechanisms 9/21, 53/325, "
                                            "160/900; 70% mixed, 20% with transport; host (pinned) in and out"}
         print(json.dumps(line), flush=True)
+    pool.shutdown(wait=True)
     if world > 1:
         dist.destroy_process_group()
 
@@ -601,6 +647,155 @@ def run_alternatives(args):
                       "transport_fits": tr}), flush=True)
 
 
+def run_peaks(args):
+    """Measured per-clock rates of the arithmetic pipes (kx_probe_pipe): float64
+    FMA, float32 FMA, the special-function unit's float32 2^x, and CUDA's own
+    float64 exp, log and division per call.  Each probe is calibrated to about
+    a quarter of a second per launch, timed with CUDA events on its stream
+    (best of three after a warm-up) while nvidia-smi samples the SM clock; the
+    per-clock rate divides by the median sampled clock.  --write-peaks stores
+    the record that the roofline of the default line reads."""
+    import torch
+    from paper_2411_02640_gb300 import kx
+    torch.cuda.set_device(0)
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    blocks, threads = sms * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    with ClockSampler(0) as clk:
+        for op in kx.PROBE_OPS:
+            it = 64
+            while True:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                nops = kx.probe_pipe(op, it, blocks, threads, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                if ms > 20.0 or it > (1 << 30):
+                    break
+                it *= 4
+            it = max(1, int(it * 250.0 / ms))
+            kx.probe_pipe(op, it, blocks, threads, sink, stream)   # warm-up at the final size
+            best = None
+            for _ in range(3):
+                e0.record(stream)
+                nops = kx.probe_pipe(op, it, blocks, threads, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            res[op] = {"ops_per_s": nops / (best * 1e-3), "ms": best, "iters": it}
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or 2070.0
+    per_clk = {op: r["ops_per_s"] / (mhz * 1e6 * sms) for op, r in res.items()}
+    rec = {"metric": "arithmetic pipe rates", "gpu": props.name, "sms": sms, "launch": f"{blocks} x {threads}",
+           "sm_mhz_median": mhz, "clocks": clocks, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "ops_per_s": {op: r["ops_per_s"] for op, r in res.items()}, "per_clk_per_sm": per_clk,
+           "ms": {op: r["ms"] for op, r in res.items()},
+           "float64_cost_in_dfma": {op: per_clk["dfma"] / per_clk[op] for op in ("exp64", "log64", "div64")},
+           "note": "eight independent chains per thread; exp64/log64/div64 are per call of CUDA's float64 "
+                   "routines (log and division chains include one add each)"}
+    if args.write_peaks:
+        with open(PEAKS_RECORD, "w") as f:
+            json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
+
+
+def time_calls(fn, K, W, stream):
+    """Mean milliseconds of fn() over K calls after W warm-ups, CUDA events on `stream`."""
+    import torch
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / K
+
+
+def step_block(mech, name, n, dev, stream, K, W, prec, sm_max, T=None, p=None, Y=None):
+    """Mpoints/s of the whole step (production rates, thermo, viscosity and
+    conductivity, diffusion) of one mechanism at n states, with per-kernel
+    times and the roofline of the dominant kernel."""
+    import torch
+    from paper_2411_02640_gb300 import synth
+    ns = mech.n_species
+    if T is None:
+        T, p, Y = (torch.from_numpy(a).to(dev) for a in synth.make_states(ns, synth.STATE_SPECS[name], 0, n))
+    w = torch.empty((ns, n), dtype=torch.float64, device=dev)
+    cp, hm, mu, lam = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4))
+    D = torch.empty((ns, n), dtype=torch.float64, device=dev)
+    calls = [lambda: mech.production_rates(T, p, Y, out=w, precision=prec),
+             lambda: mech.thermo(T, p, Y, out=(cp, hm)),
+             lambda: mech.viscosity_conductivity(T, p, Y, out=(mu, lam), precision=prec),
+             lambda: mech.diffusion(T, p, Y, out=D, precision=prec)]
+    kms = [time_calls(c, K, W, stream) for c in calls]
+    total = time_calls(lambda: [c() for c in calls], K, W, stream)
+    knames = ("wdot_" + prec, "thermo", "visc_" + prec, "diff_" + prec)
+    dom = int(np.argmax(kms))
+    return {"value": n / (total * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": total, "points": n,
+            "kernel_ms": dict(zip(knames, kms)),
+            "grxn_s": n / (total * 1e-3) * mech.n_reactions / 1e9, "gdof_s": n / (total * 1e-3) * (ns + 2) / 1e9,
+            "roofline": kernel_roofline(mech, knames[dom], n, kms[dom], sm_max)}
+
+
+def run_sweep(args):
+    """Point-count sweep (2^10 .. 2^22 states) of the whole step on the 9/21 and
+    53/325 mechanisms, float64-accurate and mixed: Mpoints/s, GRXN/s and GDOF/s."""
+    import torch
+    from paper_2411_02640_gb300 import kx, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sm_max = float(peaks().get("sm_max_mhz", 2070.0))
+    out = {"metric": "point-count sweep", "rows": []}
+    for name in ("h2o2_9_21", MECH):
+        mech = kx.Mechanism(synth.mechanism_file(name, os.path.join(CACHE, "mech")), cache_dir=CACHE)
+        big = synth.make_states_torch(mech.n_species, synth.STATE_SPECS[name], 1 << 22, seed=synth.STATE_SPECS[name].seed)
+        for lg in range(10, 23, 2):
+            n = 1 << lg
+            T, p, Y = big[0][:n], big[1][:n], big[2][:, :n].contiguous()
+            K = max(3, min(200, int(2e6 / n)))
+            for prec in ("fp64", "mixed"):
+                b = step_block(mech, name, n, dev, stream, K, 3, prec, sm_max, T, p, Y)
+                out["rows"].append({"mechanism": name, "points": n, "precision": prec, "mpoints_s": b["value"],
+                                    "grxn_s": b["grxn_s"], "gdof_s": b["gdof_s"], "ms_per_step": b["ms_per_step"],
+                                    "kernel_ms": b["kernel_ms"]})
+        del big
+    print(json.dumps(out), flush=True)
+
+
+def large_block(mech, dev, stream, K, W, sm_max, n=1 << 22, name="large_160_900"):
+    """Production rates of the 160/900 mechanism at 2^22 states (states drawn on
+    the device with torch's seeded generator): float64-accurate and mixed
+    Mpoints/s, the kernels' rooflines and the mixed path's error against the
+    float64-accurate path over every state."""
+    import torch
+    from paper_2411_02640_gb300 import synth
+    spec = synth.STATE_SPECS[name]
+    T, p, Y = synth.make_states_torch(mech.n_species, spec, n, seed=spec.seed)
+    w64 = torch.empty((mech.n_species, n), dtype=torch.float64, device=dev)
+    w32 = torch.empty_like(w64)
+    out = {"workload": f"{name}: synthetic 160 species / 900 reactions (72 three-body, 54 Troe), {n} states "
+                       "drawn on the device, T U[500,2800] K, p log-U[1,60] atm, Y Dirichlet(0.2)", "points": n}
+    for prec, w in (("fp64", w64), ("mixed", w32)):
+        ms = time_calls(lambda: mech.production_rates(T, p, Y, out=w, precision=prec), K, W, stream)
+        out[prec] = {"mpoints_s": n / (ms * 1e-3) / 1e6, "ms": ms,
+                     "grxn_s": n / (ms * 1e-3) * mech.n_reactions / 1e9,
+                     "roofline": kernel_roofline(mech, "wdot_" + prec, n, ms, sm_max)}
+    Wt = torch.tensor(mech.W, dtype=torch.float64, device=dev)[:, None]
+    e = ((Wt * (w32 - w64).abs()).amax(dim=0) / (Wt * w64.abs()).amax(dim=0)).cpu().numpy()
+    out["mixed"]["error_vs_fp64_gpu"] = {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)),
+                                         "measure": "per state max_k W_k |dwdot_k| / max_k W_k |wdot_k|"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,11 +817,20 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sample in the default line")
     ap.add_argument("--alternatives", action="store_true",
                     help="time the production-rate kernel in each arithmetic / equilibrium form only")
+    ap.add_argument("--peaks", action="store_true", help="measure the arithmetic pipes' per-clock rates only")
+    ap.add_argument("--write-peaks", action="store_true", help="with --peaks: store the record the roofline reads")
+    ap.add_argument("--sweep", action="store_true", help="point-count sweep of the step on 9/21 and 53/325 only")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the native float64, 9/21 (4096 states) and 160/900 blocks of the default line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.alternatives:
         run_alternatives(args)
+    elif args.peaks:
+        run_peaks(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.serve:
         print(json.dumps({"metric": "serving", "serving": run_serve_suite(args, sweep=True)}), flush=True)
     else:

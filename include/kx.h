@@ -291,6 +291,19 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
 kx_status kx_copy_rows_async(void* dst, int64_t dst_ld, const void* src, int64_t src_ld, int64_t rows, int64_t n,
                              void* stream);
 
+/* Arithmetic-pipe probe for the roofline denominators (the paper has no
+ * counterpart; it measures the machine, not the method): launches `blocks`
+ * blocks of `threads` threads (a multiple of 32, at most 256) that each run
+ * eight independent chains of `iters` operations of kind `op`: 0 float64
+ * FMA, 1 float32 FMA, 2 float32 base-2 exponential on the special-function
+ * unit (ex2.approx), 3 CUDA's float64 exp, 4 CUDA's float64 log (plus one
+ * add), 5 float64 division (plus one add).  `sink` is a device buffer of
+ * blocks * threads doubles that receives the chains' results; *ops (may be
+ * NULL) gets the number of operations launched (8 iters blocks threads).
+ * Asynchronous on `stream`; the caller times it with events on that stream.
+ * Returns KX_ERR_ARG for a bad argument, KX_ERR_CUDA if the launch fails. */
+kx_status kx_probe_pipe(int op, int64_t iters, int blocks, int threads, double* sink, void* stream, double* ops);
+
 const char* kx_status_string(kx_status s);
 
 /* Message of the calling thread's last failed call (empty if none). */

@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
         L.kx_kernel_op_counts.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
         L.kx_kernel_source_hash.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64)]
         L.kx_copy_rows_async.argtypes = [vp, i64, vp, i64, i64, i64, vp]
+        L.kx_probe_pipe.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_double)]
         L.kx_status_string.argtypes = [ctypes.c_int]
         L.kx_status_string.restype = ctypes.c_char_p
         L.kx_last_error.restype = ctypes.c_char_p
@@ -276,6 +277,22 @@ class Mechanism:
                                     ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(ex)))
         return dict(registers=r.value, local_bytes=lb.value, compile_seconds=cs.value, fp64_ops=f64.value,
                     fp32_ops=f32.value, exps=ex.value)
+
+
+PROBE_OPS = ("dfma", "ffma", "mufu_ex2", "exp64", "log64", "div64")
+
+
+def probe_pipe(op: str, iters: int, blocks: int, threads: int, sink, stream=None) -> float:
+    """Enqueue one arithmetic-pipe probe launch (kx_probe_pipe) on the stream;
+    returns the number of operations it performs.  sink: a CUDA float64
+    tensor of at least blocks * threads elements."""
+    assert sink.dtype.is_floating_point and sink.element_size() == 8 and sink.numel() >= blocks * threads
+    ops = ctypes.c_double()
+    st = lib().kx_probe_pipe(PROBE_OPS.index(op), iters, blocks, threads, sink.data_ptr(), _stream(stream),
+                             ctypes.byref(ops))
+    if st != 0:
+        raise KxError(st, f"kx_probe_pipe({op}) failed")
+    return ops.value
 
 
 def copy_rows(dst, src, stream=None) -> None:
