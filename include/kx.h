@@ -113,6 +113,13 @@ typedef struct {
   int libmath;        /* 1: CUDA's exp/log in the float64 kernels instead of the library's own */
   int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);
                          launch calls on such a handle return KX_ERR_UNSUPPORTED */
+  int rates_layout;   /* double-float KX_FP64 production rates: 0 (default) or 2 warp-cooperative --
+                         a warp evaluates a group of states together, the reactions of each class
+                         dealt out over its lanes as (state, reaction) pairs, the species vectors
+                         and per-reaction rates in shared memory, wdot gathered species-major;
+                         1 one thread per state with its species vectors in local memory */
+  int rates_group;    /* warp-cooperative production rates: states per warp, a power of two up to
+                         32; 0 (default) as many as the shared memory of four blocks allows */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 
@@ -244,6 +251,11 @@ kx_status kx_kernel_op_counts(kx_handle h, const char* kernel, double* counts);
 /* 64-bit FNV-1a hash of a kernel's emitted source: identifies the exact
  * kernel that a profile was taken of. */
 kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash);
+
+/* The emitted CUDA C++ source of one kernel (for inspection and tests):
+ * *len receives its length in bytes; if buf is not NULL, up to cap - 1
+ * bytes of it are copied there, followed by a terminating zero. */
+kx_status kx_kernel_source(kx_handle h, const char* kernel, char* buf, size_t cap, size_t* len);
 
 /* Outputs of kx_evaluate_host (bit mask). */
 #define KX_OUT_WDOT 1

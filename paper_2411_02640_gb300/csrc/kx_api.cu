@@ -57,6 +57,7 @@ struct Kernel {
   int registers = -1, local_bytes = -1;
   int max_blocks = 0;          // resident blocks for a persistent grid (per device 0 at load)
   int smem = 0;                // dynamic shared memory per block, bytes
+  int states_per_block = 0;    // states one block serves per pass of its grid-stride loop (0: one per thread)
   int device = -1;
   std::mutex mu;
   bool ready = false;
@@ -251,8 +252,10 @@ kx_status launch(kx_mech* h, const char* name, void** args, int64_t n, void* str
   if (h->opt.compile_only) return fail(KX_ERR_UNSUPPORTED, "handle was loaded with compile_only");
   kx_status s = ensure_ready(h, *k);
   if (s != KX_OK) return s;
-  const int64_t want = (n + k->eopt.block - 1) / k->eopt.block;
-  const int grid = (int)std::min<int64_t>(want, (int64_t)k->max_blocks * 4);
+  const int spb = k->states_per_block > 0 ? k->states_per_block : k->eopt.block;
+  const int64_t want = (n + spb - 1) / spb;
+  // warp-cooperative kernels: one resident wave, each warp looping over groups of states
+  const int grid = (int)std::min<int64_t>(want, (int64_t)k->max_blocks * (k->states_per_block > 0 ? 1 : 4));
   cudaError_t e =
       cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(k->eopt.block), args, k->smem, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
@@ -329,6 +332,9 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.rates_arith < 0 || h->opt.rates_arith > 2) return fail(KX_ERR_ARG, "rates_arith must be 0, 1 or 2");
   if (h->opt.tr_layout < 0 || h->opt.tr_layout > 3) return fail(KX_ERR_ARG, "tr_layout must be 0, 1, 2 or 3");
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
+  if (h->opt.rates_layout < 0 || h->opt.rates_layout > 2) return fail(KX_ERR_ARG, "rates_layout must be 0, 1 or 2");
+  if (h->opt.rates_group < 0 || h->opt.rates_group > 32 || (h->opt.rates_group & (h->opt.rates_group - 1)))
+    return fail(KX_ERR_ARG, "rates_group must be 0 or a power of two up to 32");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
   h->opt.cache_dir = nullptr;
   std::string err;
@@ -359,6 +365,16 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.rates_mode = h->opt.rates_mode;
     k->eopt.rates_arith = h->opt.rates_arith;
     k->eopt.scratch = std::strcmp(sp.name, "wdot_fp64_noalloc") == 0;
+    k->eopt.rates_layout = h->opt.rates_layout;
+    k->eopt.rates_group = h->opt.rates_group;
+    if (kx::wdot_is_wc(h->m, sp.kind, k->eopt)) {
+      const kx::WcShape w = kx::wdot_wc_shape(h->m, k->eopt);
+      if (w.smem_per_block > 200 * 1024)
+        return fail(KX_ERR_UNSUPPORTED, "warp-cooperative rate kernel: one block's shared memory exceeds 200 KB "
+                                        "(choose a smaller rates_group or rates_layout 1)");
+      k->smem = w.smem_per_block;
+      k->states_per_block = w.states_per_block;
+    }
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
       k->eopt.tr_layout = h->opt.tr_layout == 0 ? 3 : h->opt.tr_layout;
@@ -802,6 +818,20 @@ kx_status kx_kernel_source_hash(kx_handle h, const char* kernel, uint64_t* hash)
   kx_status s = kx_kernel_info(h, kernel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   if (s != KX_OK) return s;
   *hash = fnv1a(find_kernel(h, kernel)->source);
+  return KX_OK;
+}
+
+kx_status kx_kernel_source(kx_handle h, const char* kernel, char* buf, size_t cap, size_t* len) {
+  if (!h || !kernel || !len) return fail(KX_ERR_ARG, "null argument");
+  kx_status s = kx_kernel_info(h, kernel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (s != KX_OK) return s;
+  const std::string& src = find_kernel(h, kernel)->source;
+  *len = src.size();
+  if (buf && cap > 0) {
+    const size_t m = std::min(cap - 1, src.size());
+    std::memcpy(buf, src.data(), m);
+    buf[m] = '\0';
+  }
   return KX_OK;
 }
 

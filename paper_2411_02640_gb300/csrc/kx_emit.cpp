@@ -491,6 +491,29 @@ __device__ __forceinline__ kx_df kx_df_exp_sc(kx_df x, int S, float Sl) {
   const float sc = __int_as_float(((k >> 8) - S + 127) << 23);
   return kx_mk(__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc));
 }
+// e^x of a float pair as v 2^p: v a float pair in [1, 2) (unnormalised), p the
+// integer power of two of the reduction x = k ln2/256 + r (p = k >> 8).
+// x <= -760 gives v = 0 and p = -2000 (below every float64); x >= 720 gives
+// v = inf and p = 1100 (above every float64); nan gives 0.  |x| < 760 keeps
+// |k| < 2^19, so the 5-bit first part of ln2/256 keeps k E1 exact.
+__device__ __forceinline__ kx_df kx_df_exp_m(kx_df x, int& p) {
+  if (!(x.hi > -760.0f)) { p = -2000; return kx_mk(0.0f, 0.0f); }
+  if (!(x.hi < 720.0f)) { p = 1100; return kx_mk(KX_INF_F, 0.0f); }
+  const float tk = __fmaf_rn(x.hi, KX_256_OVER_LN2F, KX_RND_F);
+  const int k = __float_as_int(tk) - 0x4b400000;
+  const float kf = __fsub_rn(tk, KX_RND_F);
+  const float t1 = __fmaf_rn(-kf, KX_E1F, x.hi);
+  const float pp = __fmul_rn(kf, KX_E2F);
+  const float pe = __fmaf_rn(kf, KX_E2F, -pp);
+  kx_df r = kx_ts(t1, -pp);
+  r = kx_ts(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, KX_E3F))));   // x.lo may exceed r.hi: two-sum
+  const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(r.hi, 8.33333333e-3f, 4.16666667e-2f), r.hi, 0.166666667f), r.hi, 0.5f);
+  kx_df s = kx_qts(r.hi, __fmul_rn(__fmul_rn(r.hi, r.hi), q));
+  s = kx_qts(s.hi, __fadd_rn(s.lo, r.lo));
+  const float2 tj = kx_s_dexp[k & 255];
+  p = k >> 8;
+  return kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
+}
 // Element k of a per-thread vector kept in global scratch at stride s.
 template <typename V> struct kx_strided {
   V* p;
@@ -1507,11 +1530,12 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
   }
 }
 
-void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
+// Reaction classes of one code shape and their constant tables: per class the
+// packed species entries (kx_s<c>), the Arrhenius / blend records (kx_f<c>) and
+// the efficiency / PLOG index pairs (kx_e<c>); the efficiencies, PLOG tables
+// and per-species G/RT coefficients, T_mid, 1/W and ln W shared by all classes.
+std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m) {
   const int ns = m.ns;
-  // mixed precision: float32 rates, float-pair chemical potentials and Gibbs sums, float64 accumulation
-  const bool mx = opt.mixed;
-  // ---- classes and their tables
   std::vector<DfClass> cls;
   for (int i = 0; i < m.nr(); ++i) {
     const Reaction& r = m.rx[i];
@@ -1617,6 +1641,15 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   g(fmt("__device__ const long long kx_tmidb[%d] = {%s0LL};", ns + 1, tmb.c_str()));
   g(fmt("__device__ const float kx_iwf[%d] = {%s0.0f};", 2 * ns + 1, iw.c_str()));
   g(fmt("__device__ const float kx_lwf[%d] = {%s0.0f};", 2 * ns + 1, lw.c_str()));
+
+  return cls;
+}
+
+void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
+  const int ns = m.ns;
+  // mixed precision: float32 rates, float-pair chemical potentials and Gibbs sums, float64 accumulation
+  const bool mx = opt.mixed;
+  std::vector<DfClass> cls = emit_class_tables(g, m);
 
   // ---- per state: T, ln T, 1/T, C_M, sigma, and the species vectors
   bool any_plog = false;
@@ -2680,6 +2713,433 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   c.fp64 += 5 * ns + 4; c.div64 += ns + 2;
 }
 
+// ------------------------------------------------------------------ warp-cooperative rates
+// Float64-accurate production rates with G states per warp (G a power of two
+// up to 32) and the reactions of each class spread over the lanes.  Each
+// warp keeps its states' species vectors {ln |C_k|, mu_k} and one entry per
+// reaction (the signed rate as a float-pair mantissa and a power of two) in
+// its own slice of shared memory, so no per-state vector lives in local
+// memory; the work of a class is dealt out as (state, reaction) pairs,
+// lane + 32 t, so partial rounds are shared by the group's states.  Phases
+// per group of G states (warp-synchronous, no block barrier):
+//   1. per-state scalars (lane g < G): T, ln T, 1/T, C_M, ln(p_atm/RT);
+//   2. species (lane l serves state l mod G): sigma = sum Y_k/W_k reduced
+//      over the state's lanes in a fixed tree order, then ln |C_k|, G_k/RT
+//      (Eq. (Ck)) and mu_k = G_k/RT + ln |C_k| into shared memory;
+//   3. reaction classes: ln k_f (Eq. (k_f)), third body and falloff blend,
+//      ln |R_f| and ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/RT) (Eq. (K_p)),
+//      the net rate from the larger rate and that ratio, kept unscaled as
+//      m 2^e (m a float pair, e an integer);
+//   4. the state's scale 2^-S from the largest e (the largest scaled rate
+//      near 2^62), each rate scaled in place;
+//   5. production rates gathered species-major (wdot_k = sum_i nu_ki q_i,
+//      a fixed order) from per-lane chunks of a balanced entry list, partial
+//      sums of species that straddle chunks combined in chunk order;
+//   6. wdot_k 2^S written out as float64.
+struct WcLayout {
+  int G = 1, warps = 4, nw32 = 1, svs = 1;
+  int off_sv = 0, off_qm = 0, off_sci = 0, off_nm = 0, off_qe = 0, warp_bytes = 0;
+};
+
+WcLayout wc_layout_of(const Mechanism& m, int group, int block) {
+  WcLayout L;
+  L.warps = block / 32;
+  L.nw32 = (m.ns + 31) / 32;
+  // species region per state: the {ln |C|, mu} float4s, later reused for up to ns + 31 float-pair slots
+  L.svs = std::max(m.ns, (m.ns + 32) / 2 + 1);
+  const int per_state = 80 + 16 * L.svs + 8 * m.nr() + 8 + 4 * L.nw32 + 2 * m.nr();
+  if (group > 0) {
+    L.G = group;
+  } else {
+    // as many states per warp as keep four blocks of this size within ~200 KB of shared memory
+    const int budget = 200 * 1024 / (4 * L.warps) - 1536;
+    L.G = 1;
+    while (L.G < 32 && 2 * L.G * per_state <= budget) L.G *= 2;
+  }
+  const int G = L.G;
+  auto up16 = [](int b) { return (b + 15) / 16 * 16; };
+  L.off_sv = up16(80 * G);
+  L.off_qm = up16(L.off_sv + 16 * G * L.svs);
+  L.off_sci = up16(L.off_qm + 8 * G * m.nr());
+  L.off_nm = up16(L.off_sci + 8 * G);
+  L.off_qe = up16(L.off_nm + 4 * G * L.nw32);
+  L.warp_bytes = up16(L.off_qe + 2 * G * m.nr());
+  return L;
+}
+
+std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::string& entry, OpCounts& c,
+                         Out& globals) {
+  const int ns = m.ns, nr = m.nr();
+  const WcLayout L = wc_layout_of(m, opt.rates_group, opt.block);
+  const int G = L.G, NW32 = L.nw32, SVS = L.svs;
+  const int LG = __builtin_ctz(G);
+  std::vector<DfClass> cls = emit_class_tables(globals, m);
+  Out& g = globals;
+
+  // ---- gather table: species-major entries (reaction, net coefficient), cut into 32/G chunks of
+  // nearly equal length, stored entry-major ([j][chunk]) so that the lanes' loads of one step are
+  // contiguous; each entry: reaction index in bits 0-14, "last entry of its slot" in bit 15 and the
+  // upper half of the float32 coefficient in bits 16-31.  A slot is one chunk's partial sum of one
+  // species; species k sums its slots kx_wslot[k] .. + count in chunk order.
+  struct GE { int r; int k; int nu; };
+  std::vector<GE> ent;
+  int maxnu = 0;
+  for (int k = 0; k < ns; ++k)
+    for (int i = 0; i < nr; ++i) {
+      int nu = 0;
+      for (auto& s : m.rx[i].reac) if (s.first == k) nu -= s.second;
+      for (auto& s : m.rx[i].prod) if (s.first == k) nu += s.second;
+      if (nu != 0) { ent.push_back({i, k, nu}); maxnu = std::max(maxnu, std::abs(nu)); }
+    }
+  const int NCH = 32 / G, NE = (int)ent.size();
+  const int CL = std::max(1, (NE + NCH - 1) / NCH);
+  std::vector<int> tab((size_t)CL * NCH, 0);   // padding entries: reaction 0, coefficient 0
+  std::vector<int> chslot(NCH, 0), sfirst(ns, 0), scount(ns, 0);
+  int nslot = 0;
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int b = ch * NE / NCH, e = (ch + 1) * NE / NCH;
+    chslot[ch] = nslot;
+    for (int j = b; j < e; ++j) {
+      const bool last = j + 1 == e || ent[j + 1].k != ent[j].k;
+      const float fc = (float)ent[j].nu;
+      uint32_t fb;
+      std::memcpy(&fb, &fc, 4);
+      tab[(size_t)(j - b) * NCH + ch] = (int32_t)((fb & 0xffff0000u) | (last ? 0x8000u : 0u) | (uint32_t)ent[j].r);
+      if (j == b || ent[j - 1].k != ent[j].k) { if (scount[ent[j].k] == 0) sfirst[ent[j].k] = nslot; }
+      if (last) { ++scount[ent[j].k]; ++nslot; }
+    }
+  }
+  if (nr > 0x7fff) return "";
+  {
+    std::string t;
+    for (int v : tab) t += std::to_string(v) + ",";
+    g(fmt("__device__ const int kx_wtab[%d] = {%s0};", (int)tab.size() + 1, t.c_str()));
+    std::string cs, ss;
+    for (int ch = 0; ch < NCH; ++ch) cs += std::to_string(chslot[ch]) + ",";
+    for (int k = 0; k < ns; ++k) ss += fmt("{%d,%d},", sfirst[k], scount[k]);
+    g(fmt("__device__ const int kx_wchs[%d] = {%s0};", NCH + 1, cs.c_str()));
+    g(fmt("__device__ const int2 kx_wslot[%d] = {%s{0,0}};", ns + 1, ss.c_str()));
+  }
+
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  Out o;
+  o.ind = 1;
+  o(fmt("const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;"));
+  o(fmt("unsigned char* const wsm = kx_dyn + wib * %d;", L.warp_bytes));
+  o("#define KX_PF(p) kx_mk((p)[0], (p)[1])");
+  o("float4* const sc4 = (float4*)wsm;   // [G][5]: {Td, ln T}, {1/T, ln(p_atm/RT)}, {C_M, C_M/sigma}, {ln p}, {T, p bits}");
+  o(fmt("float4* const sv = (float4*)(wsm + %d);   // [G][%d]: {ln |C_k|, mu_k} float pairs; later the gather slots", L.off_sv, SVS));
+  o(fmt("float2* const qm = (float2*)(wsm + %d);   // [G][nr]: rate mantissas, then scaled rates", L.off_qm));
+  o(fmt("int2* const sci = (int2*)(wsm + %d);      // [G]: {largest rate exponent, flag: 0 ok, 1 outside the domain, 2 past n}", L.off_sci));
+  o(fmt("unsigned* const nmk = (unsigned*)(wsm + %d);   // [G][%d]: bit k set for Y_k < 0", L.off_nm, NW32));
+  o(fmt("short* const qe = (short*)(wsm + %d);     // [G][nr]: rate exponents", L.off_qe));
+  o(fmt("const long long nwarp = (long long)gridDim.x * %d;", L.warps));
+  o(fmt("for (long long i0 = ((long long)blockIdx.x * %d + wib) * %d; i0 < n; i0 += nwarp * %d) {", L.warps, G, G));
+  ++o.ind;
+  // ---- 1. per-state scalars
+  o(fmt("if (lane < %d) {", G));
+  ++o.ind;
+  o("const long long i = i0 + lane;");
+  o("double T = 1000.0, P = 101325.0;");
+  o("int flag = 2;");
+  o("if (i < n) {");
+  o("  T = T_[i]; P = P_[i]; flag = 0;");
+  o("  if (!(T > 0.0 && P > 0.0 && T < KX_INF && P < KX_INF)) { flag = 1; T = 1000.0; P = 101325.0; }");
+  o("}");
+  o("const kx_df Td = kx_d2df_i(T);");
+  o("const kx_df lnT = kx_df_log_d(T);");
+  o("const kx_df iT = kx_df_div(kx_mk(1.0f, 0.0f), Td);");
+  o(fmt("const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
+  o(fmt("const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
+  o("sc4[5 * lane + 0] = make_float4(Td.hi, Td.lo, lnT.hi, lnT.lo);");
+  o("sc4[5 * lane + 1] = make_float4(iT.hi, iT.lo, lnPRT.hi, lnPRT.lo);");
+  o("sc4[5 * lane + 2] = make_float4(cM.hi, cM.lo, 0.0f, 0.0f);");
+  if (any_plog) {
+    o("const kx_df lnP = kx_df_log_d(P);");
+    o("sc4[5 * lane + 3] = make_float4(lnP.hi, lnP.lo, 0.0f, 0.0f);");
+  }
+  o("sc4[5 * lane + 4] = make_float4(__int_as_float(__double2loint(T)), __int_as_float(__double2hiint(T)), "
+    "__int_as_float(__double2loint(P)), __int_as_float(__double2hiint(P)));");
+  o("sci[lane] = make_int2(-32768, flag);");
+  o(fmt("for (int w = 0; w < %d; ++w) nmk[%d * lane + w] = 0u;", NW32, NW32));
+  --o.ind;
+  o("}");
+  o("__syncwarp();");
+  c.fp32 += 40 + 45 + kDfDiv + 2 * kDfMul + kDfAdd;
+  // ---- 2. species: lane serves state gs = lane mod G, species lane/G + (32/G) t
+  const int NT = (ns * G + 31) / 32;
+  o(fmt("const int gs = lane & %d;", G - 1));
+  o("const long long is = i0 + gs;");
+  o("const bool inb = is < n;");
+  o(fmt("double Yv[%d];", NT));
+  o("kx_df sg = kx_mk(0.0f, 0.0f);");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o(fmt("  const int k = (lane >> %d) + %d * t;", LG, 32 / G));
+  o(fmt("  Yv[t] = (k < %d && inb) ? Y_[(long long)k * ld + is] : 0.0;", ns));
+  o(fmt("  if (k < %d) sg = kx_df_fma(kx_d2df_i(Yv[t]), KX_PF(kx_iwf + 2 * k), sg);", ns));
+  o("}");
+  o("// sigma of state gs: a butterfly over the lanes that serve it, then lane gs's sum for all");
+  for (int off = G; off < 32; off *= 2)
+    o(fmt("{ const float h = __shfl_xor_sync(0xffffffffu, sg.hi, %d), l = __shfl_xor_sync(0xffffffffu, sg.lo, %d); "
+          "sg = kx_df_add(sg, kx_mk(h, l)); }", off, off));
+  o("sg = kx_mk(__shfl_sync(0xffffffffu, sg.hi, gs), __shfl_sync(0xffffffffu, sg.lo, gs));");
+  o(fmt("const float4 s0 = sc4[5 * gs + 0], s1 = sc4[5 * gs + 1], s2 = sc4[5 * gs + 2], s4 = sc4[5 * gs + 4];"));
+  o("const kx_df Tg = kx_mk(s0.x, s0.y), lnTg = kx_mk(s0.z, s0.w), iTg = kx_mk(s1.x, s1.y);");
+  o("const long long Tb = ((long long)__float_as_int(s4.y) << 32) | (unsigned)__float_as_int(s4.x);   // T's float64 bits");
+  o("const kx_df fC = kx_df_div(kx_mk(s2.x, s2.y), sg);");
+  o("const kx_df lnfC = kx_df_log(fC);");
+  o("__syncwarp();");
+  o(fmt("if (lane < %d) {", G));
+  o("  sc4[5 * lane + 2] = make_float4(s2.x, s2.y, fC.hi, fC.lo);");
+  o("  if (!(sg.hi > 0.0f && sg.hi < KX_INF_F) && sci[lane].y == 0) sci[lane].y = 1;");
+  o("}");
+  o("bool neg = false;");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o(fmt("  const int k = (lane >> %d) + %d * t;", LG, 32 / G));
+  o(fmt("  if (k < %d) {", ns));
+  o("    const double Yk = Yv[t];");
+  o("    const long long yb = __double_as_longlong(Yk) & 0x7fffffffffffffffLL;");
+  o("    kx_df l = kx_mk(-700.0f, 0.0f);   // ln |C_k|, floored at -700 (absent species)");
+  o("    if (yb >= 0x0010000000000000LL && yb < 0x7ff0000000000000LL) {");
+  o("      l = kx_df_add(kx_df_log_d(__longlong_as_double(yb)), kx_df_sub(lnfC, KX_PF(kx_lwf + 2 * k)));");
+  o("      if (!(l.hi > -700.0f)) l = kx_mk(-700.0f, 0.0f);");
+  o("    }");
+  o(fmt("    if (Yk < 0.0) { neg = true; atomicOr(&nmk[%d * gs + (k >> 5)], 1u << (k & 31)); }", NW32));
+  o("    const float* a = kx_gcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("    kx_df gk = kx_df_fma(KX_PF(a + 8), Tg, KX_PF(a + 6));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 4));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 2));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 0));");
+  o("    gk = kx_df_fma(KX_PF(a + 10), iTg, gk);");
+  o("    gk = kx_df_fma(KX_PF(a + 12), lnTg, gk);");
+  o("    const kx_df mk_ = kx_df_add(gk, l);");
+  o(fmt("    sv[%d * gs + k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);", SVS));
+  o("  }");
+  o("}");
+  o("const bool grpneg = __any_sync(0xffffffffu, neg);");
+  o("__syncwarp();");
+  c.fp32 += ns * (12 + kDfFma) + kDfDiv + kDfLog + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
+
+  // ---- 3. reaction classes
+  static const char* xyzw[4] = {"x", "y", "z", "w"};
+  auto comp = [&](const char* base, int j) { return fmt("%s%d.%s", base, j / 4, xyzw[j % 4]); };
+  auto main_pass = [&](OpCounts& c, bool sgn) {
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+      const DfClass& d = cls[ci];
+      const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const int NF = fo ? 7 : tb ? 3 : 2;
+      const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+      const int NC = (int)d.rx.size();
+      o(fmt("#pragma unroll 1"));
+      o(fmt("for (int p = lane; p < %d; p += 32) {   // class %d: %d reactions, %d reactant and %d product entries", G * NC,
+            (int)ci, NC, d.nre, d.npr));
+      ++o.ind;
+      o(fmt("const int g = p / %d, r = p - g * %d;", NC, NC));
+      o("const float4 A0 = sc4[5 * g + 0], A1 = sc4[5 * g + 1];");
+      o("const kx_df Td = kx_mk(A0.x, A0.y), lnT = kx_mk(A0.z, A0.w), iT = kx_mk(A1.x, A1.y), lnPRT = kx_mk(A1.z, A1.w);");
+      if (tb) {
+        o("const float4 A2 = sc4[5 * g + 2];");
+        o("const kx_df cM = kx_mk(A2.x, A2.y), fC = kx_mk(A2.z, A2.w);");
+        o("const long long iy = i0 + g < n ? i0 + g : n - 1;   // states past n read a valid row; their results are dropped");
+      }
+      if (d.kind == Kind::Plog) {
+        o("const float4 A3 = sc4[5 * g + 3], A4 = sc4[5 * g + 4];");
+        o("const kx_df lnP = kx_mk(A3.x, A3.y);");
+        o("const double P = __hiloint2double(__float_as_int(A4.w), __float_as_int(A4.z));");
+      }
+      o(fmt("const int4* sp4 = (const int4*)kx_s%d + %d * r;", (int)ci, P / 4));
+      for (int q = 0; q < P / 4; ++q) o(fmt("const int4 c%d = sp4[%d];", q, q));
+      o(fmt("const float4* svg = sv + %d * g;", SVS));
+      for (int j = 0; j < E; ++j) o(fmt("const float4 v%d = svg[%s & 0xffff];", j, comp("c", j).c_str()));
+      if (sgn) {
+        o(fmt("const unsigned* nmg = nmk + %d * g;", NW32));
+        for (int j = 0; j < E; ++j) o(fmt("const int k%d = %s & 0xffff;", j, comp("c", j).c_str()));
+      }
+      o(fmt("const int ri = %s;", comp("c", E).c_str()));
+      o(fmt("const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+      o("const float4 f0 = f[0], f1 = f[1];");
+      o(d.kconst ? "kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
+                 : "kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
+      if (tb) {
+        o(fmt("const int2 e = kx_e%d[r];", (int)ci));
+        o("const float4 f2 = f[2];");
+        o("kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
+        o("if (e.y < 0) {");
+        o("  const int kc = kx_effd[e.x].k;");
+        o("  X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + iy]), KX_PF(kx_iwf + 2 * kc)), fC);");
+        o("} else {");
+        o("  kx_df t = kx_mk(0.0f, 0.0f);");
+        o("  for (int j = 0; j < e.y; ++j) {");
+        o("    const kx_effd_t q = kx_effd[e.x + j];");
+        o("    t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + iy]), KX_PF(kx_iwf + 2 * q.k)), t);");
+        o("  }");
+        o("  X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+        o("}");
+        c.fp32 += NC * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
+      }
+      if (fo) {
+        o("const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+        o("const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
+        o("kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+        o("if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+        o("kx_df lnF = kx_mk(0.0f, 0.0f);");
+        const std::string il10 = DFc(1.0 / std::log(10.0));
+        if (d.blend == Blend::Troe) {
+          o("kx_df Fc = kx_df_exp_s(kx_df_mul(kx_mk(f6.x, f6.y), iT));");
+          o("Fc = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))), Fc);");
+          o("Fc = kx_df_fma(kx_mk(f4.z, f4.w), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.z, f5.w))), Fc);");
+          o(fmt("const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+          o(fmt("const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+          o(fmt("const kx_df ff = kx_df_div(xx, kx_df_fma(%s, xx, kx_df_fma(%s, lFc, %s)));", DFc(-0.14).c_str(), DFc(-1.27).c_str(),
+                DFc(0.75).c_str()));
+          o(fmt("lnF = kx_df_div(kx_df_mul(%s, lFc), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));", DFc(std::log(10.0)).c_str()));
+          c.fp32 += NC * (3 * (kDfMul + kDfExp) + 2 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 2 * kDfDiv + kDfMul);
+        } else if (d.blend == Blend::Sri) {
+          o(fmt("const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+          o("const kx_df base = kx_df_fma(kx_mk(f4.x, f4.y), kx_df_exp_s(kx_df_mul(kx_mk(f4.z, f4.w), iT)), kx_df_exp_s(kx_df_mul(Td, kx_mk(f5.x, f5.y))));");
+          o("lnF = kx_df_add(kx_mk(f5.z, f5.w), kx_df_fma(kx_mk(f6.x, f6.y), lnT, kx_df_div(kx_df_log(base), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)))));");
+          c.fp32 += NC * (2 * (kDfMul + kDfExp) + kDfFma + kDfMul + kDfLog + 2 * kDfFma + kDfDiv + kDfAdd);
+        }
+        o("const bool small = lnPr.hi < 0.0f;");
+        o("const kx_df l1p = kx_df_log1p(kx_df_exp_n(small ? lnPr : kx_df_neg(lnPr)));");
+        if (d.kind == Kind::Falloff) o("lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
+        else o("lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
+        c.fp32 += NC * (2 * kDfFma + 2 * kDfAdd + kDfLog + kDfExp + kDfLog + 3 * kDfAdd);
+      } else if (d.kind == Kind::Plog) {
+        o(fmt("const int2 e = kx_e%d[r];", (int)ci));
+        o("const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+        o("const long long Pb = __double_as_longlong(P);");
+        o("if (Pb <= tp[0]) lk = kx_df_fma(KX_PF(t + 4), lnT, kx_df_fma(KX_PF(t + 6), iT, KX_PF(t + 2)));");
+        o("else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2))); }");
+        o("else {");
+        o("  int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+        o("  const float* u = t + 8 * j;");
+        o("  const kx_df l1 = kx_df_fma(KX_PF(u + 4), lnT, kx_df_fma(KX_PF(u + 6), iT, KX_PF(u + 2)));");
+        o("  const kx_df l2 = kx_df_fma(KX_PF(u + 12), lnT, kx_df_fma(KX_PF(u + 14), iT, KX_PF(u + 10)));");
+        o("  lk = kx_df_fma(kx_df_sub(l2, l1), kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u))), l1);");
+        o("}");
+        c.fp32 += NC * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
+      }
+      o("kx_df lf = lk;");
+      for (int j = 0; j < d.nre; ++j) o(fmt("lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
+      auto negbit = [&](int j) { return fmt("((nmg[k%d >> 5] >> (k%d & 31)) & 1)", j, j); };
+      std::string sfx = "0", srx = "0";
+      if (sgn) {
+        for (int j = 0; j < d.nre; ++j) sfx += " ^ " + negbit(j);
+        for (int j = d.nre; j < E; ++j) srx += " ^ " + negbit(j);
+      }
+      o("int sf = " + sfx + ";");
+      o("kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
+      c.fp32 += NC * ((d.kconst ? 0 : 2 * kDfFma) + d.nre * kDfAdd + kDfExp + kDfMul);
+      if (d.rev) {
+        const int dn = d.npr - d.nre;
+        o("{   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
+        std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+        o("  kx_df dl = " + first + ";");
+        for (int j = 1; j < E; ++j)
+          o(fmt("  dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+        if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+        else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+        o("  const int sr = " + srx + ";");
+        o("  const bool rev = dl.hi > 0.0f;");
+        o("  if (rev) L = kx_df_add_u(lf, dl);");
+        o("  const kx_df e = kx_df_exp_n(rev ? kx_df_neg(dl) : dl);");
+        o("  const float pm = sf == sr ? -1.0f : 1.0f;   // |R_f| -+ |R_r| = larger (1 -+ e^-|ln ratio|)");
+        o("  const kx_df s1 = kx_qts(1.0f, pm * e.hi);");
+        o("  fac = kx_mk(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
+        o("  if (sf == sr) sf ^= (int)rev;");
+        o("}");
+        c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+      }
+      o("int ex;");
+      o("kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex");
+      o("if (sf) q = kx_df_neg(q);");
+      if (d.kind == Kind::ThreeBody) { o("q = kx_df_mul_u(q, X);"); c.fp32 += NC * kDfMul; }
+      o(fmt("qm[%d * g + ri] = make_float2(q.hi, q.lo);", nr));
+      o(fmt("qe[%d * g + ri] = (short)ex;", nr));
+      --o.ind;
+      o("}");
+    }
+  };
+  o("if (grpneg) {");
+  ++o.ind;
+  main_pass(c, true);
+  --o.ind;
+  o("} else {");
+  ++o.ind;
+  {
+    OpCounts once;
+    main_pass(once, false);
+  }
+  --o.ind;
+  o("}");
+  // ---- 4. the largest exponent of each state (a warp max over its rates); rates scaled in place
+  o("__syncwarp();");
+  o(fmt("for (int g = 0; g < %d; ++g) {", G));
+  o("  int e = -32768;");
+  o(fmt("  for (int r = lane; r < %d; r += 32) e = max(e, (int)qe[%d * g + r]);", nr, nr));
+  o("  e = __reduce_max_sync(0xffffffffu, e);");
+  o("  if (lane == 0) sci[g].x = e;");
+  o("}");
+  o("__syncwarp();");
+  o("#pragma unroll 1");
+  o(fmt("for (int p = lane; p < %d; p += 32) {", G * nr));
+  o(fmt("  const int g = p / %d;", nr));
+  o("  const int d = (int)qe[p] - (sci[g].x - 62);   // S = e_max - 62; 2^d normal for d >= -126 (below: under 2^-188 of the largest)");
+  o("  const float2 v = qm[p];");
+  o("  const float sc = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f;");
+  o("  qm[p] = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));");
+  o("}");
+  o("__syncwarp();");
+  c.fp32 += nr * 4;
+  // ---- 5. gather: lane serves state gs and chunk lane / G
+  o(fmt("{   // species-major sums from chunk %s of the entry list", "lane / G"));
+  ++o.ind;
+  o(fmt("const int ch = lane >> %d;", LG));
+  o(fmt("const float2* qg = qm + %d * gs;", nr));
+  o(fmt("float2* const slot = (float2*)(sv + %d * gs);", SVS));
+  o("int sl = kx_wchs[ch];");
+  o("kx_df acc = kx_mk(0.0f, 0.0f);");
+  o("#pragma unroll 4");
+  o(fmt("for (int j = 0; j < %d; ++j) {", CL));
+  o(fmt("  const unsigned w = (unsigned)kx_wtab[%d * j + ch];", NCH));
+  o("  const float2 q = qg[w & 0x7fffu];");
+  o(fmt("  acc = kx_df_add_u(acc, %s(kx_mk(q.x, q.y), __uint_as_float(w & 0xffff0000u)));",
+        maxnu <= 2 ? "kx_df_scale2" : "kx_df_mulf"));
+  o("  if (w & 0x8000u) { slot[sl++] = make_float2(acc.hi, acc.lo); acc = kx_mk(0.0f, 0.0f); }");
+  o("}");
+  --o.ind;
+  o("}");
+  o("__syncwarp();");
+  c.fp32 += (double)NE * (kDfAdd + (maxnu <= 2 ? 2 : kDfMulf));
+  if (nslot > 2 * SVS) return "";
+  // ---- 6. output: pairs (state, species), consecutive lanes on consecutive states
+  o("#pragma unroll 1");
+  o(fmt("for (int p = lane; p < %d; p += 32) {", G * ns));
+  o(fmt("  const int g = p & %d, k = p >> %d;", G - 1, LG));
+  o("  const long long i = i0 + g;");
+  o("  const int2 st = sci[g];");
+  o("  if (st.y == 2) continue;");
+  o("  if (st.y == 1) { out_[(long long)k * ld + i] = KX_NAN; continue; }");
+  o("  const int2 sl = kx_wslot[k];");
+  o(fmt("  const float2* slot = (const float2*)(sv + %d * g);", SVS));
+  o("  kx_df w = kx_mk(0.0f, 0.0f);");
+  o("  for (int j = 0; j < sl.y; ++j) w = kx_df_add_u(w, kx_mk(slot[sl.x + j].x, slot[sl.x + j].y));");
+  o("  out_[(long long)k * ld + i] = kx_df2d_s(w, st.x - 62);");
+  o("}");
+  o(fmt("if (lane < %d && sci[lane].y == 1) atomicMin(&kx_bad_first, (unsigned long long)(i0 + lane));", G));
+  o("__syncwarp();");
+  --o.ind;
+  o("}");
+  c.fp64 += ns;
+  c.fp32 += ns * kDfAdd;
+  return o.o.str();
+}
+
 }  // namespace
 
 // Shared memory per thread of the transport kernels, in bytes.
@@ -2691,6 +3151,50 @@ int transport_smem_per_thread(const Mechanism& m, bool mixed, int part, int layo
 }
 
 // ------------------------------------------------------------------ kernels
+bool wdot_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt) {
+  (void)m;
+  return kind == KernelKind::Wdot && !opt.mixed && !opt.scratch && opt.rates_arith != 1 && opt.rates_layout != 1;
+}
+
+WcShape wdot_wc_shape(const Mechanism& m, const EmitOptions& opt) {
+  const WcLayout L = wc_layout_of(m, opt.rates_group, opt.block);
+  WcShape w;
+  w.states_per_warp = L.G;
+  w.states_per_block = L.G * L.warps;
+  w.smem_per_block = L.warp_bytes * L.warps;
+  return w;
+}
+
+// The warp-cooperative production-rate kernel (emit_wdot_wc) with its own
+// grid-stride loop over groups of states.
+std::string emit_wc_kernel(const Mechanism& m, const EmitOptions& opt, const std::string& entry, OpCounts* counts) {
+  OpCounts c;
+  Out globals;
+  globals.ind = 0;
+  const std::string body = emit_wdot_wc(m, opt, entry, c, globals);
+  if (body.empty()) return "";
+  std::ostringstream s;
+  s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
+  s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
+  s << "#define KX_T64 0\n#define KX_TDF 1\n#define KX_TDFR 1\n";
+  s << kTables << "\n" << kDevicePrelude << "\n";
+  s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
+  s << globals.o.str();
+  s << "__device__ unsigned long long kx_bad_first = 0xffffffffffffffffull;\n";
+  // 128 registers by default (four blocks of 128 threads per SM), fewer where the shared memory
+  // of more blocks fits
+  const int rreg = opt.maxrreg > 0 ? opt.maxrreg : 128;
+  const int min_blocks = std::max(1, 65536 / (rreg * opt.block));
+  s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ", " << min_blocks << ") " << entry
+    << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
+    << "double* __restrict__ out_, long long n)\n{\n";
+  s << "  kx_load_tables();\n";
+  s << body;
+  s << "}\n";
+  if (counts) *counts = c;
+  return s.str();
+}
+
 std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
                         OpCounts* counts) {
   OpCounts c;
@@ -2702,6 +3206,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
     case KernelKind::Wdot:
     case KernelKind::Rop: {
       const bool rop = kind == KernelKind::Rop;
+      if (wdot_is_wc(m, kind, opt)) return emit_wc_kernel(m, opt, entry, counts);
       outs = "double* __restrict__ out_";
       if (opt.scratch && !rop) outs += ", unsigned char* __restrict__ kx_scr, long long nthr";
       nan_fill = fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = KX_NAN;", rop ? m.nr() : m.ns);

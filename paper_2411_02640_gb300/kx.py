@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("diff_mode", ctypes.c_int), ("kc_mode", ctypes.c_int), ("tr_mode", ctypes.c_int), ("rates_mode", ctypes.c_int),
                 ("rates_arith", ctypes.c_int), ("tr_layout", ctypes.c_int), ("maxrreg", ctypes.c_int),
                 ("block", ctypes.c_int), ("lazy", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("libmath", ctypes.c_int), ("compile_only", ctypes.c_int), ("cache_dir", ctypes.c_char_p)]
+                ("libmath", ctypes.c_int), ("compile_only", ctypes.c_int), ("rates_layout", ctypes.c_int),
+                ("rates_group", ctypes.c_int), ("cache_dir", ctypes.c_char_p)]
 
 
 def library_path() -> str:
@@ -72,6 +73,7 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.kx_kernel_op_counts.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
         L.kx_kernel_source_hash.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64)]
+        L.kx_kernel_source.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
         L.kx_copy_rows_async.argtypes = [vp, i64, vp, i64, i64, i64, vp]
         L.kx_probe_pipe.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_double)]
         L.kx_status_string.argtypes = [ctypes.c_int]
@@ -263,6 +265,14 @@ class Mechanism:
         h = ctypes.c_uint64()
         _check(lib().kx_kernel_source_hash(self.h, name.encode(), ctypes.byref(h)))
         return f"{h.value:016x}"
+
+    def kernel_source(self, name: str) -> str:
+        """The emitted CUDA C++ source of one kernel."""
+        n = ctypes.c_size_t()
+        _check(lib().kx_kernel_source(self.h, name.encode(), None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(lib().kx_kernel_source(self.h, name.encode(), buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
 
     def op_counts(self, name: str) -> dict:
         """Per-point operation counts the emitter tallied for one kernel."""
