@@ -13,9 +13,10 @@ from tests.gpu_common import CACHE, to_device, torch_cuda, wdot_error
 pytestmark = pytest.mark.gpu
 
 
-def _mechanism(tmp_path_factory):
-    d = str(tmp_path_factory.mktemp("kinds"))
-    rx = [toys.recomb("elementary"), toys.recomb("three_body", efficiencies={3: 2.0, 0: 0.7}),
+def reactions():
+    """One reaction of every kind the kernels support (also used by the CPU test of the
+    warp-cooperative gather tables)."""
+    return [toys.recomb("elementary"), toys.recomb("three_body", efficiencies={3: 2.0, 0: 0.7}),
           toys.recomb("three_body", collider=3, rate=(3e9, -0.5, 200.0)),
           toys.recomb("falloff", rate=(1e9, 0.3, 400.0), rate_low=(1e12, 0.1, 100.0)),
           toys.recomb("falloff", rate=(5e8, 0.0, 800.0), rate_low=(1e13, -1.1, 100.0), troe=(0.5, 100.0, 2000.0, 3000.0),
@@ -29,7 +30,11 @@ def _mechanism(tmp_path_factory):
           # net coefficients of 3 (the float-pair product path of the accumulation, not the exact scaling)
           Reaction(kind="elementary", reversible=True, reactants=[(2, 3)], products=[(0, 3), (1, 3)],
                    rate=(1e8, 0.5, 1000.0))]
-    _, path = toys.toy("kinds", rx, d)
+
+
+def _mechanism(tmp_path_factory):
+    d = str(tmp_path_factory.mktemp("kinds"))
+    _, path = toys.toy("kinds", reactions(), d)
     return path
 
 
