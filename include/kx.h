@@ -113,13 +113,18 @@ typedef struct {
   int libmath;        /* 1: CUDA's exp/log in the float64 kernels instead of the library's own */
   int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);
                          launch calls on such a handle return KX_ERR_UNSUPPORTED */
-  int rates_layout;   /* double-float KX_FP64 production rates: 0 (default) or 2 warp-cooperative --
-                         a warp evaluates a group of states together, the reactions of each class
-                         dealt out over its lanes as (state, reaction) pairs, the species vectors
-                         and per-reaction rates in shared memory, wdot gathered species-major;
-                         1 one thread per state with its species vectors in local memory */
+  int rates_layout;   /* double-float KX_FP64 production rates: 0 (default) by batch size -- the
+                         warp-cooperative kernel for batches smaller than the thread-per-state
+                         kernel's resident capacity (one wave of its blocks on every SM; ~78k states
+                         on GB300 at 128 threads per block), the thread-per-state kernel above it;
+                         1 always one thread per state (species vectors in local memory);
+                         2 always warp-cooperative (the states of a warp share its lanes: the
+                         reactions of each class dealt out as (state, reaction) pairs, species
+                         vectors and per-reaction rates in shared memory, wdot gathered
+                         species-major).  The two kernels agree to ~1e-11 of the per-point scale,
+                         not bit for bit (different summation orders). */
   int rates_group;    /* warp-cooperative production rates: states per warp, a power of two up to
-                         32; 0 (default) as many as the shared memory of four blocks allows */
+                         32; 0 (default) one */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 
@@ -233,7 +238,8 @@ kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double
 /* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
  * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
  * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp" and
- * "wdot_fp64_noalloc" (the kernel of kx_production_rates_noalloc).  Any
+ * "wdot_fp64_noalloc" (the kernel of kx_production_rates_noalloc) and
+ * "wdot_fp64_wc" (the warp-cooperative production-rate kernel).  Any
  * output pointer may be NULL.  registers and local_bytes: per thread, from
  * the compiler's report (local_bytes is the stack frame: local arrays and
  * register spills, the local memory the driver backs for every resident

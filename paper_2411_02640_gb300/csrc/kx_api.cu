@@ -348,7 +348,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
       {"thermo", kx::KernelKind::Thermo, false, 0},       {"visc_fp64", kx::KernelKind::Transport, false, 1},
       {"diff_fp64", kx::KernelKind::Transport, false, 2}, {"visc_mixed", kx::KernelKind::Transport, true, 1},
       {"diff_mixed", kx::KernelKind::Transport, true, 2}, {"vjp", kx::KernelKind::Vjp, false, 0},
-      {"wdot_fp64_noalloc", kx::KernelKind::Wdot, false, 0},
+      {"wdot_fp64_noalloc", kx::KernelKind::Wdot, false, 0}, {"wdot_fp64_wc", kx::KernelKind::Wdot, false, 0},
   };
   for (const Spec& sp : specs) {
     std::unique_ptr<Kernel> k(new Kernel());
@@ -365,7 +365,9 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.rates_mode = h->opt.rates_mode;
     k->eopt.rates_arith = h->opt.rates_arith;
     k->eopt.scratch = std::strcmp(sp.name, "wdot_fp64_noalloc") == 0;
-    k->eopt.rates_layout = h->opt.rates_layout;
+    const bool wc_spec = std::strcmp(sp.name, "wdot_fp64_wc") == 0;
+    k->eopt.rates_layout = wc_spec ? 2 : h->opt.rates_layout;
+    if (wc_spec) k->eopt.rates_arith = 0;
     k->eopt.rates_group = h->opt.rates_group;
     if (kx::wdot_is_wc(h->m, sp.kind, k->eopt)) {
       const kx::WcShape w = kx::wdot_wc_shape(h->m, k->eopt);
@@ -453,6 +455,14 @@ kx_status kx_production_rates(kx_handle h, const double* T, const double* p, con
   if (n == 0) return KX_OK;
   long long ldl = ld, nl = n;
   void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
+  if (precision == KX_FP64 && h->opt.rates_layout == 0 && h->opt.rates_arith != 1) {
+    // batches smaller than the thread-per-state kernel's resident capacity (it would leave SMs idle and
+    // take one state's whole latency) go to the warp-cooperative kernel, whose warps share each state
+    Kernel* tps = find_kernel(h, "wdot_fp64");
+    s = ensure_ready(h, *tps);
+    if (s != KX_OK) return s;
+    if (n < (int64_t)tps->max_blocks * tps->eopt.block) return launch(h, "wdot_fp64_wc", args, n, stream);
+  }
   return launch(h, precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed", args, n, stream);
 }
 

@@ -1534,18 +1534,24 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c)
 // packed species entries (kx_s<c>), the Arrhenius / blend records (kx_f<c>) and
 // the efficiency / PLOG index pairs (kx_e<c>); the efficiencies, PLOG tables
 // and per-species G/RT coefficients, T_mid, 1/W and ln W shared by all classes.
-std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m) {
+// merged: one class per (kind, reversibility, blend), entry counts the class's largest, shorter
+// reactions padded with entries of species ns (a zero vector the warp-cooperative kernel keeps) and
+// each record's f1.w holding -dn, the negated change in mole count (the padding hides it)
+std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m, bool merged = false) {
   const int ns = m.ns;
   std::vector<DfClass> cls;
   for (int i = 0; i < m.nr(); ++i) {
     const Reaction& r = m.rx[i];
     const int nre = (int)entries(r.reac).size(), npr = (int)entries(r.prod).size();
     const Blend bl = (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) ? r.blend : Blend::Lindemann;
-    const bool kc = (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && r.k.beta == 0.0 && r.k.E == 0.0;
+    const bool kc = !merged && (r.kind == Kind::Elementary || r.kind == Kind::ThreeBody) && r.k.beta == 0.0 && r.k.E == 0.0;
     auto it = std::find_if(cls.begin(), cls.end(), [&](const DfClass& d) {
-      return d.kind == r.kind && d.rev == r.reversible && d.blend == bl && d.nre == nre && d.npr == npr && d.kconst == kc;
+      return d.kind == r.kind && d.rev == r.reversible && d.blend == bl &&
+             (merged || (d.nre == nre && d.npr == npr && d.kconst == kc));
     });
     if (it == cls.end()) { cls.push_back(DfClass{r.kind, r.reversible, bl, nre, npr, kc, {}, 0}); it = cls.end() - 1; }
+    it->nre = std::max(it->nre, nre);
+    it->npr = std::max(it->npr, npr);
     it->rx.push_back(i);
   }
   std::string eff, plog, plogp;
@@ -1560,6 +1566,11 @@ std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m) {
     for (int i : d.rx) {
       const Reaction& r = m.rx[i];
       auto er = entries(r.reac), ep = entries(r.prod);
+      const int dn_i = (int)ep.size() - (int)er.size();
+      if (merged) {
+        while ((int)er.size() < d.nre) er.push_back(ns);
+        while ((int)ep.size() < d.npr) ep.push_back(ns);
+      }
       {
         // entry j: species k in the low 16 bits, and in the high 16 bits the upper half of the float32
         // of c, the species' net coefficient on its first entry and 0 on repeats (so that the
@@ -1585,7 +1596,7 @@ std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m) {
       double maxeff = r.default_eff;
       for (auto& x : r.eff) maxeff = std::max(maxeff, x.second);
       sf += "{" + fpair(std::log(r.k.A > 0 ? r.k.A : 1e-300)) + "," + fpair(r.k.beta) + "},";
-      sf += "{" + fpair(-r.k.E) + "," + F(std::log(std::max(maxeff, 1e-30))) + ",0.0f},";
+      sf += "{" + fpair(-r.k.E) + "," + F(std::log(std::max(maxeff, 1e-30))) + "," + (merged ? F(-dn_i) : std::string("0.0f")) + "},";
       if (tb) {
         double p[5] = {0, 0, 0, 0, 0};
         if (r.blend == Blend::Troe) { p[0] = 1.0 - r.troe[0]; p[1] = r.troe[0]; p[2] = -1.0 / r.troe[1]; p[3] = -1.0 / r.troe[2]; p[4] = -r.troe[3]; }
@@ -2738,28 +2749,26 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
 //   6. wdot_k 2^S written out as float64.
 struct WcLayout {
   int G = 1, warps = 4, nw32 = 1, svs = 1;
-  int off_sv = 0, off_qm = 0, off_sci = 0, off_nm = 0, off_qe = 0, warp_bytes = 0;
+  int off_sv = 0, off_yv = 0, off_qm = 0, off_sci = 0, off_nm = 0, off_qe = 0, warp_bytes = 0;
 };
 
 WcLayout wc_layout_of(const Mechanism& m, int group, int block) {
   WcLayout L;
   L.warps = block / 32;
-  L.nw32 = (m.ns + 31) / 32;
-  // species region per state: the {ln |C|, mu} float4s, later reused for up to ns + 31 float-pair slots
-  L.svs = std::max(m.ns, (m.ns + 32) / 2 + 1);
-  const int per_state = 80 + 16 * L.svs + 8 * m.nr() + 8 + 4 * L.nw32 + 2 * m.nr();
-  if (group > 0) {
-    L.G = group;
-  } else {
-    // as many states per warp as keep four blocks of this size within ~200 KB of shared memory
-    const int budget = 200 * 1024 / (4 * L.warps) - 1536;
-    L.G = 1;
-    while (L.G < 32 && 2 * L.G * per_state <= budget) L.G *= 2;
-  }
+  L.nw32 = (m.ns + 32) / 32;   // species 0..ns (ns: the zero entry that pads shorter reactions)
+  // species region per state: the {ln |C|, mu} float4s of species 0..ns, later reused for up to
+  // ns + 31 float-pair slots
+  L.svs = std::max(m.ns + 1, (m.ns + 32) / 2 + 1);
+  const int per_state = 80 + 16 * L.svs + 8 * L.svs + 8 * m.nr() + 8 + 4 * L.nw32 + 2 * m.nr();
+  // one state per warp unless asked otherwise: the kernel serves small batches, where the
+  // parallelism of many warps per state matters most
+  L.G = group > 0 ? group : 1;
+  (void)per_state;
   const int G = L.G;
   auto up16 = [](int b) { return (b + 15) / 16 * 16; };
   L.off_sv = up16(80 * G);
-  L.off_qm = up16(L.off_sv + 16 * G * L.svs);
+  L.off_yv = up16(L.off_sv + 16 * G * L.svs);
+  L.off_qm = up16(L.off_yv + 8 * G * L.svs);
   L.off_sci = up16(L.off_qm + 8 * G * m.nr());
   L.off_nm = up16(L.off_sci + 8 * G);
   L.off_qe = up16(L.off_nm + 4 * G * L.nw32);
@@ -2773,7 +2782,8 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
   const WcLayout L = wc_layout_of(m, opt.rates_group, opt.block);
   const int G = L.G, NW32 = L.nw32, SVS = L.svs;
   const int LG = __builtin_ctz(G);
-  std::vector<DfClass> cls = emit_class_tables(globals, m);
+  const bool merged = true;
+  std::vector<DfClass> cls = emit_class_tables(globals, m, merged);
   Out& g = globals;
 
   // ---- gather table: species-major entries (reaction, net coefficient), cut into 32/G chunks of
@@ -2830,6 +2840,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
   o("#define KX_PF(p) kx_mk((p)[0], (p)[1])");
   o("float4* const sc4 = (float4*)wsm;   // [G][5]: {Td, ln T}, {1/T, ln(p_atm/RT)}, {C_M, C_M/sigma}, {ln p}, {T, p bits}");
   o(fmt("float4* const sv = (float4*)(wsm + %d);   // [G][%d]: {ln |C_k|, mu_k} float pairs; later the gather slots", L.off_sv, SVS));
+  o(fmt("float2* const yv = (float2*)(wsm + %d);   // [G][%d]: Y_k/W_k float pairs (third-body sums)", L.off_yv, SVS));
   o(fmt("float2* const qm = (float2*)(wsm + %d);   // [G][nr]: rate mantissas, then scaled rates", L.off_qm));
   o(fmt("int2* const sci = (int2*)(wsm + %d);      // [G]: {largest rate exponent, flag: 0 ok, 1 outside the domain, 2 past n}", L.off_sci));
   o(fmt("unsigned* const nmk = (unsigned*)(wsm + %d);   // [G][%d]: bit k set for Y_k < 0", L.off_nm, NW32));
@@ -2863,6 +2874,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
     "__int_as_float(__double2loint(P)), __int_as_float(__double2hiint(P)));");
   o("sci[lane] = make_int2(-32768, flag);");
   o(fmt("for (int w = 0; w < %d; ++w) nmk[%d * lane + w] = 0u;", NW32, NW32));
+  o(fmt("sv[%d * lane + %d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // the padding species: ln |C| = mu = 0", SVS, ns));
   --o.ind;
   o("}");
   o("__syncwarp();");
@@ -2878,7 +2890,11 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
   o(fmt("for (int t = 0; t < %d; ++t) {", NT));
   o(fmt("  const int k = (lane >> %d) + %d * t;", LG, 32 / G));
   o(fmt("  Yv[t] = (k < %d && inb) ? Y_[(long long)k * ld + is] : 0.0;", ns));
-  o(fmt("  if (k < %d) sg = kx_df_fma(kx_d2df_i(Yv[t]), KX_PF(kx_iwf + 2 * k), sg);", ns));
+  o(fmt("  if (k < %d) {", ns));
+  o("    const kx_df yk = kx_df_mul(kx_d2df_i(Yv[t]), KX_PF(kx_iwf + 2 * k));");
+  o(fmt("    yv[%d * gs + k] = make_float2(yk.hi, yk.lo);", SVS));
+  o("    sg = kx_df_add(sg, yk);");
+  o("  }");
   o("}");
   o("// sigma of state gs: a butterfly over the lanes that serve it, then lane gs's sum for all");
   for (int off = G; off < 32; off *= 2)
@@ -2938,13 +2954,13 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
       o(fmt("for (int p = lane; p < %d; p += 32) {   // class %d: %d reactions, %d reactant and %d product entries", G * NC,
             (int)ci, NC, d.nre, d.npr));
       ++o.ind;
-      o(fmt("const int g = p / %d, r = p - g * %d;", NC, NC));
+      o(fmt("const int g = p & %d, r = p >> %d;   // lanes of one reaction side by side (its record loaded once)", G - 1, LG));
       o("const float4 A0 = sc4[5 * g + 0], A1 = sc4[5 * g + 1];");
       o("const kx_df Td = kx_mk(A0.x, A0.y), lnT = kx_mk(A0.z, A0.w), iT = kx_mk(A1.x, A1.y), lnPRT = kx_mk(A1.z, A1.w);");
       if (tb) {
         o("const float4 A2 = sc4[5 * g + 2];");
         o("const kx_df cM = kx_mk(A2.x, A2.y), fC = kx_mk(A2.z, A2.w);");
-        o("const long long iy = i0 + g < n ? i0 + g : n - 1;   // states past n read a valid row; their results are dropped");
+        o(fmt("const float2* yg = yv + %d * g;", SVS));
       }
       if (d.kind == Kind::Plog) {
         o("const float4 A3 = sc4[5 * g + 3], A4 = sc4[5 * g + 4];");
@@ -2970,12 +2986,12 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         o("kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
         o("if (e.y < 0) {");
         o("  const int kc = kx_effd[e.x].k;");
-        o("  X = kx_df_mul(kx_df_mul(kx_d2df_i(Y_[(long long)kc * ld + iy]), KX_PF(kx_iwf + 2 * kc)), fC);");
+        o("  X = kx_df_mul(kx_mk(yg[kc].x, yg[kc].y), fC);");
         o("} else {");
         o("  kx_df t = kx_mk(0.0f, 0.0f);");
         o("  for (int j = 0; j < e.y; ++j) {");
         o("    const kx_effd_t q = kx_effd[e.x + j];");
-        o("    t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_df_mul(kx_d2df_i(Y_[(long long)q.k * ld + iy]), KX_PF(kx_iwf + 2 * q.k)), t);");
+        o("    t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_mk(yg[q.k].x, yg[q.k].y), t);");
         o("  }");
         o("  X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
         o("}");
@@ -3024,6 +3040,11 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         o("}");
         c.fp32 += NC * (4 * kDfFma + 3 * kDfAdd + kDfDiv);
       }
+      int real_re = 0, real_e = 0;   // entries without the padding, for the operation counts
+      for (int i : d.rx) {
+        real_re += (int)entries(m.rx[i].reac).size();
+        real_e += (int)entries(m.rx[i].reac).size() + (int)entries(m.rx[i].prod).size();
+      }
       o("kx_df lf = lk;");
       for (int j = 0; j < d.nre; ++j) o(fmt("lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
       auto negbit = [&](int j) { return fmt("((nmg[k%d >> 5] >> (k%d & 31)) & 1)", j, j); };
@@ -3034,7 +3055,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
       }
       o("int sf = " + sfx + ";");
       o("kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
-      c.fp32 += NC * ((d.kconst ? 0 : 2 * kDfFma) + d.nre * kDfAdd + kDfExp + kDfMul);
+      c.fp32 += NC * (2 * kDfFma + kDfExp + kDfMul) + real_re * kDfAdd;
       if (d.rev) {
         const int dn = d.npr - d.nre;
         o("{   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
@@ -3042,7 +3063,8 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         o("  kx_df dl = " + first + ";");
         for (int j = 1; j < E; ++j)
           o(fmt("  dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
-        if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+        if (merged) o("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, f1.w));   // -dn ln(p_atm/RT), dn of this reaction");
+        else if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
         else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
         o("  const int sr = " + srx + ";");
         o("  const bool rev = dl.hi > 0.0f;");
@@ -3053,7 +3075,8 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         o("  fac = kx_mk(s1.hi, __fmaf_rn(pm, e.lo, s1.lo));");
         o("  if (sf == sr) sf ^= (int)rev;");
         o("}");
-        c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+        c.fp32 += (real_e - NC) * kDfAdd + NC * (kDfAdd + kDfMulf + kDfAdd + kDfExp + 10);
+        (void)dn;
       }
       o("int ex;");
       o("kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex");
@@ -3153,7 +3176,7 @@ int transport_smem_per_thread(const Mechanism& m, bool mixed, int part, int layo
 // ------------------------------------------------------------------ kernels
 bool wdot_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt) {
   (void)m;
-  return kind == KernelKind::Wdot && !opt.mixed && !opt.scratch && opt.rates_arith != 1 && opt.rates_layout != 1;
+  return kind == KernelKind::Wdot && !opt.mixed && !opt.scratch && opt.rates_arith != 1 && opt.rates_layout == 2;
 }
 
 WcShape wdot_wc_shape(const Mechanism& m, const EmitOptions& opt) {
@@ -3181,9 +3204,9 @@ std::string emit_wc_kernel(const Mechanism& m, const EmitOptions& opt, const std
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   s << "__device__ unsigned long long kx_bad_first = 0xffffffffffffffffull;\n";
-  // 128 registers by default (four blocks of 128 threads per SM), fewer where the shared memory
-  // of more blocks fits
-  const int rreg = opt.maxrreg > 0 ? opt.maxrreg : 128;
+  // 80 registers by default: six blocks of 128 threads per SM (measured on 53/325 with one state per
+  // warp: 64 / 80 / 96 registers -> 8.97 / 8.74 / 8.93 ms per 2^20 states)
+  const int rreg = opt.maxrreg > 0 ? opt.maxrreg : 80;
   const int min_blocks = std::max(1, 65536 / (rreg * opt.block));
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ", " << min_blocks << ") " << entry
     << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "

@@ -74,10 +74,9 @@ struct EmitOptions {
   int rates_arith = 0;      // float64-accurate rates: 0/2 double-float (reaction classes), 1 native float64
   bool scratch = false;     // float-pair rates: species vectors in a global scratch array passed by the
                             // caller (strided by the grid's thread count) instead of local memory
-  int rates_layout = 0;     // float-pair production rates: 0 auto (warp-cooperative), 1 thread per state,
-                            // 2 warp-cooperative (states of a warp share their lanes, vectors in shared memory)
-  int rates_group = 0;      // warp-cooperative: states per warp (power of two up to 32; 0: as many as the
-                            // shared memory of four blocks allows)
+  int rates_layout = 0;     // float-pair production rates: 0/1 thread per state, 2 warp-cooperative (the
+                            // states of a warp share its lanes, species vectors in shared memory)
+  int rates_group = 0;      // warp-cooperative: states per warp (power of two up to 32; 0: one)
 };
 
 // Launch shape of the warp-cooperative production-rate kernel.

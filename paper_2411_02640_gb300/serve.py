@@ -16,9 +16,14 @@ mechanisms.  A scheduler thread
   * completes a request's Future when its batch's event has fired, and
     records its latency (submit to completion).
 
-Every state's computation is independent of the others in its batch and
-runs the same instruction sequence wherever it lands, so a request's
-result is bit-identical alone and in the mix.
+Every state's computation is independent of the others in its batch.  The
+mixed-precision rate kernel and the transport kernels run the same
+instruction sequence for a state wherever it lands, so those results are
+bit-identical alone and in the mix; the float64-accurate production rates
+use the warp-cooperative kernel for batches below the thread-per-state
+kernel's resident capacity and the thread-per-state kernel above it, so a
+request's result alone and in the mix agree within the float64 bar (about
+1e-11 of the per-point scale), not bit for bit.
 """
 from __future__ import annotations
 
@@ -61,6 +66,31 @@ class Result:
     latency_s: float = 0.0
 
 
+class _PinnedPool:
+    """Pinned host staging buffers reused from batch to batch: allocating
+    (and pinning) host memory takes far longer than a copy, so it is done
+    once per size class (powers of two, at least 1 MiB) and the buffers are
+    handed back when their batch's results have been copied out."""
+
+    def __init__(self, torch):
+        self.torch = torch
+        self.free: Dict[int, List[object]] = collections.defaultdict(list)
+        self.lock = threading.Lock()
+        self.allocated = 0
+
+    def get(self, nbytes: int):
+        cls = max(1 << 20, 1 << (max(1, int(nbytes)) - 1).bit_length())
+        with self.lock:
+            if self.free[cls]:
+                return self.free[cls].pop()
+            self.allocated += cls
+        return self.torch.empty(cls, dtype=self.torch.uint8, pin_memory=True)
+
+    def put(self, buf) -> None:
+        with self.lock:
+            self.free[int(buf.numel())].append(buf)
+
+
 @dataclass(eq=False)
 class _Batch:
     key: tuple
@@ -70,6 +100,7 @@ class _Batch:
     nbytes: int
     outs: Dict[str, object] = field(default_factory=dict)
     offsets: List[int] = field(default_factory=list)
+    staging: List[object] = field(default_factory=list)   # pooled pinned buffers behind outs
 
 
 class Server:
@@ -99,6 +130,10 @@ class Server:
         self.points_done = 0
         self.launches = 0
         self.error: Optional[BaseException] = None
+        self.pool = _PinnedPool(torch)
+        # results of requests without their own host buffers are copied out of the pooled staging
+        # buffers off the scheduling thread
+        self.copier = cf.ThreadPoolExecutor(max_workers=2, thread_name_prefix="kx-serve-copy")
 
     # ---------------------------------------------------------------- API
     def bytes_per_point(self, name: str, transport: bool) -> int:
@@ -160,6 +195,7 @@ class Server:
             self.lock.notify()
         if self.thread:
             self.thread.join(timeout)
+        self.copier.shutdown(wait=True)
 
     def __enter__(self):
         return self.start()
@@ -262,8 +298,12 @@ class Server:
                 o += r.n
             w = mech.production_rates(T, p, Y, precision=prec, stream=stream)
 
+            staging = []
+
             def down(t):
-                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                buf = self.pool.get(t.numel() * 8)
+                staging.append(buf)
+                h = buf[:t.numel() * 8].view(torch.float64).view(t.shape)
                 h.copy_(t, non_blocking=True)
                 return h
             dev = {"wdot": w}
@@ -283,7 +323,7 @@ class Server:
             ev = torch.cuda.Event()
             ev.record(stream)
         self.launches += 1
-        self.inflight.append(_Batch(key, reqs, stream, ev, nbytes, outs, offs))
+        self.inflight.append(_Batch(key, reqs, stream, ev, nbytes, outs, offs, staging))
 
     def _complete(self) -> None:
         done = []
@@ -299,21 +339,35 @@ class Server:
                 self.free_streams.append(b.stream)
             if done:
                 self.lock.notify()
-        now = time.perf_counter()
         for b in done:
-            for r, o in zip(b.reqs, b.offsets):
-                if r.out is not None:
-                    res = Result(wdot=r.out["wdot"].numpy())
-                    if r.transport:
-                        res.mu, res.lam, res.Dk = (r.out[k].numpy() for k in ("mu", "lam", "Dk"))
-                else:
-                    res = Result(wdot=b.outs["wdot"][:, o:o + r.n].numpy())
-                    if r.transport:
-                        res.mu = b.outs["mu"][o:o + r.n].numpy()
-                        res.lam = b.outs["lam"][o:o + r.n].numpy()
-                        res.Dk = b.outs["Dk"][:, o:o + r.n].numpy()
-                r.t_done = now
-                res.latency_s = now - r.t_submit
+            if b.staging:
+                self.copier.submit(self._finish, b)
+            else:
+                self._finish(b)
+
+    def _finish(self, b: _Batch) -> None:
+        """Hand each request of a finished batch its Result: views of its own
+        host buffers, or copies out of the pooled staging buffers (which then
+        go back to the pool)."""
+        for r, o in zip(b.reqs, b.offsets):
+            if r.out is not None:
+                res = Result(wdot=r.out["wdot"].numpy())
+                if r.transport:
+                    res.mu, res.lam, res.Dk = (r.out[k].numpy() for k in ("mu", "lam", "Dk"))
+            else:
+                res = Result(wdot=b.outs["wdot"][:, o:o + r.n].numpy().copy())
+                if r.transport:
+                    res.mu = b.outs["mu"][o:o + r.n].numpy().copy()
+                    res.lam = b.outs["lam"][o:o + r.n].numpy().copy()
+                    res.Dk = b.outs["Dk"][:, o:o + r.n].numpy().copy()
+            now = time.perf_counter()
+            r.t_done = now
+            res.latency_s = now - r.t_submit
+            with self.lock:
                 self.latencies.append(res.latency_s)
                 self.points_done += r.n
-                r.future.set_result(res)
+            r.future.set_result(res)
+        for buf in b.staging:
+            self.pool.put(buf)
+        b.staging = []
+        b.outs = {}

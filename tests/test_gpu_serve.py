@@ -1,4 +1,7 @@
-"""The continuous-batching server: results identical alone and in the mix,
+"""The continuous-batching server: results the same alone and in the mix
+(bit for bit for the mixed-precision rates and the transport; within the
+float64 bar for the float64-accurate rates, whose kernel depends on the
+batch size),
 admission under a device-memory budget, rejection of oversize requests,
 and agreement with direct library calls."""
 import threading
@@ -7,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2411_02640_gb300 import synth
-from tests.gpu_common import mechanism, torch_cuda
+from tests.gpu_common import mechanism, torch_cuda, wdot_error
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +65,14 @@ def test_result_identical_alone_and_in_the_mix(server_parts):
         alone = [srv.submit(name, T, p, Y, precision=prec, transport=tr).result(timeout=300)
                  for name, (T, p, Y), prec, tr in work]
     for a, b, (name, _, prec, tr) in zip(mixed, alone, work):
-        assert np.array_equal(a.wdot, b.wdot, equal_nan=True), name
+        if prec == "fp64":
+            # a request alone may be small enough for the warp-cooperative rate kernel and in the mix
+            # part of a batch large enough for the thread-per-state one: the two agree within the
+            # float64 bar (1e-10 of the per-point scale), not bit for bit
+            W = np.array(server_parts[name].W)
+            assert wdot_error(W, a.wdot, b.wdot).max() <= 1e-10, name
+        else:
+            assert np.array_equal(a.wdot, b.wdot, equal_nan=True), name
         if tr:
             assert np.array_equal(a.mu, b.mu) and np.array_equal(a.lam, b.lam) and np.array_equal(a.Dk, b.Dk)
 

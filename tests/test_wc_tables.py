@@ -65,8 +65,8 @@ def _replay(src, ns, nr, q):
 
 def _check(mech_obj, path, tmp_cache):
     m = kx.Mechanism(path, cache_dir=tmp_cache, compile_only=1, lazy=1)
-    src = m.kernel_source("wdot_fp64")
-    assert "kx_wtab" in src, "the default float-pair rate kernel is warp-cooperative"
+    src = m.kernel_source("wdot_fp64_wc")
+    assert "kx_wtab" in src
     ns, nr = mech_obj.n_species, len(mech_obj.reactions)
     rng = np.random.default_rng(3)
     q = rng.standard_normal(nr) * np.exp(rng.uniform(-20, 20, nr))
@@ -93,7 +93,7 @@ def test_gather_tables_every_group_size(group, tmp_path):
     mech = synth.mechanism(name)
     path = synth.mechanism_file(name, str(tmp_path))
     m = kx.Mechanism(path, cache_dir=str(tmp_path / "cache"), compile_only=1, lazy=1, rates_group=group)
-    src = m.kernel_source("wdot_fp64")
+    src = m.kernel_source("wdot_fp64_wc")
     assert f"const int gs = lane & {group - 1};" in src
     rng = np.random.default_rng(group)
     q = rng.standard_normal(len(mech.reactions))
