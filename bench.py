@@ -275,7 +275,7 @@ def run_kx(args):
         extra["large"] = pool.submit(load, "large_160_900")
     mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg, rates_mode=args.rates_mode,
                         rates_arith=args.rates_arith, tr_layout=args.tr_layout, block=args.block,
-                        diff_mode=args.diff_mode)
+                        diff_mode=args.diff_mode, rates_layout=args.rates_layout, rates_group=args.rates_group)
     ns = mech.n_species
     T, p, Y = make_inputs(rank, n)
     dev = torch.device("cuda", local)
@@ -828,6 +828,26 @@ def large_block(mech, dev, stream, K, W, sm_max, n=1 << 22, name="large_160_900"
     return out
 
 
+def run_profile_rates(args):
+    """A short driver for ncu captures of one production-rate kernel: loads
+    --mech with the given layout options, draws --points states on the
+    device and calls kx_production_rates twice (capture the second launch
+    with -s 1 -c 1)."""
+    import torch
+    from paper_2411_02640_gb300 import kx, synth
+    torch.cuda.set_device(0)
+    spec = synth.STATE_SPECS[args.mech]
+    opts = dict(rates_layout=args.rates_layout, rates_group=args.rates_group, maxrreg=args.maxrreg,
+                rates_arith=args.rates_arith, block=args.block, lazy=1)
+    m = kx.Mechanism(synth.mechanism_file(args.mech, os.path.join(CACHE, "mech")), cache_dir=CACHE, **opts)
+    T, p, Y = synth.make_states_torch(m.n_species, spec, args.points, seed=spec.seed)
+    w = m.production_rates(T, p, Y, precision=args.precision)
+    m.production_rates(T, p, Y, out=w, precision=args.precision)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_rates": args.mech, "points": args.points, "options": opts, "precision": args.precision,
+                      "finite": bool(torch.isfinite(w).all())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -852,6 +872,13 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="measure the arithmetic pipes' per-clock rates only")
     ap.add_argument("--write-peaks", action="store_true", help="with --peaks: store the record the roofline reads")
     ap.add_argument("--sweep", action="store_true", help="point-count sweep of the step on 9/21 and 53/325 only")
+    ap.add_argument("--profile-rates", action="store_true",
+                    help="two production-rate calls on --mech at --points states (a driver for ncu captures)")
+    ap.add_argument("--mech", default=MECH, help="mechanism of --profile-rates")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="precision of --profile-rates")
+    ap.add_argument("--rates-layout", type=int, default=0,
+                    help="float-pair rates: 0 by batch size, 1 thread per state, 2 warp-cooperative")
+    ap.add_argument("--rates-group", type=int, default=0, help="warp-cooperative rates: states per warp (0: one)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the native float64, 9/21 (4096 states) and 160/900 blocks of the default line")
     args = ap.parse_args()
@@ -861,6 +888,8 @@ def main():
         run_alternatives(args)
     elif args.peaks:
         run_peaks(args)
+    elif args.profile_rates:
+        run_profile_rates(args)
     elif args.sweep:
         run_sweep(args)
     elif args.serve:
