@@ -114,9 +114,12 @@ typedef struct {
   int compile_only;   /* 1: emit and compile but do not load onto a device (no GPU needed);
                          launch calls on such a handle return KX_ERR_UNSUPPORTED */
   int rates_layout;   /* double-float KX_FP64 production rates: 0 (default) by batch size -- the
-                         warp-cooperative kernel for batches smaller than the thread-per-state
-                         kernel's resident capacity (one wave of its blocks on every SM; ~78k states
-                         on GB300 at 128 threads per block), the thread-per-state kernel above it;
+                         warp-cooperative kernel for batches below min(C, 49152 u) states and the
+                         thread-per-state kernel from there on, C being the thread-per-state
+                         kernel's resident capacity (one wave of its blocks on every SM; ~78k
+                         states on GB300 at 128 threads per block) and u the share of lane slots
+                         the warp-cooperative class rounds fill (~0.2 for 9/21, ~0.9 for 53/325);
+                         the crossover measured on GB300;
                          1 always one thread per state (species vectors in local memory);
                          2 always warp-cooperative (the states of a warp share its lanes: the
                          reactions of each class dealt out as (state, reaction) pairs, species

@@ -58,6 +58,7 @@ struct Kernel {
   int max_blocks = 0;          // resident blocks for a persistent grid (per device 0 at load)
   int smem = 0;                // dynamic shared memory per block, bytes
   int states_per_block = 0;    // states one block serves per pass of its grid-stride loop (0: one per thread)
+  double lane_use = 1.0;       // warp-cooperative kernels: lane use of their class rounds
   int device = -1;
   std::mutex mu;
   bool ready = false;
@@ -376,6 +377,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
                                         "(choose a smaller rates_group or rates_layout 1)");
       k->smem = w.smem_per_block;
       k->states_per_block = w.states_per_block;
+      k->lane_use = w.lane_use;
     }
     if (sp.kind == kx::KernelKind::Transport) {
       // species vectors staged in shared memory: as many threads as fit in ~216 KB, a multiple of 32
@@ -456,12 +458,18 @@ kx_status kx_production_rates(kx_handle h, const double* T, const double* p, con
   long long ldl = ld, nl = n;
   void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
   if (precision == KX_FP64 && h->opt.rates_layout == 0 && h->opt.rates_arith != 1) {
-    // batches smaller than the thread-per-state kernel's resident capacity (it would leave SMs idle and
-    // take one state's whole latency) go to the warp-cooperative kernel, whose warps share each state
+    // Small batches go to the warp-cooperative kernel, whose warps share each state: the
+    // thread-per-state kernel would leave SMs idle and take one state's whole latency.  The
+    // crossover, measured on GB300, sits near 48k states times the lane use of the warp-cooperative
+    // class rounds (53/325: ~44k, 160/900: ~46k, 9/21 with its few reactions per class: ~11k), and
+    // never above the thread-per-state kernel's resident capacity.
     Kernel* tps = find_kernel(h, "wdot_fp64");
+    Kernel* wc = find_kernel(h, "wdot_fp64_wc");
     s = ensure_ready(h, *tps);
+    if (s == KX_OK) s = ensure_ready(h, *wc);
     if (s != KX_OK) return s;
-    if (n < (int64_t)tps->max_blocks * tps->eopt.block) return launch(h, "wdot_fp64_wc", args, n, stream);
+    const int64_t cap = (int64_t)tps->max_blocks * tps->eopt.block;
+    if (n < std::min<int64_t>(cap, (int64_t)(49152.0 * wc->lane_use))) return launch(h, "wdot_fp64_wc", args, n, stream);
   }
   return launch(h, precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed", args, n, stream);
 }

@@ -46,6 +46,7 @@
 #include <map>
 #include <set>
 #include <sstream>
+#include <tuple>
 
 #include "kx_internal.h"
 
@@ -3212,6 +3213,17 @@ WcShape wdot_wc_shape(const Mechanism& m, const EmitOptions& opt) {
   w.states_per_warp = L.G;
   w.states_per_block = L.G * L.warps;
   w.smem_per_block = L.warp_bytes * L.warps;
+  // lane use of the merged classes: one class per (kind, reversibility, blend)
+  std::map<std::tuple<int, bool, int>, int> count;
+  for (auto& r : m.rx)
+    ++count[std::make_tuple((int)r.kind, r.reversible,
+                            (r.kind == Kind::Falloff || r.kind == Kind::ChemAct) ? (int)r.blend : (int)Blend::Lindemann)];
+  double pairs = 0, slots = 0;
+  for (auto& kv : count) {
+    pairs += (double)L.G * kv.second;
+    slots += 32.0 * std::ceil(L.G * kv.second / 32.0);
+  }
+  w.lane_use = slots > 0 ? pairs / slots : 1.0;
   return w;
 }
 

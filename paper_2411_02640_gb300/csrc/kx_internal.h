@@ -82,6 +82,7 @@ struct EmitOptions {
 // Launch shape of the warp-cooperative production-rate kernel.
 struct WcShape {
   int states_per_warp = 1, states_per_block = 1, smem_per_block = 0;
+  double lane_use = 1.0;   // (state, reaction) pairs over lane slots of the class rounds
 };
 bool wdot_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt);
 WcShape wdot_wc_shape(const Mechanism& m, const EmitOptions& opt);
