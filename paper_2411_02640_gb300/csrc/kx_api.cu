@@ -448,6 +448,42 @@ kx_status kx_mechanism_info(kx_handle h, int* n_species, int* n_reactions, doubl
   return KX_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The production-rate kernel for a batch of n states.  Small float64-accurate batches go to the
+// warp-cooperative kernel, whose warps share each state: the thread-per-state kernel would leave
+// SMs idle and take one state's whole latency.  The crossover, measured on GB300, sits near 48k
+// states times the lane use of the warp-cooperative class rounds (53/325: ~44k, 160/900: ~46k, 9/21
+// with its few reactions per class: ~11k), and never above the thread-per-state kernel's resident
+// capacity.
+kx_status wdot_kernel_for(kx_mech* h, int64_t n, kx_precision precision, const char** name) {
+  *name = precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed";
+  if (precision != KX_FP64 || h->opt.rates_layout != 0 || h->opt.rates_arith == 1) return KX_OK;
+  Kernel* tps = find_kernel(h, "wdot_fp64");
+  Kernel* wc = find_kernel(h, "wdot_fp64_wc");
+  kx_status s = ensure_ready(h, *tps);
+  if (s == KX_OK) s = ensure_ready(h, *wc);
+  if (s != KX_OK) return s;
+  const int64_t cap = (int64_t)tps->max_blocks * tps->eopt.block;
+  if (n < std::min<int64_t>(cap, (int64_t)(49152.0 * wc->lane_use))) *name = "wdot_fp64_wc";
+  return KX_OK;
+}
+
+// Production rates of n states with the kernel `name`.
+kx_status production_rates_with(kx_mech* h, const char* name, const double* T, const double* p, const double* Y,
+                                int64_t ld, double* wdot, int64_t n, void* stream) {
+  if (n == 0) return KX_OK;
+  long long ldl = ld, nl = n;
+  void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
+  return launch(h, name, args, n, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
 kx_status kx_production_rates(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                               double* wdot, int64_t n, kx_precision precision, void* stream) {
   kx_status s = check_state(h, T, p, Y, ld, n);
@@ -455,23 +491,9 @@ kx_status kx_production_rates(kx_handle h, const double* T, const double* p, con
   if (n > 0 && !wdot) return fail(KX_ERR_ARG, "null output");
   if (precision != KX_FP64 && precision != KX_MIXED) return fail(KX_ERR_ARG, "bad precision");
   if (n == 0) return KX_OK;
-  long long ldl = ld, nl = n;
-  void* args[] = {&T, &p, &Y, &ldl, &wdot, &nl};
-  if (precision == KX_FP64 && h->opt.rates_layout == 0 && h->opt.rates_arith != 1) {
-    // Small batches go to the warp-cooperative kernel, whose warps share each state: the
-    // thread-per-state kernel would leave SMs idle and take one state's whole latency.  The
-    // crossover, measured on GB300, sits near 48k states times the lane use of the warp-cooperative
-    // class rounds (53/325: ~44k, 160/900: ~46k, 9/21 with its few reactions per class: ~11k), and
-    // never above the thread-per-state kernel's resident capacity.
-    Kernel* tps = find_kernel(h, "wdot_fp64");
-    Kernel* wc = find_kernel(h, "wdot_fp64_wc");
-    s = ensure_ready(h, *tps);
-    if (s == KX_OK) s = ensure_ready(h, *wc);
-    if (s != KX_OK) return s;
-    const int64_t cap = (int64_t)tps->max_blocks * tps->eopt.block;
-    if (n < std::min<int64_t>(cap, (int64_t)(49152.0 * wc->lane_use))) return launch(h, "wdot_fp64_wc", args, n, stream);
-  }
-  return launch(h, precision == KX_FP64 ? "wdot_fp64" : "wdot_mixed", args, n, stream);
+  const char* name = nullptr;
+  if ((s = wdot_kernel_for(h, n, precision, &name)) != KX_OK) return s;
+  return production_rates_with(h, name, T, p, Y, ld, wdot, n, stream);
 }
 
 kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
@@ -676,10 +698,14 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   if (c < 256) return fail(KX_ERR_ARG, "workspace smaller than two chunks of 256 states");
   // ... and, where it holds one, a whole number of waves of the launched kernels (states that fill
   // every SM's resident blocks once): a partial last wave in every chunk would idle SMs per chunk
+  // every chunk takes the production-rate kernel that one call over all n states would take, so
+  // that the results do not depend on the chunking
+  const char* wdot_name = nullptr;
+  if ((s = wdot_kernel_for(h, n, precision, &wdot_name)) != KX_OK) return s;
   {
     const bool fp = precision == KX_FP64;
     std::vector<const char*> used;
-    if (outputs & KX_OUT_WDOT) used.push_back(fp ? "wdot_fp64" : "wdot_mixed");
+    if (outputs & KX_OUT_WDOT) used.push_back(wdot_name);
     if (outputs & KX_OUT_THERMO) used.push_back("thermo");
     if (outputs & KX_OUT_TRANSPORT) { used.push_back(fp ? "visc_fp64" : "visc_mixed"); used.push_back(fp ? "diff_fp64" : "diff_mixed"); }
     int64_t wave = 0;
@@ -687,7 +713,7 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
       Kernel* k = find_kernel(h, name);
       if (!k) return fail(KX_ERR_UNSUPPORTED, std::string("no kernel ") + name);
       if ((s = ensure_ready(h, *k)) != KX_OK) return s;
-      wave = std::max<int64_t>(wave, (int64_t)k->max_blocks * k->eopt.block);
+      wave = std::max<int64_t>(wave, (int64_t)k->max_blocks * (k->states_per_block > 0 ? k->states_per_block : k->eopt.block));
     }
     if (wave > 0 && c >= wave) c = c / wave * wave;
   }
@@ -796,7 +822,7 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
     cudaError_t e = cudaStreamWaitEvent(qa, in_done[i % 2], 0);
     if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(qa, out_done[i % 2], 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    if ((outputs & KX_OUT_WDOT) && (s = kx_production_rates(h, dT, dp, dY, c, dw, m, precision, qa)) != KX_OK) return s;
+    if ((outputs & KX_OUT_WDOT) && (s = production_rates_with(h, wdot_name, dT, dp, dY, c, dw, m, qa)) != KX_OK) return s;
     if ((outputs & KX_OUT_THERMO) && (s = kx_thermo(h, dT, dp, dY, c, dcp, dh, m, qa)) != KX_OK) return s;
     if ((outputs & KX_OUT_TRANSPORT) && (s = kx_transport(h, dT, dp, dY, c, dmu, dl, dD, m, precision, qa)) != KX_OK) return s;
     e = cudaEventRecord(comp_done[i % 2], qa);

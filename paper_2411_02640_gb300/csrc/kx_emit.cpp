@@ -187,23 +187,6 @@ __device__ __forceinline__ double kx_net_rate_s(float lnRf, float a, int sf, int
   return neg ? -mag : mag;
 }
 
-// fac 2^t as a float for t below ~127 (the state's scale keeps t <= 64): 0 for
-// t <= -126 (a rate under 2^-189 of the state's largest), nan for nan.
-__device__ __forceinline__ float kx_pow2f_scaled(float t, float fac) {
-  if (!(t > -126.0f)) return t != t ? t : 0.0f;
-  return exp2f(t) * fac;
-}
-// Net rate of progress as in kx_net_rate_s, as a float32 scaled by 2^-S
-// (Sf = S as a float): the mixed-precision production rates accumulate it in
-// float pairs.
-__device__ __forceinline__ float kx_net_rate_sf(float lnRf, float a, int sf, int sr, float Sf) {
-  const float e = lnRf + fmaxf(a, 0.0f);
-  const float fac = sf == sr ? -expm1f(-fabsf(a)) : 1.0f + __expf(-fabsf(a));
-  const float mag = kx_pow2f_scaled(__fmaf_rn(e, KX_LOG2E_F, -Sf), fac);
-  const int neg = sf == sr ? ((a > 0.0f) != (sf != 0)) : sf;
-  return neg ? -mag : mag;
-}
-
 // ln(Pr/(1+Pr)) and ln(1/(1+Pr)) from ln Pr without overflow (float32).
 __device__ __forceinline__ float kx_ln_pr_ratio(float lnPr) {
   return lnPr < 0.0f ? lnPr - log1pf(__expf(lnPr)) : -log1pf(__expf(-lnPr));
@@ -370,11 +353,6 @@ __device__ __forceinline__ kx_df kx_df_add(kx_df a, kx_df b) {
 __device__ __forceinline__ kx_df kx_df_add_u(kx_df a, kx_df b) {
   const kx_df s = kx_ts(a.hi, b.hi);
   return kx_mk(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-// a + b for a float b, without the final renormalisation (running sums)
-__device__ __forceinline__ kx_df kx_df_addf_u(kx_df a, float b) {
-  const kx_df s = kx_ts(a.hi, b);
-  return kx_mk(s.hi, __fadd_rn(s.lo, a.lo));
 }
 __device__ __forceinline__ kx_df kx_df_norm(kx_df a) { return kx_ts(a.hi, a.lo); }
 __device__ __forceinline__ kx_df kx_df_neg(kx_df a) { return kx_mk(-a.hi, -a.lo); }
@@ -1478,10 +1456,8 @@ std::vector<int> entries(const std::vector<std::pair<int, int>>& side) {
 // Mixed-precision body of one reaction class (see emit_rates_mixed for the
 // split): float32 ln k_f, [X], falloff blend and ln |R_f|; the float-pair
 // Gibbs sum ln(|R_r|/|R_f|) rounded once to float32; q as a float64 from
-// kx_net_rate_s (rates of progress) or as a float32 scaled by the state's
-// 2^-S (kx_net_rate_sf, production rates: accumulated in float pairs).
-// Species vectors {ln |C|, C (float32), mu (pair)} in v_j.
-void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c, bool rop) {
+// kx_net_rate_s.  Species vectors {ln |C|, C (float32), mu (pair)} in v_j.
+void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c) {
   const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
   const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
   o(d.kconst ? "  float lk = f0.x;   // k = A" : "  float lk = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
@@ -1546,13 +1522,11 @@ void emit_class_mixed_body(Out& o, const DfClass& d, int ci, int E, OpCounts& c,
       o(fmt("  dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
     if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
     else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
-    if (rop) o("  const double q = kx_net_rate_s(lnRf, __fadd_rn(dl.hi, dl.lo), sf, anyneg ? (" + srx + ") : 0);");
-    else o("  const float q = kx_net_rate_sf(lnRf, __fadd_rn(dl.hi, dl.lo), sf, anyneg ? (" + srx + ") : 0, Sf);");
+    o("  const double q = kx_net_rate_s(lnRf, __fadd_rn(dl.hi, dl.lo), sf, anyneg ? (" + srx + ") : 0);");
     c.fp32 += d.rx.size() * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + 10); c.exp32 += d.rx.size() * 2;
   } else {
-    if (rop) o("  const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
-    else o("  const float q0 = kx_pow2f_scaled(__fmaf_rn(lnRf, KX_LOG2E_F, -Sf), 1.0f);");
-    o(rop ? "  const double q = sf ? -q0 : q0;" : "  const float q = sf ? -q0 : q0;");
+    o("  const double q0 = kx_pow2_scaled(lnRf * KX_LOG2E_F, 1.0f);");
+    o("  const double q = sf ? -q0 : q0;");
     c.exp32 += d.rx.size(); c.fp32 += d.rx.size() * 2;
   }
 }
@@ -1706,7 +1680,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     o(fmt("const kx_strided<kx_df> w{(kx_df*)(kx_scr + (long long)%d * 16 * nthr) + gtid, nthr};", ns));
   } else if (mx) {
     o(fmt("float4 sv[%d];   // {ln |C_k|, C_k (float32), mu_k (pair)}", ns));
-    if (!rop) o(fmt("kx_df w[%d];   // production rates 2^-S, float pairs", ns));
+    if (!rop) o(fmt("double w[%d];", ns));
   } else {
     o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k (pair)}", ns));
     if (!rop) o(fmt("kx_df w[%d];", ns));
@@ -1749,7 +1723,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   o("  const kx_df mk_ = kx_df_add(gk, l);");
   if (mx) {
     o("  sv[k] = make_float4(l.hi, kx_df_mul(kx_d2df_i(Yk), KX_PF(kx_iwf + 2 * k)).hi * fC.hi, mk_.hi, mk_.lo);");
-    if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
+    if (!rop) o("  w[k] = 0.0;");
   } else {
     o("  sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
     if (!rop) o("  w[k] = kx_mk(0.0f, 0.0f);");
@@ -1791,9 +1765,8 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   // ---- pre-pass: float32 upper bound U of ln max(|R_f|, |R_r|) over the reactions
   if (mx) o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, cMf = cM.hi;");
   if (mx && any_plog) o("const float lnPf = lnP.hi;");
-  if (!rop) {
-    o(mx ? "const float lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);"
-         : "const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
+  if (!rop && !mx) {
+    o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
     o("float U = -1.0e30f;");
     for (size_t ci = 0; ci < cls.size(); ++ci) {
       const DfClass& d = cls[ci];
@@ -1847,7 +1820,6 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     o("// largest scaled rate near 2^63.5; |S| < 2^11 keeps S ln2 exact to the float-pair precision");
     o("const int S = kx_rint(fminf(fmaxf(U * KX_LOG2E_F, -1000.0f), 1000.0f)) - 63;");
     o("const float lnSf = __fmul_rn(kx_i2f(S), 0.693147182f);   // S ln2 for the range tests of the scaled exponential");
-    if (mx) o("const float Sf = kx_i2f(S);");
   }
 
   // ---- main pass, one loop per class.  Emitted twice: for warps in which some state has a
@@ -1867,19 +1839,19 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         std::string pdecl = "int";
         for (int j = 0; j < E; ++j) pdecl += fmt("%s p%d = 0", j ? "," : "", j);
         o(pdecl + ";   // entries of the previous reaction (coefficient 0: nothing to add)");
-        o(mx ? "float qp = 0.0f;" : "kx_df qp = kx_mk(0.0f, 0.0f);");
+        o(mx ? "double qp = 0.0;" : "kx_df qp = kx_mk(0.0f, 0.0f);");
       }
       o("#pragma unroll 1");
       o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
       if (!rop)
-        for (int j = 0; j < E; ++j) o(fmt("  const kx_df wl%d = w[p%d & 0xffff];", j, j));
+        for (int j = 0; j < E; ++j) o(fmt("  const %s wl%d = w[p%d & 0xffff];", mx ? "double" : "kx_df", j, j));
       prefetch(d);
       for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
       if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
       o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
       o("  const float4 f0 = f[0], f1 = f[1];");
       if (mx) {
-        emit_class_mixed_body(o, d, (int)ci, E, c, rop);
+        emit_class_mixed_body(o, d, (int)ci, E, c);
       } else {
         o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
                    : "  kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
@@ -1990,10 +1962,10 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         c.fp64 += d.rx.size();
       } else if (mx) {
         for (int j = 0; j < E; ++j)
-          o(fmt("  { const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) w[p%d & 0xffff] = kx_df_addf_u(wl%d, __fmul_rn(qp, __uint_as_float(cj))); }", j, j, j));
+          o(fmt("  { const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) w[p%d & 0xffff] = fma(kx_f2d(__uint_as_float(cj)), qp, wl%d); }", j, j, j));
         o("  qp = q;");
         for (int j = 0; j < E; ++j) o(fmt("  p%d = %s;", j, comp("c", j).c_str()));
-        c.fp32 += d.rx.size() * E * 7 / 2.0;
+        c.fp64 += d.rx.size() * E;
       } else {
         // the previous reaction's rate into its accumulators (loaded at the top of this iteration)
         for (int j = 0; j < E; ++j)
@@ -2007,7 +1979,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       o("}");
       if (!rop && mx)
         for (int j = 0; j < E; ++j)
-          o(fmt("{ const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) { const int kk = p%d & 0xffff; w[kk] = kx_df_addf_u(w[kk], __fmul_rn(qp, __uint_as_float(cj))); } }",
+          o(fmt("{ const unsigned cj = (unsigned)p%d & 0xffff0000u; if (cj != 0u) { const int kk = p%d & 0xffff; w[kk] = fma(kx_f2d(__uint_as_float(cj)), qp, w[kk]); } }",
                 j, j));
       else if (!rop)
         for (int j = 0; j < E; ++j)
@@ -2031,8 +2003,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
   --o.ind;
   o("}");
   if (!rop) {
-    o(fmt("for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));
-    c.fp64 += ns;
+    o(fmt(mx ? "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = w[k];"
+             : "for (int k = 0; k < %d; ++k) out_[(long long)k * ld + i] = kx_df2d_s(w[k], S);", ns));
+    c.fp64 += mx ? 0 : ns;
   }
 }
 
