@@ -1762,64 +1762,15 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
     for (int j = 0; j < E; ++j) o(fmt("  v%d = u%d;", j, j));
   };
 
-  // ---- pre-pass: float32 upper bound U of ln max(|R_f|, |R_r|) over the reactions
   if (mx) o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, cMf = cM.hi;");
   if (mx && any_plog) o("const float lnPf = lnP.hi;");
   if (!rop && !mx) {
-    o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
-    o("float U = -1.0e30f;");
-    for (size_t ci = 0; ci < cls.size(); ++ci) {
-      const DfClass& d = cls[ci];
-      const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
-      const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
-      const int NF = fo ? 7 : tb ? 3 : 2;
-      o("{");
-      ++o.ind;
-      prologue(d, (int)ci);
-      o("#pragma unroll 1");
-      o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
-      prefetch(d);
-      o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
-      o("  const float4 f0 = f[0], f1 = f[1];");
-      o(d.kconst ? "  float b = f0.x;" : "  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
-      if (d.kind == Kind::ThreeBody) {
-        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-        o("  b += e.y < 0 ? sv[kx_effd[e.x].k].x : lncMf + f1.z;");
-      } else if (fo) {
-        o("  const float4 f2 = f[2], f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
-        o("  // ln F <= max(0, ln F_cent) (Troe); ln d + e ln T + max(0, ln base) (SRI)");
-        if (d.blend == Blend::Troe)
-          o("  const float lf = fmaxf(0.0f, __logf(f4.x * __expf(Tf * f5.x) + f4.z * __expf(Tf * f5.z) + __expf(f6.x * iTf)));");
-        else if (d.blend == Blend::Sri)
-          o("  const float lf = f5.z + f6.x * lnTf + fmaxf(0.0f, __logf(f4.x * __expf(f4.z * iTf) + __expf(Tf * f5.x)));");
-        else
-          o("  const float lf = 0.0f;");
-        if (d.kind == Kind::ChemAct) o("  b = fmaf(f3.x, lnTf, fmaf(f3.z, iTf, f2.z)) + lf;");
-        else o("  b += lf;");
-      } else if (d.kind == Kind::Plog) {
-        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
-        o("  const float* t = kx_plogf + 8 * e.x;");
-        o("  b = -1.0e30f;");
-        o("  for (int j = 0; j < e.y; ++j) b = fmaxf(b, fmaf(t[8 * j + 4], lnTf, fmaf(t[8 * j + 6], iTf, t[8 * j + 2])));");
-      }
-      for (int j = 0; j < d.nre; ++j) o(fmt("  b += v%d.x;", j));
-      if (d.rev) {
-        const int dn = d.npr - d.nre;
-        std::string s = dn == 0 ? std::string("0.0f") : fmt("%s * lnPRTf", F(-dn).c_str());
-        for (int j = 0; j < d.nre; ++j) s += fmt(" - v%d.z", j);
-        for (int j = d.nre; j < d.nre + d.npr; ++j) s += fmt(" + v%d.z", j);
-        o("  b += fmaxf(" + s + ", 0.0f);");
-      }
-      o("  U = fmaxf(U, b);");
-      advance(d);
-      o("}");
-      --o.ind;
-      o("}");
-      c.fp32 += d.rx.size() * (8.0 + 2 * (d.nre + d.npr));
-    }
-    o("// largest scaled rate near 2^63.5; |S| < 2^11 keeps S ln2 exact to the float-pair precision");
-    o("const int S = kx_rint(fminf(fmaxf(U * KX_LOG2E_F, -1000.0f), 1000.0f)) - 63;");
-    o("const float lnSf = __fmul_rn(kx_i2f(S), 0.693147182f);   // S ln2 for the range tests of the scaled exponential");
+    // the state's scale 2^-S: set by its first rate (scaled to 2^62) and raised to a later rate (to
+    // 2^62 again), with every accumulator rescaled, when that rate would land above 2^96.  The largest
+    // scaled rate thus sits between 2^62 and 2^97, a running sum stays below ~2^116, and float pairs keep
+    // their full precision for terms down to 2^-164 of the largest (anchoring the largest rate lower,
+    // near 2^0, measured 5e-10 errors: rescaled partial sums fell into the subnormal range)
+    o("int S = -100000;   // no rate yet");
   }
 
   // ---- main pass, one loop per class.  Emitted twice: for warps in which some state has a
@@ -1844,7 +1795,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       o("#pragma unroll 1");
       o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
       if (!rop)
-        for (int j = 0; j < E; ++j) o(fmt("  const %s wl%d = w[p%d & 0xffff];", mx ? "double" : "kx_df", j, j));
+        for (int j = 0; j < E; ++j) o(fmt("  %s wl%d = w[p%d & 0xffff];", mx ? "const double" : "kx_df", j, j));
       prefetch(d);
       for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s;", j, spc("c", j).c_str()));
       if (rop) o(fmt("  const int ri = %s;", comp("c", E).c_str()));
@@ -1952,7 +1903,18 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
           c.fp32 += d.rx.size() * 4;
         } else {
-          o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S (the products and sums after it take hi + lo as is)");
+          o("  int ex;");
+          o("  kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex (products and sums after it take hi + lo as is)");
+          o("  if (ex > S + 96) {   // the state's first rate, or one 2^34 above its scale's anchor: raise the scale");
+          o("    const int d = S - (ex - 62);");
+          o("    const float f = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f;");
+          o(fmt("    for (int k = 0; k < %d; ++k) w[k] = kx_mk(__fmul_rn(w[k].hi, f), __fmul_rn(w[k].lo, f));", ns));
+          for (int j = 0; j < E; ++j) o(fmt("    wl%d = kx_mk(__fmul_rn(wl%d.hi, f), __fmul_rn(wl%d.lo, f));", j, j, j));
+          o("    qp = kx_mk(__fmul_rn(qp.hi, f), __fmul_rn(qp.lo, f));");
+          o("    S = ex - 62;");
+          o("  }");
+          o("  { const int d = ex - S; const float sc = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f; "
+            "q = kx_mk(__fmul_rn(q.hi, sc), __fmul_rn(q.lo, sc)); }   // q 2^(ex - S)");
         }
         o("  if (sf) q = kx_df_neg(q);");
         if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul_u(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
@@ -2556,7 +2518,11 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
     o(fmt("  const %s den = %s;", md.ty, FMA("rho", ld(VS("sZ2", "k")), FMA("r1", ONE1, FMA("r0", ONE1, "Xk"))).c_str()));
     o(fmt("  mu = fma(%s * %s, kx_sqw[k] / %s, mu);", TOD("Xk").c_str(), TOD(MUL("u", "u")).c_str(), TOD("den").c_str()));
     o("}");
-    count_fma(ns * (ns - 1) / 2.0 * 5 + ns * 10); count_exp(ns);
+    // per unordered pair three accumulating multiply-adds and two products; in float pairs these are the
+    // unnormalised forms (12 and 4 float32 instructions), not the renormalised ones of count_fma
+    if (md.kind == TrMode::DF) c.fp32 += ns * (ns - 1) / 2.0 * (3 * 12 + 2 * 4);
+    else count_fma(ns * (ns - 1) / 2.0 * 5);
+    count_fma(ns * 10.0); count_exp(ns);
     c.fp64 += 4 * ns; c.div64 += ns;
   } else {
   o("#pragma unroll 1");
