@@ -1659,6 +1659,12 @@ std::vector<DfClass> emit_class_tables(Out& g, const Mechanism& m, bool merged =
 
 void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, bool rop, OpCounts& c) {
   const int ns = m.ns;
+  // The per-state scale 2^-S of the accumulation: up to 64 species it is set by the first rate and
+  // raised when a later rate outgrows it (no extra pass over the reactions; 53/325: 8.4 -> 7.8 ms per
+  // 2^20 states); larger mechanisms, whose rates span more decades and whose every rescale touches
+  // more accumulators, bound all rates first in float32 (160/900: 142-150 against 158-160 ms per 2^22
+  // states with the running scale)
+  const bool bounded = ns > 64;
   // mixed precision: float32 rates, float-pair chemical potentials and Gibbs sums, float64 accumulation
   const bool mx = opt.mixed;
   std::vector<DfClass> cls = emit_class_tables(g, m);
@@ -1764,7 +1770,64 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
 
   if (mx) o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, cMf = cM.hi;");
   if (mx && any_plog) o("const float lnPf = lnP.hi;");
-  if (!rop && !mx) {
+  if (!rop && !mx && bounded) {
+    o("const float lnTf = lnT.hi, iTf = iT.hi, Tf = Td.hi, lnPRTf = lnPRT.hi, lncMf = __logf(cM.hi);");
+    o("float U = -1.0e30f;");
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+      const DfClass& d = cls[ci];
+      const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+      const int NF = fo ? 7 : tb ? 3 : 2;
+      o("{");
+      ++o.ind;
+      prologue(d, (int)ci);
+      o("#pragma unroll 1");
+      o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
+      prefetch(d);
+      o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+      o("  const float4 f0 = f[0], f1 = f[1];");
+      o(d.kconst ? "  float b = f0.x;" : "  float b = fmaf(f0.z, lnTf, fmaf(f1.x, iTf, f0.x));");
+      if (d.kind == Kind::ThreeBody) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  b += e.y < 0 ? sv[kx_effd[e.x].k].x : lncMf + f1.z;");
+      } else if (fo) {
+        o("  const float4 f2 = f[2], f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+        o("  // ln F <= max(0, ln F_cent) (Troe); ln d + e ln T + max(0, ln base) (SRI)");
+        if (d.blend == Blend::Troe)
+          o("  const float lf = fmaxf(0.0f, __logf(f4.x * __expf(Tf * f5.x) + f4.z * __expf(Tf * f5.z) + __expf(f6.x * iTf)));");
+        else if (d.blend == Blend::Sri)
+          o("  const float lf = f5.z + f6.x * lnTf + fmaxf(0.0f, __logf(f4.x * __expf(f4.z * iTf) + __expf(Tf * f5.x)));");
+        else
+          o("  const float lf = 0.0f;");
+        if (d.kind == Kind::ChemAct) o("  b = fmaf(f3.x, lnTf, fmaf(f3.z, iTf, f2.z)) + lf;");
+        else o("  b += lf;");
+      } else if (d.kind == Kind::Plog) {
+        o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+        o("  const float* t = kx_plogf + 8 * e.x;");
+        o("  b = -1.0e30f;");
+        o("  for (int j = 0; j < e.y; ++j) b = fmaxf(b, fmaf(t[8 * j + 4], lnTf, fmaf(t[8 * j + 6], iTf, t[8 * j + 2])));");
+      }
+      for (int j = 0; j < d.nre; ++j) o(fmt("  b += v%d.x;", j));
+      if (d.rev) {
+        const int dn = d.npr - d.nre;
+        std::string s = dn == 0 ? std::string("0.0f") : fmt("%s * lnPRTf", F(-dn).c_str());
+        for (int j = 0; j < d.nre; ++j) s += fmt(" - v%d.z", j);
+        for (int j = d.nre; j < d.nre + d.npr; ++j) s += fmt(" + v%d.z", j);
+        o("  b += fmaxf(" + s + ", 0.0f);");
+      }
+      o("  U = fmaxf(U, b);");
+      advance(d);
+      o("}");
+      --o.ind;
+      o("}");
+      c.fp32 += d.rx.size() * (8.0 + 2 * (d.nre + d.npr));
+    }
+    o("// largest scaled rate near 2^63.5; |S| < 2^11 keeps S ln2 exact to the float-pair precision");
+    o("const int S = kx_rint(fminf(fmaxf(U * KX_LOG2E_F, -1000.0f), 1000.0f)) - 63;");
+    o("const float lnSf = __fmul_rn(kx_i2f(S), 0.693147182f);   // S ln2 for the range tests of the scaled exponential");
+  }
+
+  if (!rop && !mx && !bounded) {
     // the state's scale 2^-S: set by its first rate (scaled to 2^62) and raised to a later rate (to
     // 2^62 again), with every accumulator rescaled, when that rate would land above 2^96.  The largest
     // scaled rate thus sits between 2^62 and 2^97, a running sum stays below ~2^116, and float pairs keep
@@ -1903,6 +1966,9 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
           c.fp32 += d.rx.size() * 4;
         } else {
+          if (bounded) {
+            o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S (the products and sums after it take hi + lo as is)");
+          } else {
           o("  int ex;");
           o("  kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex (products and sums after it take hi + lo as is)");
           o("  if (ex > S + 96) {   // the state's first rate, or one 2^34 above its scale's anchor: raise the scale");
@@ -1915,6 +1981,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  }");
           o("  { const int d = ex - S; const float sc = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f; "
             "q = kx_mk(__fmul_rn(q.hi, sc), __fmul_rn(q.lo, sc)); }   // q 2^(ex - S)");
+          }
         }
         o("  if (sf) q = kx_df_neg(q);");
         if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul_u(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
