@@ -180,7 +180,12 @@ kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const doub
 /* Vector-Jacobian product of the production rates at fixed p: for each
  * point, gT = sum_k v_k d wdot_k/dT and gY[j] = sum_k v_k d wdot_k/dY_j,
  * with v[N_s][ld] and gY[N_s][ld].  The paper lists the analytical
- * Jacobian as future work (Sec. 4); this is its adjoint form.  FP64. */
+ * Jacobian as future work (Sec. 4); this is its adjoint form.  Float64
+ * accuracy: by default double-float arithmetic on the float32 pipe, each
+ * derivative term formed from the log-space rates (so an absent species,
+ * Y_k = 0, keeps its exact derivative) and accumulated under a running
+ * power-of-two scale of its own; kx_options.rates_arith = 1 selects the
+ * native float64 kernel.  One thread per point. */
 kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                   const double* v, double* gT, double* gY, int64_t n, void* stream);
 

@@ -515,6 +515,43 @@ __device__ __forceinline__ kx_df kx_df_exp_m(kx_df x, int& p) {
   p = k >> 8;
   return kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
 }
+// A running sum as a float pair under its own scale 2^-s, 16 bytes (one load and one store).
+struct __align__(16) kx_acc { float hi, lo; int s, pad; };
+__device__ __forceinline__ void kx_acc_add(kx_df& acc, int& s, kx_df m, int e);
+__device__ __forceinline__ void kx_acc_add(kx_acc& a, kx_df m, int e) {
+  kx_acc t = a;
+  kx_df v = kx_mk(t.hi, t.lo);
+  int s = t.s;
+  kx_acc_add(v, s, m, e);
+  t.hi = v.hi; t.lo = v.lo; t.s = s;
+  a = t;
+}
+// acc 2^s += m 2^e for a running sum kept as a float pair under its own
+// scale 2^-s (s = -100000: empty).  m is first brought to [1, 2) (its power
+// of two moved into e); a term that would land above 2^96 raises the scale
+// so that it sits at 2^62 (the sum rescaled by the exact power of two); a
+// term under 2^-126 of the scale drops out; inf and nan propagate.
+__device__ __forceinline__ void kx_acc_add(kx_df& acc, int& s, kx_df m, int e) {
+  const float ah = fabsf(m.hi);
+  if (!(ah < KX_INF_F)) { acc = kx_mk(m.hi, 0.0f); if (s < e) s = e; return; }
+  if (ah == 0.0f) return;
+  const int eh = max((int)((__float_as_uint(ah) >> 23) & 0xffu) - 127, -126);
+  const int h1 = eh >> 1, h2 = eh - h1;   // 2^-eh in two exact steps (|h1|, |h2| <= 64)
+  const float n1 = __int_as_float((127 - h1) << 23), n2 = __int_as_float((127 - h2) << 23);
+  m = kx_mk(__fmul_rn(__fmul_rn(m.hi, n1), n2), __fmul_rn(__fmul_rn(m.lo, n1), n2));
+  e += eh;
+  if (e > s + 96) {
+    const int d = s - (e - 62);
+    const float f = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f;
+    acc = kx_mk(__fmul_rn(acc.hi, f), __fmul_rn(acc.lo, f));
+    s = e - 62;
+  }
+  const int d = e - s;
+  if (d >= -126) {
+    const float sc = __int_as_float((d + 127) << 23);
+    acc = kx_df_add_u(acc, kx_mk(__fmul_rn(m.hi, sc), __fmul_rn(m.lo, sc)));
+  }
+}
 // Element k of a per-thread vector kept in global scratch at stride s.
 template <typename V> struct kx_strided {
   V* p;
@@ -2239,6 +2276,368 @@ void emit_vjp64(Out& o, const Mechanism& m, OpCounts& c) {
     o(fmt("gY_[(long long)%d * ld + i] = fC * (%s - gavg) * %s;", k, used[k] ? fmt("gC_%d", k).c_str() : "0.0", D(1.0 / m.W[k]).c_str()));
 }
 
+// Vector-Jacobian product of the production rates in double-float
+// arithmetic on the float32 pipe (float64 accuracy), thread per state, one
+// loop per reaction class over the forward kernel's tables.  With
+// a_i = sum_k nu_ki v_k, v^T wdot = sum_i a_i q_i, so each reaction adds a_i
+// dq_i to the adjoints of its own inputs; every term is formed from the
+// log-space rates as a float-pair mantissa times a power of two:
+//   d/dT (at fixed C, G/RT):  a_i c_i ((R_f - R_r) dln k_f/dT - dn R_r / T),
+//   d/d(G_k/RT):             -a_i c_i nu_k R_r,
+//   d/dC_k:                  a_i c_i (nu'_k R_f - nu''_k R_r) / C_k, one term
+//                            exp(ln |R| - ln |C_k|) per entry (so absent
+//                            species, C_k = 0, keep their exact derivative),
+//   d/d[X] (third body):     a_i (R_f - R_r) (times dln k_f/d[X] for falloff).
+// The rates span hundreds of decades and R/C_k more, so every accumulator
+// carries its own running power-of-two scale (kx_acc_add).  The chain to
+// (T, Y) is closed per state in float64: Gibbs-Helmholtz for G_k/RT(T),
+// C_k = [M] y_k / sigma with [M] = p/(R T).
+void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
+  const int ns = m.ns;
+  std::vector<DfClass> cls = emit_class_tables(g, m);
+  // H/RT coefficients per species and NASA range: a0, a1/2, a2/3, a3/4, a4/5 (in T) and a5 (over T)
+  {
+    std::string hc, iwd;
+    for (int k = 0; k < ns; ++k) {
+      for (int rg = 0; rg < 2; ++rg) {
+        const double* a = rg == 0 ? &m.a_lo[7 * k] : &m.a_hi[7 * k];
+        const double h[6] = {a[0], a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0, a[5]};
+        for (int j = 0; j < 6; ++j) hc += D(h[j]) + ",";
+      }
+      iwd += D(1.0 / m.W[k]) + ",";
+    }
+    g(fmt("__device__ const double kx_hrt[%d] = {%s0.0};", 12 * ns + 1, hc.c_str()));
+    std::string hf;
+    for (int k = 0; k < ns; ++k)
+      for (int rg = 0; rg < 2; ++rg) {
+        const double* a = rg == 0 ? &m.a_lo[7 * k] : &m.a_hi[7 * k];
+        const double h[8] = {a[0], a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0, a[5], 0.0, 0.0};
+        for (int j = 0; j < 8; ++j) hf += fpair(h[j]) + ",";
+      }
+    g(fmt("__device__ const __align__(16) float kx_hcf[%d] = {%s0.0f};", 32 * ns + 4, hf.c_str()));
+    g(fmt("__device__ const double kx_iwd[%d] = {%s0.0};", ns + 1, iwd.c_str()));
+  }
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  o("#define KX_PF(p) kx_mk((p)[0], (p)[1])");
+  o("const kx_df Td = kx_d2df_i(T);");
+  o("const kx_df lnT = kx_df_log_d(T);");
+  o("const kx_df iT = kx_df_div(kx_mk(1.0f, 0.0f), Td);");
+  o("const kx_df iT2 = kx_df_mul(iT, iT);");
+  if (any_plog) o("const kx_df lnP = kx_df_log_d(P);");
+  o(fmt("const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
+  o(fmt("const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
+  o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k = G_k/RT + ln |C_k| (pair)}", ns));
+  o(fmt("float2 yv[%d];   // Y_k/W_k (pair)", ns));
+  o(fmt("float4 vh[%d];   // {cotangent v_k (pair), H_k/RT (pair)}", ns));
+  o(fmt("float4 ic[%d];   // 1/|C_k| = {mantissa (pair), power of two (int bits), 0}", ns));
+  o(fmt("kx_acc gc[%d];   // adjoints of C_k, each a float pair under its own scale 2^-s", ns));
+  o("kx_df gTa = kx_mk(0.0f, 0.0f), gMa = kx_mk(0.0f, 0.0f);   // adjoints of T (fixed C) and of [M]");
+  o("int sT = -100000, sM = -100000;");
+  o("kx_df sig = kx_mk(0.0f, 0.0f);");
+  o(fmt("for (int k = 0; k < %d; ++k) sig = kx_df_fma(kx_d2df_i(Y_[(long long)k * ld + i]), KX_PF(kx_iwf + 2 * k), sig);", ns));
+  o("if (!(sig.hi > 0.0f && sig.hi < KX_INF_F)) KX_BAD_POINT");
+  o("const kx_df fC = kx_df_div(cM, sig);");
+  o("const kx_df lnfC = kx_df_log(fC);");
+  o("const long long Tb = __double_as_longlong(T);");
+  const int nw = (ns + 63) / 64;
+  for (int q = 0; q < nw; ++q) o(fmt("unsigned long long nm%d = 0ull;", q));
+  {
+    std::string sel = fmt("nm%d", nw - 1);
+    for (int q = nw - 2; q >= 0; --q) sel = fmt("((k) < %d ? nm%d : %s)", 64 * (q + 1), q, sel.c_str());
+    o("#define KX_NEG(k) ((int)((" + sel + " >> ((k) & 63)) & 1ull))");
+  }
+  o(fmt("for (int k = 0; k < %d; ++k) {", ns));
+  o("  const double Yk = Y_[(long long)k * ld + i];");
+  o("  const long long yb = __double_as_longlong(Yk) & 0x7fffffffffffffffLL;");
+  o("  kx_df l = kx_mk(-700.0f, 0.0f);   // ln |C_k|, floored at -700 (absent species)");
+  o("  if (yb >= 0x0010000000000000LL && yb < 0x7ff0000000000000LL) {");
+  o("    l = kx_df_add(kx_df_log_d(__longlong_as_double(yb)), kx_df_sub(lnfC, KX_PF(kx_lwf + 2 * k)));");
+  o("    if (!(l.hi > -700.0f)) l = kx_mk(-700.0f, 0.0f);");
+  o("  }");
+  {
+    std::string s = "  if (Yk < 0.0) {";
+    for (int q = 0; q < nw; ++q) s += fmt(" %sif ((k >> 6) == %d) nm%d |= 1ull << (k & 63);", q ? "else " : "", q, q);
+    o(s + " }");
+  }
+  o("  const float* a = kx_gcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("  kx_df gk = kx_df_fma(KX_PF(a + 8), Td, KX_PF(a + 6));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 4));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 2));");
+  o("  gk = kx_df_fma(gk, Td, KX_PF(a + 0));");
+  o("  gk = kx_df_fma(KX_PF(a + 10), iT, gk);");
+  o("  gk = kx_df_fma(KX_PF(a + 12), lnT, gk);");
+  o("  const kx_df mk_ = kx_df_add(gk, l);");
+  o("  sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
+  o("  const kx_df yk = kx_df_mul(kx_d2df_i(Yk), KX_PF(kx_iwf + 2 * k));");
+  o("  yv[k] = make_float2(yk.hi, yk.lo);");
+  o("  const kx_df vk = kx_d2df_i(V_[(long long)k * ld + i]);");
+  o("  const float* hc = kx_hcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("  kx_df hk = kx_df_fma(KX_PF(hc + 8), Td, KX_PF(hc + 6));");
+  o("  hk = kx_df_fma(hk, Td, KX_PF(hc + 4));");
+  o("  hk = kx_df_fma(hk, Td, KX_PF(hc + 2));");
+  o("  hk = kx_df_fma(hk, Td, KX_PF(hc + 0));");
+  o("  hk = kx_df_fma(KX_PF(hc + 10), iT, hk);   // H_k/RT");
+  o("  vh[k] = make_float4(vk.hi, vk.lo, hk.hi, hk.lo);");
+  o("  { int e; const kx_df mi = kx_df_exp_m(kx_df_neg(l), e); ic[k] = make_float4(mi.hi, mi.lo, __int_as_float(e), 0.0f); }");
+  o("  gc[k] = kx_acc{0.0f, 0.0f, -100000, 0};");
+  o("}");
+  c.fp32 += 40 + 45 + kDfDiv + 3 * kDfMul + kDfAdd + kDfDiv + kDfLog;
+  c.fp32 += ns * (12 + kDfFma) + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd + kDfMul);
+
+  static const char* xyzw[4] = {"x", "y", "z", "w"};
+  auto comp = [&](const char* base, int j) { return fmt("%s%d.%s", base, j / 4, xyzw[j % 4]); };
+  const std::string il10 = DFc(1.0 / std::log(10.0));
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    const DfClass& d = cls[ci];
+    const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const int NF = fo ? 7 : tb ? 3 : 2;
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    const double NC = (double)d.rx.size();
+    o(fmt("{   // class %d: %d reactions, %d reactant and %d product entries", (int)ci, (int)d.rx.size(), d.nre, d.npr));
+    ++o.ind;
+    o("#pragma unroll 1");
+    o(fmt("for (int r = 0; r < %d; ++r) {", (int)d.rx.size()));
+    o(fmt("  const int4* sp4 = (const int4*)kx_s%d + %d * r;", (int)ci, P / 4));
+    for (int q = 0; q < P / 4; ++q) o(fmt("  const int4 c%d = sp4[%d];", q, q));
+    for (int j = 0; j < E; ++j) o(fmt("  const int k%d = %s & 0xffff;", j, comp("c", j).c_str()));
+    for (int j = 0; j < E; ++j) o(fmt("  const float4 v%d = sv[k%d];", j, j));
+    o(fmt("  const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+    o("  const float4 f0 = f[0], f1 = f[1];");
+    o("  // a = sum_k nu_k v_k over the reaction's species (net coefficients on first entries)");
+    o("  // and, for the chemical potentials' temperature dependence, dh = sum_k nu_k H_k/RT");
+    o("  kx_df av = kx_mk(0.0f, 0.0f), dh = kx_mk(0.0f, 0.0f);");
+    for (int j = 0; j < E; ++j)
+      o(fmt("  { const unsigned cj = (unsigned)%s & 0xffff0000u; if (cj != 0u) { const float4 w = vh[k%d]; const float cf = __uint_as_float(cj); "
+            "av = kx_df_add_u(av, kx_df_mulf(kx_mk(w.x, w.y), cf)); dh = kx_df_add_u(dh, kx_df_mulf(kx_mk(w.z, w.w), cf)); } }",
+            comp("c", j).c_str(), j));
+    o("  const kx_df lA = kx_mk(f0.x, f0.y), bA = kx_mk(f0.z, f0.w), nEA = kx_mk(f1.x, f1.y);");
+    o("  kx_df lk = kx_df_fma(bA, lnT, kx_df_fma(nEA, iT, lA));");
+    o("  kx_df dT = kx_df_mul(iT, kx_df_fma(kx_df_neg(nEA), iT, bA));   // dln k/dT = beta/T + E/T^2");
+    c.fp32 += NC * (E * (kDfAdd + kDfMulf) + 2 * kDfFma + kDfMul + kDfFma);
+    std::string aq = "av";
+    if (tb) {
+      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+      o("  const float4 f2 = f[2];");
+      o("  kx_df X;   // [X] = eff_default C_M + (C_M/sigma) sum_e (eff_e - eff_default) Y_e/W_e");
+      o("  if (e.y < 0) {");
+      o("    const int kc = kx_effd[e.x].k;");
+      o("    X = kx_df_mul(kx_mk(yv[kc].x, yv[kc].y), fC);");
+      o("  } else {");
+      o("    kx_df t = kx_mk(0.0f, 0.0f);");
+      o("    for (int j = 0; j < e.y; ++j) {");
+      o("      const kx_effd_t q = kx_effd[e.x + j];");
+      o("      t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_mk(yv[q.k].x, yv[q.k].y), t);");
+      o("    }");
+      o("    X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+      o("  }");
+      c.fp32 += NC * (kDfFma + kDfMul + 3 * kDfFma);
+    }
+    if (d.kind == Kind::ThreeBody) {
+      o("  const kx_df aq = kx_df_mul(av, X);");
+      aq = "aq";
+      c.fp32 += NC * kDfMul;
+    }
+    if (fo) {
+      o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+      o("  const kx_df b0 = kx_mk(f3.x, f3.y), nE0 = kx_mk(f3.z, f3.w);");
+      o("  const kx_df lk0 = kx_df_fma(b0, lnT, kx_df_fma(nE0, iT, kx_mk(f2.z, f2.w)));");
+      o("  const kx_df dk0 = kx_df_mul(iT, kx_df_fma(kx_df_neg(nE0), iT, b0));");
+      o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+      o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+      o("  // with e = e^-|ln Pr|: Pr/(1+Pr) and 1/(1+Pr) as e/(1+e) and 1/(1+e) (Pr < 1) or the other way round");
+      o("  const bool small = lnPr.hi < 0.0f;");
+      o("  const kx_df ee = kx_df_exp_n(small ? lnPr : kx_df_neg(lnPr));");
+      o("  const kx_df i1e = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_add(kx_mk(1.0f, 0.0f), ee));");
+      o("  const kx_df e1e = kx_df_mul(ee, i1e);");
+      o("  const kx_df P1 = small ? e1e : i1e, P0 = small ? i1e : e1e;   // Pr/(1+Pr), 1/(1+Pr)");
+      o("  const kx_df l1p = kx_df_log1p(ee);");
+      o("  kx_df lnF = kx_mk(0.0f, 0.0f), dFl = kx_mk(0.0f, 0.0f), dFT = kx_mk(0.0f, 0.0f);   // ln F, dln F/dln Pr, dln F/dT");
+      if (d.blend == Blend::Troe) {
+        o("  {   // Troe: F_cent = (1-alpha) e^(-T/T***) + alpha e^(-T/T*) + e^(-T**/T)");
+        o("    const kx_df p0 = kx_mk(f4.x, f4.y), p1 = kx_mk(f4.z, f4.w), p2 = kx_mk(f5.x, f5.y), p3 = kx_mk(f5.z, f5.w), p4 = kx_mk(f6.x, f6.y);");
+        o("    const kx_df e3 = kx_df_mul(p0, kx_df_exp_s(kx_df_mul(Td, p2)));");
+        o("    const kx_df e1 = kx_df_mul(p1, kx_df_exp_s(kx_df_mul(Td, p3)));");
+        o("    const kx_df e2 = kx_df_exp_s(kx_df_mul(p4, iT));");
+        o("    const kx_df Fc = kx_df_add(kx_df_add(e3, e1), e2);");
+        o("    const kx_df dFc = kx_df_fma(e3, p2, kx_df_fma(e1, p3, kx_df_neg(kx_df_mul(kx_df_mul(e2, p4), iT2))));");
+        o(fmt("    const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+        o(fmt("    const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+        o(fmt("    const kx_df nn = kx_df_fma(%s, lFc, %s);", DFc(-1.27).c_str(), DFc(0.75).c_str()));
+        o(fmt("    const kx_df den = kx_df_fma(%s, xx, nn);", DFc(-0.14).c_str()));
+        o("    const kx_df iden = kx_df_div(kx_mk(1.0f, 0.0f), den);");
+        o("    const kx_df ff = kx_df_mul(xx, iden);");
+        o("    const kx_df g1 = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));");
+        o(fmt("    lnF = kx_df_mul(kx_df_mul(%s, lFc), g1);", DFc(std::log(10.0)).c_str()));
+        o("    const kx_df h2 = kx_df_mul(kx_df_mul(kx_df_mul(kx_mk(-2.0f, 0.0f), ff), kx_df_mul(g1, g1)), lFc);");
+        o("    const kx_df id2 = kx_df_mul(iden, iden);");
+        o("    dFl = kx_df_mul(kx_df_mul(h2, nn), id2);");
+        o(fmt("    dFT = kx_df_mul(kx_df_fma(kx_df_mul(h2, kx_df_fma(%s, den, kx_df_mul(%s, xx))), id2, g1), kx_df_div(dFc, Fc));",
+              DFc(-0.67).c_str(), DFc(1.27 - 0.14 * 0.67).c_str()));
+        o("  }");
+        c.fp32 += NC * (3 * (kDfMul + kDfExp) + 2 * kDfMul + 2 * kDfAdd + 3 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 3 * kDfDiv + 12 * kDfMul);
+      } else if (d.blend == Blend::Sri) {
+        o("  {   // SRI: F = d T^e (a e^(-b/T) + e^(-T/c))^X, X = 1/(1 + log10^2 Pr)");
+        o("    const kx_df pa = kx_mk(f4.x, f4.y), pnb = kx_mk(f4.z, f4.w), pnc = kx_mk(f5.x, f5.y), pld = kx_mk(f5.z, f5.w), pe = kx_mk(f6.x, f6.y);");
+        o(fmt("    const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+        o("    const kx_df Xs = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)));");
+        o("    const kx_df ea = kx_df_mul(pa, kx_df_exp_s(kx_df_mul(pnb, iT)));");
+        o("    const kx_df eb = kx_df_exp_s(kx_df_mul(Td, pnc));");
+        o("    const kx_df base = kx_df_add(ea, eb);");
+        o("    const kx_df lnb = kx_df_log(base);");
+        o("    lnF = kx_df_add(pld, kx_df_fma(pe, lnT, kx_df_mul(Xs, lnb)));");
+        o(fmt("    dFl = kx_df_mul(kx_df_mul(kx_df_mul(kx_mk(-2.0f, 0.0f), lPr), kx_df_mul(Xs, Xs)), kx_df_mul(lnb, %s));", il10.c_str()));
+        o("    // dln F/dT = e/T + X (a b e^(-b/T)/T^2 - e^(-T/c)/c)/base, with pnb = -b and pnc = -1/c");
+        o("    dFT = kx_df_fma(pe, iT, kx_df_mul(Xs, kx_df_div(kx_df_fma(kx_df_neg(kx_df_mul(ea, pnb)), iT2, kx_df_mul(eb, pnc)), base)));");
+        o("  }");
+        c.fp32 += NC * (2 * (kDfMul + kDfExp) + 14 * kDfMul + 3 * kDfDiv + kDfLog + 4 * kDfFma + 2 * kDfAdd);
+      }
+      if (d.kind == Kind::Falloff) {
+        o("  lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));   // k_inf Pr/(1+Pr) F");
+        o("  const kx_df dP = kx_df_add(P0, dFl);   // dln k_f/dln Pr");
+        o("  dT = kx_df_add(kx_df_fma(kx_df_sub(dk0, dT), dP, dT), dFT);");
+      } else {
+        o("  lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));   // k_0 F/(1+Pr)");
+        o("  const kx_df dP = kx_df_sub(dFl, P1);");
+        o("  dT = kx_df_add(kx_df_fma(kx_df_sub(dk0, dT), dP, dk0), dFT);");
+      }
+      o("  const kx_df dX = kx_df_div(dP, X);   // dln k_f/d[X]");
+      c.fp32 += NC * (2 * kDfFma + kDfMul + kDfAdd + kDfLog + kDfExp + 2 * kDfDiv + kDfMul + kDfLog + 6 * kDfAdd + kDfFma);
+    } else if (d.kind == Kind::Plog) {
+      o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
+      o("  const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+      o("  const long long Pb = __double_as_longlong(P);");
+      o("  // ln k and dln k/dT of table entry u: ln A + beta ln T - E/T, beta/T + E/T^2");
+      o("#define KX_PLK(u) kx_df_fma(KX_PF((u) + 4), lnT, kx_df_fma(KX_PF((u) + 6), iT, KX_PF((u) + 2)))");
+      o("#define KX_PLD(u) kx_df_mul(iT, kx_df_fma(kx_df_neg(KX_PF((u) + 6)), iT, KX_PF((u) + 4)))");
+      o("  if (Pb <= tp[0]) { lk = KX_PLK(t); dT = KX_PLD(t); }");
+      o("  else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = KX_PLK(u); dT = KX_PLD(u); }");
+      o("  else {");
+      o("    int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+      o("    const float* u = t + 8 * j;");
+      o("    const kx_df w = kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u)));");
+      o("    const kx_df l1 = KX_PLK(u), l2 = KX_PLK(u + 8), d1 = KX_PLD(u), d2 = KX_PLD(u + 8);");
+      o("    lk = kx_df_fma(kx_df_sub(l2, l1), w, l1);");
+      o("    dT = kx_df_fma(kx_df_sub(d2, d1), w, d1);");
+      o("  }");
+      o("#undef KX_PLK");
+      o("#undef KX_PLD");
+      c.fp32 += NC * (8 * kDfFma + 4 * kDfMul + 5 * kDfAdd + kDfDiv);
+    }
+    // log-space rates and the net rate
+    o("  kx_df lf = lk;");
+    for (int j = 0; j < d.nre; ++j) o(fmt("  lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
+    std::string sfx = "0", srx = "0";
+    for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+    for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+    o("  const int sf = " + sfx + ";");
+    o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f), lr = kx_mk(0.0f, 0.0f);");
+    o("  int sq = sf;   // sign of R_f - R_r");
+    c.fp32 += NC * (d.nre * kDfAdd);
+    if (d.rev) {
+      const int dn = d.npr - d.nre;
+      o("  const int sr = " + srx + ";");
+      std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+      o("  kx_df dl = " + first + ";   // ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T))");
+      for (int j = 1; j < E; ++j)
+        o(fmt("  dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+      if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
+      else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
+      o("  lr = kx_df_add_u(lf, dl);");
+      o("  {");
+      o("    const bool rv = dl.hi > 0.0f;");
+      o("    if (rv) L = lr;");
+      o("    const kx_df ex = kx_df_exp_n(rv ? kx_df_neg(dl) : dl);");
+      o("    const float pm = sf == sr ? -1.0f : 1.0f;");
+      o("    const kx_df s1 = kx_qts(1.0f, pm * ex.hi);");
+      o("    fac = kx_mk(s1.hi, __fmaf_rn(pm, ex.lo, s1.lo));");
+      o("    if (sf == sr) sq = sf ^ (int)rv;");
+      o("  }");
+      c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
+      // R_r = sign e^(lr): exponent and signed mantissa
+      o("  int er;");
+      o("  kx_df mr = kx_df_exp_m(lr, er);");
+      o("  if (sr) mr = kx_df_neg(mr);");
+      c.fp32 += NC * kDfExp;
+      (void)dn;
+    }
+    o("  int eq;");
+    o("  kx_df mq = kx_df_mul_u(kx_df_exp_m(L, eq), fac);   // R_f - R_r = mq 2^eq");
+    o("  if (sq) mq = kx_df_neg(mq);");
+    c.fp32 += NC * (kDfExp + kDfMul);
+    // d/dT at fixed concentrations and chemical potentials
+    o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mq), eq);", aq.c_str()));
+    c.fp32 += NC * (2 * kDfMul + 20);
+    if (d.rev) {
+      const int dn = d.npr - d.nre;
+      o("  // d/dT through R_r at fixed C: a c R_r / T (sum_k nu_k H_k/RT - dn), the first part being the");
+      o("  // chemical potentials' -dG_k/RT/dT = H_k/(R T^2) (Gibbs-Helmholtz) times d q/d(G_k/RT) = -c nu_k R_r");
+      o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(kx_df_mul_u(%s, mr), iT), %s), er);", aq.c_str(),
+            dn != 0 ? fmt("kx_df_add(dh, kx_mk(%s, 0.0f))", F(-dn).c_str()).c_str() : "dh"));
+      c.fp32 += NC * (3 * kDfMul + kDfAdd + 20);
+    }
+    // d/dC_k: one term per entry, R/C_k with the sign of R/C_k.  As |R| = m 2^e and 1/|C_k| = m' 2^e'
+    // (per state), a product of mantissas; where |R| itself is below float64 (ln |R| <= -740: an absent
+    // reactant beside other small factors) the term is formed in log space, exp(ln |R| - ln |C_k|).
+    std::string lowc = "lf.hi <= -740.0f";
+    if (d.rev) lowc += " || lr.hi <= -740.0f";
+    o("  int ef;");
+    o("  kx_df mf = kx_df_exp_m(lf, ef);   // |R_f| = mf 2^ef");
+    c.fp32 += NC * kDfExp;
+    o("  if (" + lowc + ") {");
+    for (int j = 0; j < E; ++j) {
+      const bool reac = j < d.nre;
+      if (!reac && !d.rev) continue;
+      o(fmt("    { int et; kx_df mt = kx_df_exp_m(kx_df_sub(%s, kx_mk(v%d.x, v%d.y)), et);", reac ? "lf" : "lr", j, j));
+      o(fmt("      if (%s ^ KX_NEG(k%d)) mt = kx_df_neg(mt);", reac ? "sf" : "sr", j));
+      o(fmt("      kx_acc_add(gc[k%d], kx_df_mul_u(%s, mt), et); }", j, reac ? aq.c_str() : ("kx_df_neg(" + aq + ")").c_str()));
+    }
+    o("  } else {");
+    o(fmt("    const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
+    if (d.rev) o(fmt("    const kx_df ar = kx_df_mul_u(%s, mr);   // mr carries the sign of R_r", ("kx_df_neg(" + aq + ")").c_str()));
+    for (int j = 0; j < E; ++j) {
+      const bool reac = j < d.nre;
+      if (!reac && !d.rev) continue;
+      o(fmt("    { const float4 q = ic[k%d]; kx_df mt = kx_df_mul_u(%s, kx_mk(q.x, q.y)); if (KX_NEG(k%d)) mt = kx_df_neg(mt);", j,
+            reac ? "af" : "ar", j));
+      o(fmt("      kx_acc_add(gc[k%d], mt, %s + __float_as_int(q.z)); }", j, reac ? "ef" : "er"));
+    }
+    o("  }");
+    c.fp32 += NC * (2 * kDfMul + E * (kDfMul + 20));
+    // third-body adjoint a (R_f - R_r) (times dln k_f/d[X] in a falloff), spread over [M] and the listed species
+    if (tb) {
+      o(d.kind == Kind::ThreeBody ? "  const kx_df gX = kx_df_mul_u(av, mq);" : "  const kx_df gX = kx_df_mul_u(kx_df_mul_u(av, mq), dX);");
+      o("  if (e.y < 0) {");
+      o("    const int kc = kx_effd[e.x].k;");
+      o("    kx_acc_add(gc[kc], gX, eq);");
+      o("  } else {");
+      o("    kx_acc_add(gMa, sM, kx_df_mul_u(kx_mk(f2.x, f2.y), gX), eq);");
+      o("    for (int j = 0; j < e.y; ++j) {");
+      o("      const kx_effd_t q = kx_effd[e.x + j];");
+      o("      kx_acc_add(gc[q.k], kx_df_mul_u(kx_mk(q.ahi, q.alo), gX), eq);");
+      o("    }");
+      o("  }");
+      c.fp32 += NC * (2 * kDfMul + 4 * (kDfMul + 20));
+    }
+    o("}");
+    --o.ind;
+    o("}");
+  }
+  // ---- close the chain in float64
+  o("const double iTd = 1.0 / T;");
+  o("const double cMd = kx_df2d(cM), fCd = kx_df2d(fC);");
+  o("const double gT = kx_df2d_s(gTa, sT);");
+  o("double gCX = 0.0;   // sum_k gC_k C_k");
+  o(fmt("for (int k = 0; k < %d; ++k) gCX = fma(kx_df2d_s(kx_mk(gc[k].hi, gc[k].lo), gc[k].s), fCd * Y_[(long long)k * ld + i] * kx_iwd[k], gCX);", ns));
+  o("const double gM = kx_df2d_s(gMa, sM) + gCX / cMd;");
+  o("gT_[i] = fma(-gM * cMd, iTd, gT);   // [M] = p/(R T)");
+  o("const double gavg = gCX / cMd;");
+  o(fmt("for (int k = 0; k < %d; ++k) gY_[(long long)k * ld + i] = fCd * (kx_df2d_s(kx_mk(gc[k].hi, gc[k].lo), gc[k].s) - gavg) * kx_iwd[k];", ns));
+  c.fp64 += ns * 6 + 12;
+  c.fp32 += ns * 5 * kDfFma;
+}
+
 // ------------------------------------------------------------------ thermo
 // Mixture cp and h in float-pair arithmetic on the float32 pipe (float64
 // accuracy; the NASA polynomials need no float64 pipe): per species two
@@ -3303,7 +3702,8 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
     case KernelKind::Vjp:
       outs = "const double* __restrict__ V_, double* __restrict__ gT_, double* __restrict__ gY_";
       nan_fill = fmt("gT_[i] = KX_NAN; for (int k = 0; k < %d; ++k) gY_[(long long)k * ld + i] = KX_NAN;", m.ns);
-      emit_vjp64(body, m, c);
+      if (opt.rates_arith == 1) emit_vjp64(body, m, c);
+      else emit_vjp_df(body, globals, m, c);
       break;
   }
   std::ostringstream s;
@@ -3313,17 +3713,18 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
                         ((!opt.mixed && (opt.rates_arith != 1 || opt.scratch)) || (opt.mixed && opt.rates_mode == 0));
   const bool table_sel = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
   const bool mixed_unrolled = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && opt.mixed && !table_sel && !df_rates;
-  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates && !mixed_unrolled;
+  const bool vjp_df = kind == KernelKind::Vjp && opt.rates_arith != 1;
+  const bool t64 = kind != KernelKind::Thermo && kind != KernelKind::Transport && !df_rates && !mixed_unrolled && !vjp_df;
   // table-driven float64 rate kernels take their exponentials from kx_exp_r (error ~2e-12 against
   // a 1e-10 bar); the unrolled ones keep kx_exp, whose short inline sequence keeps compile time
   // of the straight-line code in check
   const bool table_rates = opt.rates_mode == 2 || (opt.rates_mode == 0 && (m.ns > 64 || m.nr() > 400));
   const bool rates64 = (kind == KernelKind::Wdot || kind == KernelKind::Rop) && !opt.mixed && table_rates && !df_rates;
-  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates || mixed_unrolled ||
+  const bool tdf = (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 0) || rates64 || df_rates || mixed_unrolled || vjp_df ||
                    kind == KernelKind::Thermo;
   s << "#define KX_T64 " << (t64 || (kind == KernelKind::Transport && !opt.mixed && opt.tr_mode == 1)) << "\n";
   s << "#define KX_TDF " << tdf << "\n";
-  s << "#define KX_TDFR " << (df_rates || mixed_unrolled || kind == KernelKind::Thermo) << "\n";
+  s << "#define KX_TDFR " << (df_rates || mixed_unrolled || vjp_df || kind == KernelKind::Thermo) << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
@@ -3352,6 +3753,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   if (rreg == 0 && kind == KernelKind::Transport)
     rreg = opt.tr_layout != 3 ? 128 : (!opt.mixed && opt.tr_mode == 0 && opt.part == 1 && opt.diff_mode != 2) ? 80 : 64;
   if (rreg == 0 && kind == KernelKind::Thermo) rreg = 48;
+  if (rreg == 0 && vjp_df) rreg = 128;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;

@@ -20,10 +20,12 @@ def torch():
     return torch_cuda()
 
 
-@pytest.mark.parametrize("name,n", [("h2o2_9_21", 300), ("gri_53_325", 256)])
-def test_vjp_matches_oracle_jacobian(torch, name, n):
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("name,n", [("h2o2_9_21", 300), ("gri_53_325", 256), ("large_160_900", 64)])
+def test_vjp_matches_oracle_jacobian(torch, name, n, arith):
+    """arith 0: the double-float adjoint (default); 1: native float64."""
     T, p, Y = _states(name, n, start=1000)
-    mech = mechanism(name)
+    mech = mechanism(name, **({"rates_arith": 1} if arith else {}))
     rng = np.random.default_rng(7)
     v = rng.standard_normal((mech.n_species, n))
     Td, pd, Yd = to_device(torch, T, p, Y)
@@ -37,6 +39,34 @@ def test_vjp_matches_oracle_jacobian(torch, name, n):
         got = np.concatenate([[gT[i]], gY[:, i]])
         tol = 1e-9 * scale.max()
         assert np.all(np.abs(got - ref) <= tol + 1e-9 * scale), (i, np.max(np.abs(got - ref) / (scale + 1e-300)))
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_vjp_absent_and_negative_species(torch, arith):
+    """States with species absent (Y_k = 0 exactly, as in a fresh mixture) and
+    small negative mass fractions: the derivative with respect to an absent
+    species is finite and nonzero (d(k C_A C_B)/dC_A = k C_B); the double-float
+    adjoint forms each such term in log space per entry, so it must match the
+    oracle's dual-number Jacobian there too."""
+    name, n = "gri_53_325", 128
+    T, p, Y = _states(name, n, start=5000)
+    rng = np.random.default_rng(11)
+    Y[rng.random(Y.shape) < 0.25] = 0.0
+    neg = rng.random(Y.shape) < 0.05
+    Y[neg] = -1e-5 * rng.random(int(neg.sum()))
+    mech = mechanism(name, **({"rates_arith": 1} if arith else {}))
+    v = rng.standard_normal((mech.n_species, n))
+    Td, pd, Yd = to_device(torch, T, p, Y)
+    gT, gY = mech.production_rates_vjp(Td, pd, Yd, torch.tensor(v, device="cuda"))
+    gT, gY = gT.cpu().numpy(), gY.cpu().numpy()
+    assert np.all(np.isfinite(gT)) and np.all(np.isfinite(gY))
+    o = oracle(name)
+    for i in range(n):
+        J = o.jacobian(T[i], p[i], Y[:, i])
+        ref = v[:, i] @ J
+        scale = np.abs(v[:, i]) @ np.abs(J)
+        got = np.concatenate([[gT[i]], gY[:, i]])
+        assert np.all(np.abs(got - ref) <= 1e-9 * scale.max() + 1e-9 * scale), (i, np.max(np.abs(got - ref) / (scale + 1e-300)))
 
 
 def test_autograd_function_and_finite_differences(torch):
