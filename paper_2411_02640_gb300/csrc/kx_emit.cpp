@@ -3753,7 +3753,9 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   if (rreg == 0 && kind == KernelKind::Transport)
     rreg = opt.tr_layout != 3 ? 128 : (!opt.mixed && opt.tr_mode == 0 && opt.part == 1 && opt.diff_mode != 2) ? 80 : 64;
   if (rreg == 0 && kind == KernelKind::Thermo) rreg = 48;
-  if (rreg == 0 && vjp_df) rreg = 128;
+  // the double-float adjoint is bound by the latency of its local-memory vectors: residency wins
+  // (53/325, 2^18 states: 64 / 80 / 96 / 123 registers -> 6.26 / 7.16 / 7.33 / 8.58 ms)
+  if (rreg == 0 && vjp_df) rreg = 64;
   const int min_blocks = rreg > 0 ? std::max(1, 65536 / (rreg * opt.block)) : 0;
   s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block;
   if (min_blocks > 0) s << ", " << min_blocks;
