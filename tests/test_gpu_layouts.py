@@ -63,3 +63,25 @@ def test_automatic_choice_follows_the_batch_size():
         assert torch.equal(a, same.production_rates(Ts, ps, Ys)), n
         other = tps if same is wc else wc
         assert wdot_error(W, a.cpu().numpy(), other.production_rates(Ts, ps, Ys).cpu().numpy()).max() <= TOL
+
+
+@pytest.mark.parametrize("layout", [1, 2])
+def test_absent_and_negative_species_each_layout(layout):
+    """Absent species (Y_k = 0, the ln |C_k| floor) and small negative mass
+    fractions (signed concentration products) in both kernels, against the
+    oracle; a batch below the crossover so that the default would pick the
+    warp-cooperative kernel."""
+    torch = torch_cuda()
+    name, n = "gri_53_325", 777
+    m = synth.mechanism(name)
+    T, p, Y = synth.make_states(m.n_species, synth.STATE_SPECS[name], 4242, n)
+    rng = np.random.default_rng(23)
+    Y[rng.random(Y.shape) < 0.3] = 0.0
+    neg = rng.random(Y.shape) < 0.05
+    Y[neg] = -1e-4 * rng.random(int(neg.sum()))
+    mech = mechanism(name, rates_layout=layout)
+    Td, pd, Yd = to_device(torch, T, p, Y, ld=n + 5)
+    w = mech.production_rates(Td, pd, Yd)[:, :n].cpu().numpy()
+    assert np.all(np.isfinite(w))
+    err = wdot_error(np.array(mech.W), w, oracle(name).production_rates(T, p, Y))
+    assert err.max() <= TOL, f"max {err.max():.3e}"
