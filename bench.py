@@ -841,11 +841,17 @@ def run_profile_rates(args):
                 rates_arith=args.rates_arith, block=args.block, lazy=1)
     m = kx.Mechanism(synth.mechanism_file(args.mech, os.path.join(CACHE, "mech")), cache_dir=CACHE, **opts)
     T, p, Y = synth.make_states_torch(m.n_species, spec, args.points, seed=spec.seed)
-    w = m.production_rates(T, p, Y, precision=args.precision)
-    m.production_rates(T, p, Y, out=w, precision=args.precision)
+    if args.profile_call == "vjp":
+        v = torch.randn((m.n_species, args.points), dtype=torch.float64, device="cuda",
+                        generator=torch.Generator("cuda").manual_seed(1))
+        gT, w = m.production_rates_vjp(T, p, Y, v)
+        m.production_rates_vjp(T, p, Y, v, out=(gT, w))
+    else:
+        w = m.production_rates(T, p, Y, precision=args.precision)
+        m.production_rates(T, p, Y, out=w, precision=args.precision)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_rates": args.mech, "points": args.points, "options": opts, "precision": args.precision,
-                      "finite": bool(torch.isfinite(w).all())}), flush=True)
+    print(json.dumps({"profile_rates": args.mech, "call": args.profile_call, "points": args.points, "options": opts,
+                      "precision": args.precision, "finite": bool(torch.isfinite(w).all())}), flush=True)
 
 
 def main():
@@ -875,6 +881,8 @@ def main():
     ap.add_argument("--profile-rates", action="store_true",
                     help="two production-rate calls on --mech at --points states (a driver for ncu captures)")
     ap.add_argument("--mech", default=MECH, help="mechanism of --profile-rates")
+    ap.add_argument("--profile-call", default="rates", choices=["rates", "vjp"],
+                    help="--profile-rates: production rates or their adjoint (random N(0,1) cotangents)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="precision of --profile-rates")
     ap.add_argument("--rates-layout", type=int, default=0,
                     help="float-pair rates: 0 by batch size, 1 thread per state, 2 warp-cooperative")
