@@ -128,6 +128,10 @@ typedef struct {
                          not bit for bit (different summation orders). */
   int rates_group;    /* warp-cooperative production rates: states per warp, a power of two up to
                          32; 0 (default) one */
+  int vjp_form;       /* double-float adjoint, the terms d R/d C_k = nu R/C_k: 0 (default) the
+                         reaction's rate mantissa times a per-state reciprocal 1/|C_k| (log space
+                         only where the rate underflows); 1 one log-space exponential
+                         exp(ln |R| - ln |C_k|) per entry (no reciprocal table) */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 

@@ -2292,8 +2292,12 @@ void emit_vjp64(Out& o, const Mechanism& m, OpCounts& c) {
 // carries its own running power-of-two scale (kx_acc_add).  The chain to
 // (T, Y) is closed per state in float64: Gibbs-Helmholtz for G_k/RT(T),
 // C_k = [M] y_k / sigma with [M] = p/(R T).
-void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
+void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c, bool recip) {
   const int ns = m.ns;
+  // a rate below float64 (ln |R| <= -740, where an absent species meets other small factors) keeps
+  // its exact mantissa and power of two: e^x = 2^-2016 e^(x + 2016 ln2), the shift a float pair
+  // (1.7e-12 relative off 2016 ln2, so such a rate is off by at most that much)
+  const std::string shift = DFc(2016.0 * std::log(2.0));
   std::vector<DfClass> cls = emit_class_tables(g, m);
   // H/RT coefficients per species and NASA range: a0, a1/2, a2/3, a3/4, a4/5 (in T) and a5 (over T)
   {
@@ -2330,7 +2334,7 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
   o(fmt("float4 sv[%d];   // {ln |C_k| (pair), mu_k = G_k/RT + ln |C_k| (pair)}", ns));
   o(fmt("float2 yv[%d];   // Y_k/W_k (pair)", ns));
   o(fmt("float4 vh[%d];   // {cotangent v_k (pair), H_k/RT (pair)}", ns));
-  o(fmt("float4 ic[%d];   // 1/|C_k| = {mantissa (pair), power of two (int bits), 0}", ns));
+  if (recip) o(fmt("float4 ic[%d];   // 1/|C_k| = {mantissa (pair), power of two (int bits), 0}", ns));
   o(fmt("kx_acc gc[%d];   // adjoints of C_k, each a float pair under its own scale 2^-s", ns));
   o("kx_df gTa = kx_mk(0.0f, 0.0f), gMa = kx_mk(0.0f, 0.0f);   // adjoints of T (fixed C) and of [M]");
   o("int sT = -100000, sM = -100000;");
@@ -2379,7 +2383,7 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
   o("  hk = kx_df_fma(hk, Td, KX_PF(hc + 0));");
   o("  hk = kx_df_fma(KX_PF(hc + 10), iT, hk);   // H_k/RT");
   o("  vh[k] = make_float4(vk.hi, vk.lo, hk.hi, hk.lo);");
-  o("  { int e; const kx_df mi = kx_df_exp_m(kx_df_neg(l), e); ic[k] = make_float4(mi.hi, mi.lo, __int_as_float(e), 0.0f); }");
+  if (recip) o("  { int e; const kx_df mi = kx_df_exp_m(kx_df_neg(l), e); ic[k] = make_float4(mi.hi, mi.lo, __int_as_float(e), 0.0f); }");
   o("  gc[k] = kx_acc{0.0f, 0.0f, -100000, 0};");
   o("}");
   c.fp32 += 40 + 45 + kDfDiv + 3 * kDfMul + kDfAdd + kDfDiv + kDfLog;
@@ -2557,7 +2561,8 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
       c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
       // R_r = sign e^(lr): exponent and signed mantissa
       o("  int er;");
-      o("  kx_df mr = kx_df_exp_m(lr, er);");
+      o(fmt("  kx_df mr = kx_df_exp_m(lr.hi <= -740.0f ? kx_df_add(lr, %s) : lr, er);", shift.c_str()));
+      o("  if (lr.hi <= -740.0f) er -= 2016;");
       o("  if (sr) mr = kx_df_neg(mr);");
       c.fp32 += NC * kDfExp;
       (void)dn;
@@ -2577,34 +2582,35 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c) {
             dn != 0 ? fmt("kx_df_add(dh, kx_mk(%s, 0.0f))", F(-dn).c_str()).c_str() : "dh"));
       c.fp32 += NC * (3 * kDfMul + kDfAdd + 20);
     }
-    // d/dC_k: one term per entry, R/C_k with the sign of R/C_k.  As |R| = m 2^e and 1/|C_k| = m' 2^e'
-    // (per state), a product of mantissas; where |R| itself is below float64 (ln |R| <= -740: an absent
-    // reactant beside other small factors) the term is formed in log space, exp(ln |R| - ln |C_k|).
-    std::string lowc = "lf.hi <= -740.0f";
-    if (d.rev) lowc += " || lr.hi <= -740.0f";
+    // d/dC_k: one term per entry, R/C_k with the sign of R/C_k: as |R| = m 2^e and 1/|C_k| = m' 2^e'
+    // (per state), a product of mantissas (recip), or one log-space exponential exp(ln |R| - ln |C_k|)
+    // per entry
     o("  int ef;");
-    o("  kx_df mf = kx_df_exp_m(lf, ef);   // |R_f| = mf 2^ef");
+    o(fmt("  kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);   // |R_f| = mf 2^ef", shift.c_str()));
+    o("  if (lf.hi <= -740.0f) ef -= 2016;");
     c.fp32 += NC * kDfExp;
-    o("  if (" + lowc + ") {");
-    for (int j = 0; j < E; ++j) {
-      const bool reac = j < d.nre;
-      if (!reac && !d.rev) continue;
-      o(fmt("    { int et; kx_df mt = kx_df_exp_m(kx_df_sub(%s, kx_mk(v%d.x, v%d.y)), et);", reac ? "lf" : "lr", j, j));
-      o(fmt("      if (%s ^ KX_NEG(k%d)) mt = kx_df_neg(mt);", reac ? "sf" : "sr", j));
-      o(fmt("      kx_acc_add(gc[k%d], kx_df_mul_u(%s, mt), et); }", j, reac ? aq.c_str() : ("kx_df_neg(" + aq + ")").c_str()));
+    if (!recip) {
+      for (int j = 0; j < E; ++j) {
+        const bool reac = j < d.nre;
+        if (!reac && !d.rev) continue;
+        o(fmt("  { int et; kx_df mt = kx_df_exp_m(kx_df_sub(%s, kx_mk(v%d.x, v%d.y)), et);", reac ? "lf" : "lr", j, j));
+        o(fmt("    if (%s ^ KX_NEG(k%d)) mt = kx_df_neg(mt);", reac ? "sf" : "sr", j));
+        o(fmt("    kx_acc_add(gc[k%d], kx_df_mul_u(%s, mt), et); }", j, reac ? aq.c_str() : ("kx_df_neg(" + aq + ")").c_str()));
+      }
+    } else {
+      o(fmt("  { const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
+      if (d.rev) o(fmt("    const kx_df ar = kx_df_mul_u(%s, mr);   // mr carries the sign of R_r", ("kx_df_neg(" + aq + ")").c_str()));
+      for (int j = 0; j < E; ++j) {
+        const bool reac = j < d.nre;
+        if (!reac && !d.rev) continue;
+        o(fmt("    { const float4 q = ic[k%d]; kx_df mt = kx_df_mul_u(%s, kx_mk(q.x, q.y)); if (KX_NEG(k%d)) mt = kx_df_neg(mt);", j,
+              reac ? "af" : "ar", j));
+        o(fmt("      kx_acc_add(gc[k%d], mt, %s + __float_as_int(q.z)); }", j, reac ? "ef" : "er"));
+      }
+      o("  }");
     }
-    o("  } else {");
-    o(fmt("    const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
-    if (d.rev) o(fmt("    const kx_df ar = kx_df_mul_u(%s, mr);   // mr carries the sign of R_r", ("kx_df_neg(" + aq + ")").c_str()));
-    for (int j = 0; j < E; ++j) {
-      const bool reac = j < d.nre;
-      if (!reac && !d.rev) continue;
-      o(fmt("    { const float4 q = ic[k%d]; kx_df mt = kx_df_mul_u(%s, kx_mk(q.x, q.y)); if (KX_NEG(k%d)) mt = kx_df_neg(mt);", j,
-            reac ? "af" : "ar", j));
-      o(fmt("      kx_acc_add(gc[k%d], mt, %s + __float_as_int(q.z)); }", j, reac ? "ef" : "er"));
-    }
-    o("  }");
-    c.fp32 += NC * (2 * kDfMul + E * (kDfMul + 20));
+    if (recip) c.fp32 += NC * (2 * kDfMul + E * (kDfMul + 20));
+    else c.fp32 += NC * E * (kDfAdd + kDfExp + kDfMul + 20);
     // third-body adjoint a (R_f - R_r) (times dln k_f/d[X] in a falloff), spread over [M] and the listed species
     if (tb) {
       o(d.kind == Kind::ThreeBody ? "  const kx_df gX = kx_df_mul_u(av, mq);" : "  const kx_df gX = kx_df_mul_u(kx_df_mul_u(av, mq), dX);");
@@ -3703,7 +3709,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
       outs = "const double* __restrict__ V_, double* __restrict__ gT_, double* __restrict__ gY_";
       nan_fill = fmt("gT_[i] = KX_NAN; for (int k = 0; k < %d; ++k) gY_[(long long)k * ld + i] = KX_NAN;", m.ns);
       if (opt.rates_arith == 1) emit_vjp64(body, m, c);
-      else emit_vjp_df(body, globals, m, c);
+      else emit_vjp_df(body, globals, m, c, opt.vjp_form == 0);
       break;
   }
   std::ostringstream s;

@@ -77,6 +77,8 @@ struct EmitOptions {
   int rates_layout = 0;     // float-pair production rates: 0/1 thread per state, 2 warp-cooperative (the
                             // states of a warp share its lanes, species vectors in shared memory)
   int rates_group = 0;      // warp-cooperative: states per warp (power of two up to 32; 0: one)
+  int vjp_form = 0;         // double-float adjoint, d/dC_k: 0 rate mantissa times a per-state reciprocal
+                            // concentration, 1 one log-space exponential per entry
 };
 
 // Launch shape of the warp-cooperative production-rate kernel.
