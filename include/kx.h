@@ -132,6 +132,9 @@ typedef struct {
                          reaction's rate mantissa times a per-state reciprocal 1/|C_k| (log space
                          only where the rate underflows); 1 one log-space exponential
                          exp(ln |R| - ln |C_k|) per entry (no reciprocal table) */
+  int vjp_layout;     /* double-float adjoint: 0 (default) or 1 one thread per state; 2
+                         warp-cooperative (one state per warp, its vectors and per-reaction terms
+                         in shared memory, d/dC_k gathered species-major) */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 

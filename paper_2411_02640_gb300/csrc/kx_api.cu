@@ -335,6 +335,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.maxrreg < 0 || h->opt.maxrreg > 255) return fail(KX_ERR_ARG, "maxrreg must be in [0, 255]");
   if (h->opt.rates_layout < 0 || h->opt.rates_layout > 2) return fail(KX_ERR_ARG, "rates_layout must be 0, 1 or 2");
   if (h->opt.vjp_form < 0 || h->opt.vjp_form > 1) return fail(KX_ERR_ARG, "vjp_form must be 0 or 1");
+  if (h->opt.vjp_layout < 0 || h->opt.vjp_layout > 2) return fail(KX_ERR_ARG, "vjp_layout must be 0, 1 or 2");
   if (h->opt.rates_group < 0 || h->opt.rates_group > 32 || (h->opt.rates_group & (h->opt.rates_group - 1)))
     return fail(KX_ERR_ARG, "rates_group must be 0 or a power of two up to 32");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
@@ -372,6 +373,13 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     if (wc_spec) k->eopt.rates_arith = 0;
     k->eopt.rates_group = h->opt.rates_group;
     k->eopt.vjp_form = h->opt.vjp_form;
+    k->eopt.vjp_layout = h->opt.vjp_layout;
+    if (kx::vjp_is_wc(h->m, sp.kind, k->eopt)) {
+      k->smem = kx::vjp_wc_smem(h->m, k->eopt);
+      k->states_per_block = k->eopt.block / 32;
+      if (k->smem > 200 * 1024)
+        return fail(KX_ERR_UNSUPPORTED, "warp-cooperative adjoint: one block's shared memory exceeds 200 KB (vjp_layout 1)");
+    }
     if (kx::wdot_is_wc(h->m, sp.kind, k->eopt)) {
       const kx::WcShape w = kx::wdot_wc_shape(h->m, k->eopt);
       if (w.smem_per_block > 200 * 1024)

@@ -3602,6 +3602,490 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
   return o.o.str();
 }
 
+// ------------------------------------------------------------------ warp-cooperative adjoint
+// The double-float adjoint with one state per warp and everything per state in shared memory:
+//   1. per-state scalars (lane 0);
+//   2. species over the lanes: ln |C_k|, mu_k, the cotangent v_k, H_k/RT, the signed reciprocal
+//      1/C_k as mantissa and power of two, Y_k/W_k;
+//   3. reactions over the lanes (classes merged by kind, as in the warp-cooperative rates): per
+//      reaction the temperature terms into the lane's running d/dT and d/d[M] sums, and the
+//      reaction's a c R_f, -a c R_r and third-body a (R_f - R_r) [dln k_f/d[X]] terms, each a
+//      mantissa and a power of two, into shared memory;
+//   4. d/dC_k gathered species-major from a balanced entry list (one chunk per lane; each term a
+//      reaction's mantissa times 1/C_k, or a third-body term times an efficiency), partial sums
+//      under their own scales, combined in chunk order;
+//   5. the chain to (T, Y) in float64 (lane sums reduced in a fixed butterfly order).
+struct VwLayout {
+  int svs = 1, nw32 = 1;
+  int off_sv = 0, off_vh = 0, off_ic = 0, off_yv = 0, off_rf = 0, off_re = 0, off_rx = 0, off_nm = 0, warp_bytes = 0;
+};
+
+VwLayout vjp_wc_layout(const Mechanism& m) {
+  VwLayout L;
+  L.nw32 = (m.ns + 32) / 32;
+  L.svs = std::max(m.ns + 1, (m.ns + 33) / 2);   // species 0..ns; sv and vh later hold ns + 32 gather slots
+  auto up16 = [](int b) { return (b + 15) / 16 * 16; };
+  const int nr = m.nr();
+  L.off_sv = 96;
+  L.off_vh = L.off_sv + 16 * L.svs;
+  L.off_ic = L.off_vh + 16 * L.svs;
+  L.off_yv = L.off_ic + 16 * L.svs;
+  L.off_rf = up16(L.off_yv + 8 * L.svs);
+  L.off_re = L.off_rf + 16 * nr;
+  L.off_rx = L.off_re + 16 * nr;
+  L.off_nm = up16(L.off_rx + 8 * nr);
+  L.warp_bytes = up16(L.off_nm + 4 * L.nw32);
+  return L;
+}
+
+std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c, Out& g) {
+  (void)opt;
+  const int ns = m.ns, nr = m.nr();
+  const VwLayout L = vjp_wc_layout(m);
+  const int SVS = L.svs, NW32 = L.nw32;
+  std::vector<DfClass> cls = emit_class_tables(g, m, true);
+  const std::string shift = DFc(2016.0 * std::log(2.0));
+  // H/RT coefficients as float pairs per species and range
+  {
+    std::string hf, iwd;
+    for (int k = 0; k < ns; ++k) {
+      for (int rg = 0; rg < 2; ++rg) {
+        const double* a = rg == 0 ? &m.a_lo[7 * k] : &m.a_hi[7 * k];
+        const double h[8] = {a[0], a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0, a[5], 0.0, 0.0};
+        for (int j = 0; j < 8; ++j) hf += fpair(h[j]) + ",";
+      }
+      iwd += D(1.0 / m.W[k]) + ",";
+    }
+    g(fmt("__device__ const __align__(16) float kx_hcf[%d] = {%s0.0f};", 32 * ns + 4, hf.c_str()));
+    g(fmt("__device__ const double kx_iwd[%d] = {%s0.0};", ns + 1, iwd.c_str()));
+  }
+  // ---- gather table: per species k, its reactant entries (kind 0: nu'_k a c R_f / C_k), product entries
+  // of reversible reactions (kind 1: -nu''_k a c R_r / C_k) and third-body efficiencies (kind 2:
+  // (eff_k - eff_default) a (R_f - R_r) [dln k_f/d[X]], or 1 for a named collider); entry bits:
+  // reaction 0-13, kind 14-15, species 16-30, "last of its slot" 31; the coefficient as a float
+  struct GE { int r, kind, k; float coef; };
+  std::vector<GE> ent;
+  for (int k = 0; k < ns; ++k)
+    for (int i = 0; i < nr; ++i) {
+      const Reaction& r = m.rx[i];
+      int a = 0, b = 0;
+      for (auto& s : r.reac) if (s.first == k) a += s.second;
+      for (auto& s : r.prod) if (s.first == k) b += s.second;
+      if (a) ent.push_back({i, 0, k, (float)a});
+      if (b && r.reversible) ent.push_back({i, 1, k, (float)b});
+      if (r.third_body()) {
+        if (r.collider >= 0) { if (r.collider == k) ent.push_back({i, 2, k, 1.0f}); }
+        else for (auto& e : r.eff) if (e.first == k && e.second != r.default_eff) ent.push_back({i, 2, k, (float)(e.second - r.default_eff)});
+      }
+    }
+  if (nr >= (1 << 14) || ns >= (1 << 15)) return "";
+  const int NCH = 32, NE = (int)ent.size();
+  const int CL = std::max(1, (NE + NCH - 1) / NCH);
+  std::vector<std::pair<int32_t, float>> tab((size_t)CL * NCH, {0, 0.0f});
+  std::vector<int> chslot(NCH, 0), sfirst(ns, 0), scount(ns, 0);
+  int nslot = 0;
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int b = ch * NE / NCH, e = (ch + 1) * NE / NCH;
+    chslot[ch] = nslot;
+    for (int j = b; j < e; ++j) {
+      const bool last = j + 1 == e || ent[j + 1].k != ent[j].k;
+      tab[(size_t)(j - b) * NCH + ch] = {(int32_t)((uint32_t)ent[j].r | ((uint32_t)ent[j].kind << 14) | ((uint32_t)ent[j].k << 16) |
+                                                   (last ? 0x80000000u : 0u)), ent[j].coef};
+      if ((j == b || ent[j - 1].k != ent[j].k) && scount[ent[j].k] == 0) sfirst[ent[j].k] = nslot;
+      if (last) { ++scount[ent[j].k]; ++nslot; }
+    }
+  }
+  if (nslot > 2 * SVS) return "";
+  {
+    std::string t;
+    for (auto& v : tab) t += fmt("{%d,%s},", v.first, F(v.second).c_str());
+    g(fmt("__device__ const __align__(8) struct { int w; float c; } kx_vtab[%d] = {%s{0,0.0f}};", (int)tab.size() + 1, t.c_str()));
+    std::string cs, ss;
+    for (int ch = 0; ch < NCH; ++ch) cs += std::to_string(chslot[ch]) + ",";
+    for (int k = 0; k < ns; ++k) ss += fmt("{%d,%d},", sfirst[k], scount[k]);
+    g(fmt("__device__ const int kx_vchs[%d] = {%s0};", NCH + 1, cs.c_str()));
+    g(fmt("__device__ const int2 kx_vslot[%d] = {%s{0,0}};", ns + 1, ss.c_str()));
+  }
+  bool any_plog = false;
+  for (auto& r : m.rx) any_plog |= r.kind == Kind::Plog;
+  const int NT = (ns + 31) / 32;
+  Out o;
+  o.ind = 1;
+  o("#define KX_PF(p) kx_mk((p)[0], (p)[1])");
+  o("const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;");
+  o(fmt("unsigned char* const wsm = kx_dyn + wib * %d;", L.warp_bytes));
+  o("float4* const sc4 = (float4*)wsm;   // {Td, ln T}, {1/T, ln(p_atm/RT)}, {C_M, C_M/sigma}, {ln p, 1/T^2}, {T, p bits}");
+  o("int* const scf = (int*)(wsm + 80);   // state flag: 0 ok, 1 outside the domain");
+  o(fmt("float4* const sv = (float4*)(wsm + %d);   // {ln |C_k|, mu_k}; later the gather slots", L.off_sv));
+  o(fmt("float4* const vh = (float4*)(wsm + %d);   // {v_k, H_k/RT}", L.off_vh));
+  o(fmt("float4* const ic = (float4*)(wsm + %d);   // 1/C_k: {signed mantissa, power of two}", L.off_ic));
+  o(fmt("float2* const yv = (float2*)(wsm + %d);   // Y_k/W_k", L.off_yv));
+  o(fmt("float4* const rf = (float4*)(wsm + %d);   // per reaction {a c R_f, -a c R_r} mantissas", L.off_rf));
+  o(fmt("int4* const re = (int4*)(wsm + %d);       // per reaction {their powers of two, the third-body term's}", L.off_re));
+  o(fmt("float2* const rx = (float2*)(wsm + %d);   // per reaction the third-body term's mantissa", L.off_rx));
+  o(fmt("unsigned* const nmk = (unsigned*)(wsm + %d);", L.off_nm));
+  o(fmt("const long long nwarp = (long long)gridDim.x * %d;", opt.block / 32));
+  o(fmt("for (long long i = (long long)blockIdx.x * %d + wib; i < n; i += nwarp) {", opt.block / 32));
+  ++o.ind;
+  // ---- 1. scalars
+  o("if (lane == 0) {");
+  o("  double T = T_[i], P = P_[i];");
+  o("  int flag = 0;");
+  o("  if (!(T > 0.0 && P > 0.0 && T < KX_INF && P < KX_INF)) { flag = 1; T = 1000.0; P = 101325.0; }");
+  o("  const kx_df Td = kx_d2df_i(T), lnT = kx_df_log_d(T), iT = kx_df_div(kx_mk(1.0f, 0.0f), Td), iT2 = kx_df_mul(iT, iT);");
+  o(fmt("  const kx_df cM = kx_df_mul(kx_df_mul(kx_d2df_i(P), iT), %s);", DFc(1.0 / R_U).c_str()));
+  o(fmt("  const kx_df lnPRT = kx_df_sub(%s, lnT);", DFc(std::log(P_ATM / R_U)).c_str()));
+  o("  sc4[0] = make_float4(Td.hi, Td.lo, lnT.hi, lnT.lo);");
+  o("  sc4[1] = make_float4(iT.hi, iT.lo, lnPRT.hi, lnPRT.lo);");
+  o("  sc4[2] = make_float4(cM.hi, cM.lo, 0.0f, 0.0f);");
+  o(any_plog ? "  const kx_df lnP = kx_df_log_d(P);" : "  const kx_df lnP = kx_mk(0.0f, 0.0f);");
+  o("  sc4[3] = make_float4(lnP.hi, lnP.lo, iT2.hi, iT2.lo);");
+  o("  sc4[4] = make_float4(__int_as_float(__double2loint(T)), __int_as_float(__double2hiint(T)), "
+    "__int_as_float(__double2loint(P)), __int_as_float(__double2hiint(P)));");
+  o("  *scf = flag;");
+  o(fmt("  for (int w = 0; w < %d; ++w) nmk[w] = 0u;", NW32));
+  o(fmt("  sv[%d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); vh[%d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // padding species", ns, ns));
+  o(fmt("  ic[%d] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); yv[%d] = make_float2(0.0f, 0.0f);", ns, ns));
+  o("}");
+  o("__syncwarp();");
+  // ---- 2. species
+  o("const float4 s0 = sc4[0], s1 = sc4[1], s2 = sc4[2], s4 = sc4[4];");
+  o("const kx_df Tg = kx_mk(s0.x, s0.y), lnTg = kx_mk(s0.z, s0.w), iTg = kx_mk(s1.x, s1.y);");
+  o("const long long Tb = ((long long)__float_as_int(s4.y) << 32) | (unsigned)__float_as_int(s4.x);");
+  o(fmt("double Yv[%d];", NT));
+  o("kx_df sg = kx_mk(0.0f, 0.0f);");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o("  const int k = lane + 32 * t;");
+  o(fmt("  Yv[t] = k < %d ? Y_[(long long)k * ld + i] : 0.0;", ns));
+  o(fmt("  if (k < %d) {", ns));
+  o("    const kx_df yk = kx_df_mul(kx_d2df_i(Yv[t]), KX_PF(kx_iwf + 2 * k));");
+  o("    yv[k] = make_float2(yk.hi, yk.lo);");
+  o("    sg = kx_df_add(sg, yk);");
+  o("  }");
+  o("}");
+  for (int off = 1; off < 32; off *= 2)
+    o(fmt("{ const float h = __shfl_xor_sync(0xffffffffu, sg.hi, %d), l = __shfl_xor_sync(0xffffffffu, sg.lo, %d); sg = kx_df_add(sg, kx_mk(h, l)); }", off, off));
+  o("sg = kx_mk(__shfl_sync(0xffffffffu, sg.hi, 0), __shfl_sync(0xffffffffu, sg.lo, 0));");
+  o("const kx_df fC = kx_df_div(kx_mk(s2.x, s2.y), sg);");
+  o("const kx_df lnfC = kx_df_log(fC);");
+  o("__syncwarp();");
+  o("if (lane == 0) {");
+  o("  sc4[2] = make_float4(s2.x, s2.y, fC.hi, fC.lo);");
+  o("  if (!(sg.hi > 0.0f && sg.hi < KX_INF_F)) *scf = 1;");
+  o("}");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o("  const int k = lane + 32 * t;");
+  o(fmt("  if (k < %d) {", ns));
+  o("    const double Yk = Yv[t];");
+  o("    const long long yb = __double_as_longlong(Yk) & 0x7fffffffffffffffLL;");
+  o("    kx_df l = kx_mk(-700.0f, 0.0f);");
+  o("    if (yb >= 0x0010000000000000LL && yb < 0x7ff0000000000000LL) {");
+  o("      l = kx_df_add(kx_df_log_d(__longlong_as_double(yb)), kx_df_sub(lnfC, KX_PF(kx_lwf + 2 * k)));");
+  o("      if (!(l.hi > -700.0f)) l = kx_mk(-700.0f, 0.0f);");
+  o("    }");
+  o("    if (Yk < 0.0) atomicOr(&nmk[k >> 5], 1u << (k & 31));");
+  o("    const float* a = kx_gcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("    kx_df gk = kx_df_fma(KX_PF(a + 8), Tg, KX_PF(a + 6));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 4));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 2));");
+  o("    gk = kx_df_fma(gk, Tg, KX_PF(a + 0));");
+  o("    gk = kx_df_fma(KX_PF(a + 10), iTg, gk);");
+  o("    gk = kx_df_fma(KX_PF(a + 12), lnTg, gk);");
+  o("    const kx_df mk_ = kx_df_add(gk, l);");
+  o("    sv[k] = make_float4(l.hi, l.lo, mk_.hi, mk_.lo);");
+  o("    const float* hc = kx_hcf + 32 * k + (Tb < kx_tmidb[k] ? 0 : 16);");
+  o("    kx_df hk = kx_df_fma(KX_PF(hc + 8), Tg, KX_PF(hc + 6));");
+  o("    hk = kx_df_fma(hk, Tg, KX_PF(hc + 4));");
+  o("    hk = kx_df_fma(hk, Tg, KX_PF(hc + 2));");
+  o("    hk = kx_df_fma(hk, Tg, KX_PF(hc + 0));");
+  o("    hk = kx_df_fma(KX_PF(hc + 10), iTg, hk);");
+  o("    const kx_df vk = kx_d2df_i(V_[(long long)k * ld + i]);");
+  o("    vh[k] = make_float4(vk.hi, vk.lo, hk.hi, hk.lo);");
+  o("    int e; kx_df mi = kx_df_exp_m(kx_df_neg(l), e);");
+  o("    if (Yk < 0.0) mi = kx_df_neg(mi);   // the reciprocal carries the concentration's sign");
+  o("    ic[k] = make_float4(mi.hi, mi.lo, __int_as_float(e), 0.0f);");
+  o("  }");
+  o("}");
+  o("__syncwarp();");
+  c.fp32 += 40 + 45 + kDfDiv + 3 * kDfMul + kDfAdd + kDfDiv + kDfLog;
+  c.fp32 += ns * (12 + kDfMul + kDfAdd) + ns * (45 + 2 * kDfAdd + 11 * kDfFma + kDfAdd + kDfExp);
+  // ---- 3. reactions
+  static const char* xyzw[4] = {"x", "y", "z", "w"};
+  auto comp = [&](const char* base, int j) { return fmt("%s%d.%s", base, j / 4, xyzw[j % 4]); };
+  const std::string il10 = DFc(1.0 / std::log(10.0));
+  o("kx_df gTa = kx_mk(0.0f, 0.0f), gMa = kx_mk(0.0f, 0.0f);   // this lane's d/dT (fixed C) and d/d[M] sums");
+  o("int sT = -100000, sM = -100000;");
+  o("{");
+  ++o.ind;
+  o("const float4 A0 = sc4[0], A1 = sc4[1], A2 = sc4[2], A3 = sc4[3], A4 = sc4[4];");
+  o("const kx_df Td = kx_mk(A0.x, A0.y), lnT = kx_mk(A0.z, A0.w), iT = kx_mk(A1.x, A1.y), lnPRT = kx_mk(A1.z, A1.w);");
+  o("const kx_df cM = kx_mk(A2.x, A2.y), fC = kx_mk(A2.z, A2.w), lnP = kx_mk(A3.x, A3.y), iT2 = kx_mk(A3.z, A3.w);");
+  o("const double P = __hiloint2double(__float_as_int(A4.w), __float_as_int(A4.z));");
+  o("(void)lnP; (void)P; (void)cM; (void)fC;");
+  o("#define KX_NEG(k) ((int)((nmk[(k) >> 5] >> ((k) & 31)) & 1u))");
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    const DfClass& d = cls[ci];
+    const bool tb = d.kind == Kind::ThreeBody || d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const bool fo = d.kind == Kind::Falloff || d.kind == Kind::ChemAct;
+    const int NF = fo ? 7 : tb ? 3 : 2;
+    const int E = d.nre + d.npr, P = (E + 1 + 3) / 4 * 4;
+    const double NC = (double)d.rx.size();
+    o("#pragma unroll 1");
+    o(fmt("for (int r = lane; r < %d; r += 32) {   // class %d: %d reactions, %d reactant and %d product entries (padded)",
+          (int)d.rx.size(), (int)ci, (int)d.rx.size(), d.nre, d.npr));
+    ++o.ind;
+    o(fmt("const int4* sp4 = (const int4*)kx_s%d + %d * r;", (int)ci, P / 4));
+    for (int q = 0; q < P / 4; ++q) o(fmt("const int4 c%d = sp4[%d];", q, q));
+    for (int j = 0; j < E; ++j) o(fmt("const int k%d = %s & 0xffff;", j, comp("c", j).c_str()));
+    for (int j = 0; j < E; ++j) o(fmt("const float4 v%d = sv[k%d];", j, j));
+    o(fmt("const int ri = %s;", comp("c", E).c_str()));
+    o(fmt("const float4* f = kx_f%d + %d * r;", (int)ci, NF));
+    o("const float4 f0 = f[0], f1 = f[1];");
+    o("kx_df av = kx_mk(0.0f, 0.0f), dh = kx_mk(0.0f, 0.0f);   // sum_k nu_k v_k, sum_k nu_k H_k/RT");
+    for (int j = 0; j < E; ++j)
+      o(fmt("{ const unsigned cj = (unsigned)%s & 0xffff0000u; if (cj != 0u) { const float4 w = vh[k%d]; const float cf = __uint_as_float(cj); "
+            "av = kx_df_add_u(av, kx_df_mulf(kx_mk(w.x, w.y), cf)); dh = kx_df_add_u(dh, kx_df_mulf(kx_mk(w.z, w.w), cf)); } }",
+            comp("c", j).c_str(), j));
+    o("const kx_df lA = kx_mk(f0.x, f0.y), bA = kx_mk(f0.z, f0.w), nEA = kx_mk(f1.x, f1.y);");
+    o("kx_df lk = kx_df_fma(bA, lnT, kx_df_fma(nEA, iT, lA));");
+    o("kx_df dT = kx_df_mul(iT, kx_df_fma(kx_df_neg(nEA), iT, bA));");
+    c.fp32 += NC * (2 * kDfFma + kDfMul + kDfFma) + NC * E * (kDfAdd + kDfMulf);
+    std::string aq = "av";
+    if (tb) {
+      o(fmt("const int2 e = kx_e%d[r];", (int)ci));
+      o("const float4 f2 = f[2];");
+      o("kx_df X;");
+      o("if (e.y < 0) {");
+      o("  const int kc = kx_effd[e.x].k;");
+      o("  X = kx_df_mul(kx_mk(yv[kc].x, yv[kc].y), fC);");
+      o("} else {");
+      o("  kx_df t = kx_mk(0.0f, 0.0f);");
+      o("  for (int j = 0; j < e.y; ++j) {");
+      o("    const kx_effd_t q = kx_effd[e.x + j];");
+      o("    t = kx_df_fma(kx_mk(q.ahi, q.alo), kx_mk(yv[q.k].x, yv[q.k].y), t);");
+      o("  }");
+      o("  X = kx_df_fma(kx_mk(f2.x, f2.y), cM, kx_df_mul(fC, t));");
+      o("}");
+      c.fp32 += NC * (kDfFma + kDfMul + 3 * kDfFma);
+    }
+    if (d.kind == Kind::ThreeBody) { o("const kx_df aq = kx_df_mul(av, X);"); aq = "aq"; c.fp32 += NC * kDfMul; }
+    if (fo) {
+      o("const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+      o("const kx_df b0 = kx_mk(f3.x, f3.y), nE0 = kx_mk(f3.z, f3.w);");
+      o("const kx_df lk0 = kx_df_fma(b0, lnT, kx_df_fma(nE0, iT, kx_mk(f2.z, f2.w)));");
+      o("const kx_df dk0 = kx_df_mul(iT, kx_df_fma(kx_df_neg(nE0), iT, b0));");
+      o("kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
+      o("if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
+      o("const bool small = lnPr.hi < 0.0f;");
+      o("const kx_df ee = kx_df_exp_n(small ? lnPr : kx_df_neg(lnPr));");
+      o("const kx_df i1e = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_add(kx_mk(1.0f, 0.0f), ee));");
+      o("const kx_df e1e = kx_df_mul(ee, i1e);");
+      o("const kx_df P1 = small ? e1e : i1e, P0 = small ? i1e : e1e;");
+      o("const kx_df l1p = kx_df_log1p(ee);");
+      o("kx_df lnF = kx_mk(0.0f, 0.0f), dFl = kx_mk(0.0f, 0.0f), dFT = kx_mk(0.0f, 0.0f);");
+      if (d.blend == Blend::Troe) {
+        o("{");
+        o("  const kx_df p0 = kx_mk(f4.x, f4.y), p1 = kx_mk(f4.z, f4.w), p2 = kx_mk(f5.x, f5.y), p3 = kx_mk(f5.z, f5.w), p4 = kx_mk(f6.x, f6.y);");
+        o("  const kx_df e3 = kx_df_mul(p0, kx_df_exp_s(kx_df_mul(Td, p2)));");
+        o("  const kx_df e1 = kx_df_mul(p1, kx_df_exp_s(kx_df_mul(Td, p3)));");
+        o("  const kx_df e2 = kx_df_exp_s(kx_df_mul(p4, iT));");
+        o("  const kx_df Fc = kx_df_add(kx_df_add(e3, e1), e2);");
+        o("  const kx_df dFc = kx_df_fma(e3, p2, kx_df_fma(e1, p3, kx_df_neg(kx_df_mul(kx_df_mul(e2, p4), iT2))));");
+        o(fmt("  const kx_df lFc = kx_df_mul(kx_df_log(Fc), %s);", il10.c_str()));
+        o(fmt("  const kx_df xx = kx_df_fma(lnPr, %s, kx_df_fma(%s, lFc, %s));", il10.c_str(), DFc(-0.67).c_str(), DFc(-0.4).c_str()));
+        o(fmt("  const kx_df nn = kx_df_fma(%s, lFc, %s);", DFc(-1.27).c_str(), DFc(0.75).c_str()));
+        o(fmt("  const kx_df den = kx_df_fma(%s, xx, nn);", DFc(-0.14).c_str()));
+        o("  const kx_df iden = kx_df_div(kx_mk(1.0f, 0.0f), den);");
+        o("  const kx_df ff = kx_df_mul(xx, iden);");
+        o("  const kx_df g1 = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_fma(ff, ff, kx_mk(1.0f, 0.0f)));");
+        o(fmt("  lnF = kx_df_mul(kx_df_mul(%s, lFc), g1);", DFc(std::log(10.0)).c_str()));
+        o("  const kx_df h2 = kx_df_mul(kx_df_mul(kx_df_mul(kx_mk(-2.0f, 0.0f), ff), kx_df_mul(g1, g1)), lFc);");
+        o("  const kx_df id2 = kx_df_mul(iden, iden);");
+        o("  dFl = kx_df_mul(kx_df_mul(h2, nn), id2);");
+        o(fmt("  dFT = kx_df_mul(kx_df_fma(kx_df_mul(h2, kx_df_fma(%s, den, kx_df_mul(%s, xx))), id2, g1), kx_df_div(dFc, Fc));",
+              DFc(-0.67).c_str(), DFc(1.27 - 0.14 * 0.67).c_str()));
+        o("}");
+        c.fp32 += NC * (3 * (kDfMul + kDfExp) + 2 * kDfMul + 2 * kDfAdd + 3 * kDfFma + kDfLog + kDfMul + 4 * kDfFma + 3 * kDfDiv + 12 * kDfMul);
+      } else if (d.blend == Blend::Sri) {
+        o("{");
+        o("  const kx_df pa = kx_mk(f4.x, f4.y), pnb = kx_mk(f4.z, f4.w), pnc = kx_mk(f5.x, f5.y), pld = kx_mk(f5.z, f5.w), pe = kx_mk(f6.x, f6.y);");
+        o(fmt("  const kx_df lPr = kx_df_mul(lnPr, %s);", il10.c_str()));
+        o("  const kx_df Xs = kx_df_div(kx_mk(1.0f, 0.0f), kx_df_fma(lPr, lPr, kx_mk(1.0f, 0.0f)));");
+        o("  const kx_df ea = kx_df_mul(pa, kx_df_exp_s(kx_df_mul(pnb, iT)));");
+        o("  const kx_df eb = kx_df_exp_s(kx_df_mul(Td, pnc));");
+        o("  const kx_df base = kx_df_add(ea, eb);");
+        o("  const kx_df lnb = kx_df_log(base);");
+        o("  lnF = kx_df_add(pld, kx_df_fma(pe, lnT, kx_df_mul(Xs, lnb)));");
+        o(fmt("  dFl = kx_df_mul(kx_df_mul(kx_df_mul(kx_mk(-2.0f, 0.0f), lPr), kx_df_mul(Xs, Xs)), kx_df_mul(lnb, %s));", il10.c_str()));
+        o("  dFT = kx_df_fma(pe, iT, kx_df_mul(Xs, kx_df_div(kx_df_fma(kx_df_neg(kx_df_mul(ea, pnb)), iT2, kx_df_mul(eb, pnc)), base)));");
+        o("}");
+        c.fp32 += NC * (2 * (kDfMul + kDfExp) + 14 * kDfMul + 3 * kDfDiv + kDfLog + 4 * kDfFma + 2 * kDfAdd);
+      }
+      if (d.kind == Kind::Falloff) {
+        o("lk = kx_df_add(lk, kx_df_add(small ? kx_df_sub(lnPr, l1p) : kx_df_neg(l1p), lnF));");
+        o("const kx_df dP = kx_df_add(P0, dFl);");
+        o("dT = kx_df_add(kx_df_fma(kx_df_sub(dk0, dT), dP, dT), dFT);");
+      } else {
+        o("lk = kx_df_add(lk0, kx_df_sub(lnF, small ? l1p : kx_df_add(lnPr, l1p)));");
+        o("const kx_df dP = kx_df_sub(dFl, P1);");
+        o("dT = kx_df_add(kx_df_fma(kx_df_sub(dk0, dT), dP, dk0), dFT);");
+      }
+      o("const kx_df dX = kx_df_div(dP, X);");
+      c.fp32 += NC * (2 * kDfFma + kDfMul + kDfAdd + kDfLog + kDfExp + 2 * kDfDiv + kDfMul + kDfLog + 6 * kDfAdd + kDfFma);
+    } else if (d.kind == Kind::Plog) {
+      o(fmt("const int2 e = kx_e%d[r];", (int)ci));
+      o("const float* t = kx_plogf + 8 * e.x; const long long* tp = kx_plogp + e.x; const int np = e.y;");
+      o("const long long Pb = __double_as_longlong(P);");
+      o("#define KX_PLK(u) kx_df_fma(KX_PF((u) + 4), lnT, kx_df_fma(KX_PF((u) + 6), iT, KX_PF((u) + 2)))");
+      o("#define KX_PLD(u) kx_df_mul(iT, kx_df_fma(kx_df_neg(KX_PF((u) + 6)), iT, KX_PF((u) + 4)))");
+      o("if (Pb <= tp[0]) { lk = KX_PLK(t); dT = KX_PLD(t); }");
+      o("else if (Pb >= tp[np - 1]) { const float* u = t + 8 * (np - 1); lk = KX_PLK(u); dT = KX_PLD(u); }");
+      o("else {");
+      o("  int j = 0; while (!(Pb < tp[j + 1])) ++j;");
+      o("  const float* u = t + 8 * j;");
+      o("  const kx_df w = kx_df_div(kx_df_sub(lnP, KX_PF(u)), kx_df_sub(KX_PF(u + 8), KX_PF(u)));");
+      o("  const kx_df l1 = KX_PLK(u), l2 = KX_PLK(u + 8), d1 = KX_PLD(u), d2 = KX_PLD(u + 8);");
+      o("  lk = kx_df_fma(kx_df_sub(l2, l1), w, l1);");
+      o("  dT = kx_df_fma(kx_df_sub(d2, d1), w, d1);");
+      o("}");
+      o("#undef KX_PLK");
+      o("#undef KX_PLD");
+      c.fp32 += NC * (8 * kDfFma + 4 * kDfMul + 5 * kDfAdd + kDfDiv);
+    }
+    o("kx_df lf = lk;");
+    for (int j = 0; j < d.nre; ++j) o(fmt("lf = kx_df_add_u(lf, kx_mk(v%d.x, v%d.y));", j, j));
+    std::string sfx = "0", srx = "0";
+    for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+    for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+    o("const int sf = " + sfx + ";");
+    o("kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
+    o("int sq = sf;");
+    o("kx_df ar = kx_mk(0.0f, 0.0f);");
+    o("int er = -100000;");
+    if (d.rev) {
+      o("const int sr = " + srx + ";");
+      std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
+      o("kx_df dl = " + first + ";");
+      for (int j = 1; j < E; ++j)
+        o(fmt("dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
+      o("dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, f1.w));   // -dn ln(p_atm/RT), dn of this reaction");
+      o("const kx_df lr = kx_df_add_u(lf, dl);");
+      o("{");
+      o("  const bool rv = dl.hi > 0.0f;");
+      o("  if (rv) L = lr;");
+      o("  const kx_df ex = kx_df_exp_n(rv ? kx_df_neg(dl) : dl);");
+      o("  const float pm = sf == sr ? -1.0f : 1.0f;");
+      o("  const kx_df s1 = kx_qts(1.0f, pm * ex.hi);");
+      o("  fac = kx_mk(s1.hi, __fmaf_rn(pm, ex.lo, s1.lo));");
+      o("  if (sf == sr) sq = sf ^ (int)rv;");
+      o("}");
+      o(fmt("kx_df mr = kx_df_exp_m(lr.hi <= -740.0f ? kx_df_add(lr, %s) : lr, er);", shift.c_str()));
+      o("if (lr.hi <= -740.0f) er -= 2016;");
+      o("if (sr) mr = kx_df_neg(mr);");
+      o(fmt("kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(kx_df_mul_u(%s, mr), iT), kx_df_add(dh, kx_mk(f1.w, 0.0f))), er);", aq.c_str()));
+      o(fmt("ar = kx_df_mul_u(kx_df_neg(%s), mr);", aq.c_str()));
+      c.fp32 += NC * ((E - 1) * kDfAdd + kDfAdd + kDfMulf + kDfAdd + 2 * kDfExp + 10 + 4 * kDfMul + kDfAdd + 20);
+    }
+    o("int eq;");
+    o("kx_df mq = kx_df_mul_u(kx_df_exp_m(L, eq), fac);   // R_f - R_r = mq 2^eq");
+    o("if (sq) mq = kx_df_neg(mq);");
+    o(fmt("kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mq), eq);", aq.c_str()));
+    o("int ef;");
+    o(fmt("kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);", shift.c_str()));
+    o("if (lf.hi <= -740.0f) ef -= 2016;");
+    o(fmt("const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
+    c.fp32 += NC * (2 * kDfExp + 4 * kDfMul + 20);
+    if (tb) {
+      o(d.kind == Kind::ThreeBody ? "const kx_df gX = kx_df_mul_u(av, mq);" : "const kx_df gX = kx_df_mul_u(kx_df_mul_u(av, mq), dX);");
+      o("if (e.y >= 0) kx_acc_add(gMa, sM, kx_df_mul_u(kx_mk(f2.x, f2.y), gX), eq);");
+      o("rx[ri] = make_float2(gX.hi, gX.lo);");
+      c.fp32 += NC * (3 * kDfMul + 20);
+    } else {
+      o("rx[ri] = make_float2(0.0f, 0.0f);");
+    }
+    o("rf[ri] = make_float4(af.hi, af.lo, ar.hi, ar.lo);");
+    o("re[ri] = make_int4(ef, er, eq, 0);");
+    --o.ind;
+    o("}");
+  }
+  o("#undef KX_NEG");
+  --o.ind;
+  o("}");
+  o("__syncwarp();");
+  // ---- 4. gather of d/dC_k
+  o("{");
+  ++o.ind;
+  o("float4* const slot = sv;   // sv and vh are free now");
+  o("int sl = kx_vchs[lane];");
+  o("kx_df acc = kx_mk(0.0f, 0.0f);");
+  o("int as = -100000;");
+  o("#pragma unroll 2");
+  o(fmt("for (int j = 0; j < %d; ++j) {", CL));
+  o(fmt("  const int wv = kx_vtab[%d * j + lane].w;", NCH));
+  o(fmt("  const float cf = kx_vtab[%d * j + lane].c;", NCH));
+  o("  if (cf != 0.0f) {");
+  o("    const int r = wv & 0x3fff, kind = (wv >> 14) & 3, k = (wv >> 16) & 0x7fff;");
+  o("    kx_df mt;");
+  o("    int et;");
+  o("    if (kind == 2) { const float2 gx = rx[r]; mt = kx_mk(gx.x, gx.y); et = re[r].z; }");
+  o("    else {");
+  o("      const float4 q = rf[r], iq = ic[k];");
+  o("      mt = kx_df_mul_u(kind == 0 ? kx_mk(q.x, q.y) : kx_mk(q.z, q.w), kx_mk(iq.x, iq.y));");
+  o("      et = (kind == 0 ? re[r].x : re[r].y) + __float_as_int(iq.z);");
+  o("    }");
+  o("    kx_acc_add(acc, as, kx_df_mulf(mt, cf), et);");
+  o("  }");
+  o("  if (wv < 0) { slot[sl++] = make_float4(acc.hi, acc.lo, __int_as_float(as), 0.0f); acc = kx_mk(0.0f, 0.0f); as = -100000; }");
+  o("}");
+  --o.ind;
+  o("}");
+  o("__syncwarp();");
+  c.fp32 += (double)NE * (kDfMul + kDfMulf + 20);
+  // ---- 5. the chain to (T, Y) in float64
+  o("const int flag = *scf;");
+  o("const float4 F2 = sc4[2], F1 = sc4[1];");
+  o("const double cMd = kx_df2d(kx_mk(F2.x, F2.y)), fCd = kx_df2d(kx_mk(F2.z, F2.w));");
+  o("const double iTd = 1.0 / __hiloint2double(__float_as_int(sc4[4].y), __float_as_int(sc4[4].x));");
+  o(fmt("double gck[%d];", NT));
+  o("double gCX = 0.0;");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o("  const int k = lane + 32 * t;");
+  o("  gck[t] = 0.0;");
+  o(fmt("  if (k < %d) {", ns));
+  o("    const int2 s = kx_vslot[k];");
+  o("    kx_df a = kx_mk(0.0f, 0.0f);");
+  o("    int sa = -100000;");
+  o("    for (int j = 0; j < s.y; ++j) { const float4 q = sv[s.x + j]; kx_acc_add(a, sa, kx_mk(q.x, q.y), __float_as_int(q.z)); }");
+  o("    gck[t] = kx_df2d_s(a, sa);");
+  o("    gCX = fma(gck[t], fCd * kx_df2d(kx_mk(yv[k].x, yv[k].y)), gCX);");
+  o("  }");
+  o("}");
+  o("double gT = kx_df2d_s(gTa, sT), gM = kx_df2d_s(gMa, sM);");
+  for (int off = 1; off < 32; off *= 2) {
+    o(fmt("gCX += __shfl_xor_sync(0xffffffffu, gCX, %d);", off));
+    o(fmt("gT += __shfl_xor_sync(0xffffffffu, gT, %d);", off));
+    o(fmt("gM += __shfl_xor_sync(0xffffffffu, gM, %d);", off));
+  }
+  o("gCX = __shfl_sync(0xffffffffu, gCX, 0); gT = __shfl_sync(0xffffffffu, gT, 0); gM = __shfl_sync(0xffffffffu, gM, 0);");
+  o("gM += gCX / cMd;");
+  o("const double gavg = gCX / cMd;");
+  o("if (lane == 0) gT_[i] = flag ? KX_NAN : fma(-gM * cMd, iTd, gT);");
+  o("#pragma unroll");
+  o(fmt("for (int t = 0; t < %d; ++t) {", NT));
+  o("  const int k = lane + 32 * t;");
+  o(fmt("  if (k < %d) gY_[(long long)k * ld + i] = flag ? KX_NAN : fCd * (gck[t] - gavg) * kx_iwd[k];", ns));
+  o("}");
+  o("if (lane == 0 && flag) atomicMin(&kx_bad_first, (unsigned long long)i);");
+  o("__syncwarp();");
+  --o.ind;
+  o("}");
+  c.fp64 += ns * 6 + 12;
+  return o.o.str();
+}
+
 }  // namespace
 
 // Shared memory per thread of the transport kernels, in bytes.
@@ -3668,8 +4152,43 @@ std::string emit_wc_kernel(const Mechanism& m, const EmitOptions& opt, const std
   return s.str();
 }
 
+bool vjp_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt) {
+  (void)m;
+  return kind == KernelKind::Vjp && opt.rates_arith != 1 && opt.vjp_layout == 2;
+}
+
+int vjp_wc_smem(const Mechanism& m, const EmitOptions& opt) { return vjp_wc_layout(m).warp_bytes * (opt.block / 32); }
+
+// The warp-cooperative adjoint (emit_vjp_wc) with its own grid-stride loop over states.
+std::string emit_vjp_wc_kernel(const Mechanism& m, const EmitOptions& opt, const std::string& entry, OpCounts* counts) {
+  OpCounts c;
+  Out globals;
+  globals.ind = 0;
+  const std::string body = emit_vjp_wc(m, opt, c, globals);
+  if (body.empty()) return "";
+  std::ostringstream s;
+  s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
+  s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
+  s << "#define KX_T64 0\n#define KX_TDF 1\n#define KX_TDFR 1\n";
+  s << kTables << "\n" << kDevicePrelude << "\n";
+  s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
+  s << globals.o.str();
+  s << "__device__ unsigned long long kx_bad_first = 0xffffffffffffffffull;\n";
+  const int rreg = opt.maxrreg > 0 ? opt.maxrreg : 128;
+  const int min_blocks = std::max(1, 65536 / (rreg * opt.block));
+  s << "extern \"C\" __global__ void __launch_bounds__(" << opt.block << ", " << min_blocks << ") " << entry
+    << "(const double* __restrict__ T_, const double* __restrict__ P_, const double* __restrict__ Y_, long long ld, "
+    << "const double* __restrict__ V_, double* __restrict__ gT_, double* __restrict__ gY_, long long n)\n{\n";
+  s << "  kx_load_tables();\n";
+  s << body;
+  s << "}\n";
+  if (counts) *counts = c;
+  return s.str();
+}
+
 std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& opt, const std::string& entry,
                         OpCounts* counts) {
+  if (vjp_is_wc(m, kind, opt)) return emit_vjp_wc_kernel(m, opt, entry, counts);
   OpCounts c;
   Out body, globals;
   body.ind = 2;

@@ -79,6 +79,7 @@ struct EmitOptions {
   int rates_group = 0;      // warp-cooperative: states per warp (power of two up to 32; 0: one)
   int vjp_form = 0;         // double-float adjoint, d/dC_k: 0 rate mantissa times a per-state reciprocal
                             // concentration, 1 one log-space exponential per entry
+  int vjp_layout = 0;       // double-float adjoint: 0/1 thread per state, 2 warp-cooperative
 };
 
 // Launch shape of the warp-cooperative production-rate kernel.
@@ -87,6 +88,8 @@ struct WcShape {
   double lane_use = 1.0;   // (state, reaction) pairs over lane slots of the class rounds
 };
 bool wdot_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt);
+bool vjp_is_wc(const Mechanism& m, KernelKind kind, const EmitOptions& opt);
+int vjp_wc_smem(const Mechanism& m, const EmitOptions& opt);   // dynamic shared memory per block
 WcShape wdot_wc_shape(const Mechanism& m, const EmitOptions& opt);
 
 // Operation counts per point, tallied while emitting (library calls such as

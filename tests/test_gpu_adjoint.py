@@ -20,12 +20,13 @@ def torch():
     return torch_cuda()
 
 
-@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("opts", [{}, {"rates_arith": 1}, {"vjp_layout": 2}])
 @pytest.mark.parametrize("name,n", [("h2o2_9_21", 300), ("gri_53_325", 256), ("large_160_900", 64)])
-def test_vjp_matches_oracle_jacobian(torch, name, n, arith):
-    """arith 0: the double-float adjoint (default); 1: native float64."""
+def test_vjp_matches_oracle_jacobian(torch, name, n, opts):
+    """{}: the double-float adjoint, one thread per state (default); rates_arith 1: native
+    float64; vjp_layout 2: the warp-cooperative double-float adjoint."""
     T, p, Y = _states(name, n, start=1000)
-    mech = mechanism(name, **({"rates_arith": 1} if arith else {}))
+    mech = mechanism(name, **opts)
     rng = np.random.default_rng(7)
     v = rng.standard_normal((mech.n_species, n))
     Td, pd, Yd = to_device(torch, T, p, Y)
@@ -41,7 +42,7 @@ def test_vjp_matches_oracle_jacobian(torch, name, n, arith):
         assert np.all(np.abs(got - ref) <= tol + 1e-9 * scale), (i, np.max(np.abs(got - ref) / (scale + 1e-300)))
 
 
-@pytest.mark.parametrize("opts", [{}, {"vjp_form": 1}, {"rates_arith": 1}])
+@pytest.mark.parametrize("opts", [{}, {"vjp_form": 1}, {"rates_arith": 1}, {"vjp_layout": 2}])
 def test_vjp_absent_and_negative_species(torch, opts):
     """States with species absent (Y_k = 0 exactly, as in a fresh mixture) and
     small negative mass fractions: the derivative with respect to an absent

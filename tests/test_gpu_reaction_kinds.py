@@ -72,14 +72,15 @@ def test_rates_of_progress_all_kinds(kinds):
     assert (np.abs(qm - ref) / gross).max() <= 2e-4
 
 
-@pytest.mark.parametrize("arith", [0, 1])
-def test_adjoint_all_kinds(kinds, arith, tmp_path_factory):
-    """Every reaction kind, the double-float adjoint (arith 0) and native float64 (1)."""
+@pytest.mark.parametrize("opts", [{}, {"rates_arith": 1}, {"vjp_layout": 2}])
+def test_adjoint_all_kinds(kinds, opts, tmp_path_factory):
+    """Every reaction kind: the double-float adjoint (thread per state and warp-cooperative) and
+    native float64."""
     import torch
     from paper_2411_02640_gb300 import kx
     mech, o = kinds
-    if arith:
-        mech = kx.Mechanism(mech.path, cache_dir=CACHE, rates_arith=1, lazy=1)
+    if opts:
+        mech = kx.Mechanism(mech.path, cache_dir=CACHE, lazy=1, **opts)
     T, p, Y = _states(200, seed=9)
     v = np.random.default_rng(1).standard_normal((4, 200))
     Td, pd, Yd = to_device(torch, T, p, Y)

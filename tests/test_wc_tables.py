@@ -99,3 +99,55 @@ def test_gather_tables_every_group_size(group, tmp_path):
     q = rng.standard_normal(len(mech.reactions))
     got = _replay(src, mech.n_species, len(mech.reactions), q)
     np.testing.assert_allclose(got, _nu(mech) @ q, rtol=1e-12, atol=1e-12)
+
+
+def _vjp_replay(src, mech_obj, af, ar, gx, ic):
+    m = re.search(r"kx_vtab\[(\d+)\] = \{(.*?)\};", src, re.S)
+    pairs = re.findall(r"\{(-?\d+),\(?([-+0-9.eE]+)f?\)?\}", m.group(2))
+    tab = [(int(w) & 0xffffffff, float(c)) for w, c in pairs][:-1]
+    chs = _array(src, "kx_vchs")[:-1]
+    ws = np.array(_array(src, "kx_vslot")).reshape(-1, 2)[:mech_obj.n_species]
+    nch = len(chs)
+    cl = len(tab) // nch
+    slots = {}
+    for ch in range(nch):
+        sl, acc = chs[ch], 0.0
+        for j in range(cl):
+            w, cf = tab[j * nch + ch]
+            if cf != 0.0:
+                r, kind, k = w & 0x3FFF, (w >> 14) & 3, (w >> 16) & 0x7FFF
+                acc += cf * (gx[r] if kind == 2 else (af[r] if kind == 0 else ar[r]) * ic[k])
+            if w & 0x80000000:
+                slots[sl] = acc
+                sl, acc = sl + 1, 0.0
+    return np.array([sum(slots[f + j] for j in range(c)) for f, c in ws])
+
+
+@pytest.mark.parametrize("name", ["h2o2_9_21", "gri_53_325"])
+def test_vjp_gather_tables_replay(name, tmp_path):
+    """The warp-cooperative adjoint's species-major entry list: replayed on
+    random per-reaction terms, d/dC_k = sum_i (nu'_ki a c R_f,i + nu''_ki
+    (-a c R_r,i)) / C_k + sum_i (eff_ki - eff_default,i) a (R_f - R_r)_i."""
+    mech_obj = synth.mechanism(name)
+    path = synth.mechanism_file(name, str(tmp_path))
+    m = kx.Mechanism(path, cache_dir=str(tmp_path / "cache"), compile_only=1, lazy=1, vjp_layout=2)
+    src = m.kernel_source("vjp")
+    ns, nr = mech_obj.n_species, len(mech_obj.reactions)
+    rng = np.random.default_rng(5)
+    af, ar, gx, ic = rng.standard_normal(nr), rng.standard_normal(nr), rng.standard_normal(nr), rng.standard_normal(ns)
+    want = np.zeros(ns)
+    for i, r in enumerate(mech_obj.reactions):
+        for k, c in r.reactants:
+            want[k] += c * af[i] * ic[k]
+        if r.reversible:
+            for k, c in r.products:
+                want[k] += c * ar[i] * ic[k]
+        if r.uses_third_body():
+            if r.collider is not None:
+                want[r.collider] += gx[i]
+            else:
+                for k, e in r.efficiencies.items():
+                    if e != r.default_eff:
+                        want[k] += (e - r.default_eff) * gx[i]
+    got = _vjp_replay(src, mech_obj, af, ar, gx, ic)
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-5)
