@@ -132,9 +132,17 @@ typedef struct {
                          reaction's rate mantissa times a per-state reciprocal 1/|C_k| (log space
                          only where the rate underflows); 1 one log-space exponential
                          exp(ln |R| - ln |C_k|) per entry (no reciprocal table) */
-  int vjp_layout;     /* double-float adjoint: 0 (default) or 1 one thread per state; 2
-                         warp-cooperative (one state per warp, its vectors and per-reaction terms
-                         in shared memory, d/dC_k gathered species-major) */
+  int vjp_layout;     /* double-float adjoint: 0 (default) by batch size -- the warp-cooperative
+                         kernel for batches below min(C, 8192 w u^2) states, C the thread-per-state
+                         kernel's resident capacity, w the warp-cooperative kernel's resident warps
+                         per SM and u the share of lane slots its class rounds fill (the crossover
+                         measured on GB300: ~8k states for 9/21, ~85k for 53/325, ~32k for
+                         160/900), one thread per state from there on; 1 always one thread per
+                         state; 2 always warp-cooperative (one state per warp, its vectors and
+                         per-reaction terms in shared memory, d/dC_k gathered species-major;
+                         mechanisms whose warp slice exceeds 50 KB keep one thread per state
+                         under 0 and are refused under 2).  The two agree to ~1e-10 of each
+                         entry's term scale, not bit for bit. */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 
@@ -192,7 +200,8 @@ kx_status kx_diffusion(kx_handle h, const double* T, const double* p, const doub
  * derivative term formed from the log-space rates (so an absent species,
  * Y_k = 0, keeps its exact derivative) and accumulated under a running
  * power-of-two scale of its own; kx_options.rates_arith = 1 selects the
- * native float64 kernel.  One thread per point. */
+ * native float64 kernel.  One thread per point, or, for batches below the
+ * crossover that kx_options.vjp_layout describes, one warp per point. */
 kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                                   const double* v, double* gT, double* gY, int64_t n, void* stream);
 
@@ -253,8 +262,10 @@ kx_status kx_production_rates_noalloc(kx_handle h, const double* T, const double
 /* Per-kernel build facts of a handle, for logs and benchmarks: kernel names
  * are "wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo",
  * "visc_fp64", "visc_mixed", "diff_fp64", "diff_mixed", "vjp" and
- * "wdot_fp64_noalloc" (the kernel of kx_production_rates_noalloc) and
- * "wdot_fp64_wc" (the warp-cooperative production-rate kernel).  Any
+ * "wdot_fp64_noalloc" (the kernel of kx_production_rates_noalloc),
+ * "wdot_fp64_wc" (the warp-cooperative production-rate kernel) and
+ * "vjp_wc" (the warp-cooperative adjoint of small batches; absent when
+ * kx_options.vjp_layout or rates_arith fixes the adjoint kernel).  Any
  * output pointer may be NULL.  registers and local_bytes: per thread, from
  * the compiler's report (local_bytes is the stack frame: local arrays and
  * register spills, the local memory the driver backs for every resident

@@ -56,6 +56,7 @@ struct Kernel {
   double compile_seconds = 0;
   int registers = -1, local_bytes = -1;
   int max_blocks = 0;          // resident blocks for a persistent grid (per device 0 at load)
+  int blocks_per_sm = 0;       // resident blocks per SM
   int smem = 0;                // dynamic shared memory per block, bytes
   int states_per_block = 0;    // states one block serves per pass of its grid-stride loop (0: one per thread)
   double lane_use = 1.0;       // warp-cooperative kernels: lane use of their class rounds
@@ -221,6 +222,7 @@ kx_status load_kernel(Kernel& k) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.fn, k.eopt.block, k.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   k.max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+  k.blocks_per_sm = per_sm > 0 ? per_sm : 1;
   k.device = dev;
   return KX_OK;
 }
@@ -352,6 +354,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
       {"diff_fp64", kx::KernelKind::Transport, false, 2}, {"visc_mixed", kx::KernelKind::Transport, true, 1},
       {"diff_mixed", kx::KernelKind::Transport, true, 2}, {"vjp", kx::KernelKind::Vjp, false, 0},
       {"wdot_fp64_noalloc", kx::KernelKind::Wdot, false, 0}, {"wdot_fp64_wc", kx::KernelKind::Wdot, false, 0},
+      {"vjp_wc", kx::KernelKind::Vjp, false, 0},
   };
   for (const Spec& sp : specs) {
     std::unique_ptr<Kernel> k(new Kernel());
@@ -374,11 +377,22 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.rates_group = h->opt.rates_group;
     k->eopt.vjp_form = h->opt.vjp_form;
     k->eopt.vjp_layout = h->opt.vjp_layout;
+    const bool vjp_wc_spec = std::strcmp(sp.name, "vjp_wc") == 0;
+    if (vjp_wc_spec) {
+      // the warp-cooperative adjoint beside the default one, for small batches
+      if (h->opt.vjp_layout != 0 || h->opt.rates_arith == 1) continue;
+      k->eopt.vjp_layout = 2;
+      kx::EmitOptions one = k->eopt;
+      one.rates_group = 1;
+      k->lane_use = kx::wdot_wc_shape(h->m, one).lane_use;
+    }
     if (kx::vjp_is_wc(h->m, sp.kind, k->eopt)) {
       k->smem = kx::vjp_wc_smem(h->m, k->eopt);
       k->states_per_block = k->eopt.block / 32;
-      if (k->smem > 200 * 1024)
+      if (k->smem > 200 * 1024) {
+        if (vjp_wc_spec) continue;   // too large for small batches too: the default adjoint serves them
         return fail(KX_ERR_UNSUPPORTED, "warp-cooperative adjoint: one block's shared memory exceeds 200 KB (vjp_layout 1)");
+      }
     }
     if (kx::wdot_is_wc(h->m, sp.kind, k->eopt)) {
       const kx::WcShape w = kx::wdot_wc_shape(h->m, k->eopt);
@@ -478,6 +492,26 @@ kx_status wdot_kernel_for(kx_mech* h, int64_t n, kx_precision precision, const c
   if (s != KX_OK) return s;
   const int64_t cap = (int64_t)tps->max_blocks * tps->eopt.block;
   if (n < std::min<int64_t>(cap, (int64_t)(49152.0 * wc->lane_use))) *name = "wdot_fp64_wc";
+  return KX_OK;
+}
+
+// The adjoint kernel for a batch of n states.  Small batches go to the warp-cooperative adjoint (one
+// state per warp) by default.  Its throughput grows with its resident warps per SM and, twice, with
+// the lane use u of its class rounds (reaction rounds and, for small mechanisms, the species
+// phases); the crossover measured on GB300 fits 8192 x resident warps per SM x u^2 states (9/21:
+// ~8k measured, 6.3k by the rule; 53/325: 65k-131k, 84k; 160/900: ~32k, 29k), and is kept below
+// the thread-per-state kernel's resident capacity.
+kx_status vjp_kernel_for(kx_mech* h, int64_t n, const char** name) {
+  *name = "vjp";
+  Kernel* wc = find_kernel(h, "vjp_wc");
+  if (!wc) return KX_OK;
+  Kernel* tps = find_kernel(h, "vjp");
+  kx_status s = ensure_ready(h, *tps);
+  if (s == KX_OK) s = ensure_ready(h, *wc);
+  if (s != KX_OK) return s;
+  const int64_t cap = (int64_t)tps->max_blocks * tps->eopt.block;
+  const double warps = (double)wc->blocks_per_sm * (wc->eopt.block / 32);
+  if (n < std::min<int64_t>(cap, (int64_t)(8192.0 * warps * wc->lane_use * wc->lane_use))) *name = "vjp_wc";
   return KX_OK;
 }
 
@@ -632,9 +666,11 @@ kx_status kx_production_rates_vjp(kx_handle h, const double* T, const double* p,
   if (s != KX_OK) return s;
   if (n > 0 && (!v || !gT || !gY)) return fail(KX_ERR_ARG, "null argument");
   if (n == 0) return KX_OK;
+  const char* name = nullptr;
+  if ((s = vjp_kernel_for(h, n, &name)) != KX_OK) return s;
   long long ldl = ld, nl = n;
   void* args[] = {&T, &p, &Y, &ldl, &v, &gT, &gY, &nl};
-  return launch(h, "vjp", args, n, stream);
+  return launch(h, name, args, n, stream);
 }
 
 kx_status kx_kernel_info(kx_handle h, const char* kernel, int* registers, int* local_bytes, double* compile_seconds,

@@ -3662,8 +3662,10 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   // ---- gather table: per species k, its reactant entries (kind 0: nu'_k a c R_f / C_k), product entries
   // of reversible reactions (kind 1: -nu''_k a c R_r / C_k) and third-body efficiencies (kind 2:
   // (eff_k - eff_default) a (R_f - R_r) [dln k_f/d[X]], or 1 for a named collider); entry bits:
-  // reaction 0-13, kind 14-15, species 16-30, "last of its slot" 31; the coefficient as a float
-  struct GE { int r, kind, k; float coef; };
+  // reaction 0-13, kind 14-15, species 16-30, "last of its slot" 31; the coefficient as a float pair
+  // (stoichiometric coefficients are exact in its high part, efficiency differences such as 0.7 - 1
+  // are not)
+  struct GE { int r, kind, k; double coef; };
   std::vector<GE> ent;
   for (int k = 0; k < ns; ++k)
     for (int i = 0; i < nr; ++i) {
@@ -3671,17 +3673,17 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
       int a = 0, b = 0;
       for (auto& s : r.reac) if (s.first == k) a += s.second;
       for (auto& s : r.prod) if (s.first == k) b += s.second;
-      if (a) ent.push_back({i, 0, k, (float)a});
-      if (b && r.reversible) ent.push_back({i, 1, k, (float)b});
+      if (a) ent.push_back({i, 0, k, (double)a});
+      if (b && r.reversible) ent.push_back({i, 1, k, (double)b});
       if (r.third_body()) {
-        if (r.collider >= 0) { if (r.collider == k) ent.push_back({i, 2, k, 1.0f}); }
-        else for (auto& e : r.eff) if (e.first == k && e.second != r.default_eff) ent.push_back({i, 2, k, (float)(e.second - r.default_eff)});
+        if (r.collider >= 0) { if (r.collider == k) ent.push_back({i, 2, k, 1.0}); }
+        else for (auto& e : r.eff) if (e.first == k && e.second != r.default_eff) ent.push_back({i, 2, k, e.second - r.default_eff});
       }
     }
   if (nr >= (1 << 14) || ns >= (1 << 15)) return "";
   const int NCH = 32, NE = (int)ent.size();
   const int CL = std::max(1, (NE + NCH - 1) / NCH);
-  std::vector<std::pair<int32_t, float>> tab((size_t)CL * NCH, {0, 0.0f});
+  std::vector<std::pair<int32_t, double>> tab((size_t)CL * NCH, {0, 0.0});
   std::vector<int> chslot(NCH, 0), sfirst(ns, 0), scount(ns, 0);
   int nslot = 0;
   for (int ch = 0; ch < NCH; ++ch) {
@@ -3698,8 +3700,9 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   if (nslot > 2 * SVS) return "";
   {
     std::string t;
-    for (auto& v : tab) t += fmt("{%d,%s},", v.first, F(v.second).c_str());
-    g(fmt("__device__ const __align__(8) struct { int w; float c; } kx_vtab[%d] = {%s{0,0.0f}};", (int)tab.size() + 1, t.c_str()));
+    for (auto& v : tab) t += fmt("{%d,%s,0},", v.first, fpair(v.second).c_str());
+    g(fmt("__device__ const __align__(16) struct { int w; float c, cl; int pad; } kx_vtab[%d] = {%s{0,0.0f,0.0f,0}};",
+          (int)tab.size() + 1, t.c_str()));
     std::string cs, ss;
     for (int ch = 0; ch < NCH; ++ch) cs += std::to_string(chslot[ch]) + ",";
     for (int k = 0; k < ns; ++k) ss += fmt("{%d,%d},", sfirst[k], scount[k]);
@@ -4024,18 +4027,19 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   o("#pragma unroll 2");
   o(fmt("for (int j = 0; j < %d; ++j) {", CL));
   o(fmt("  const int wv = kx_vtab[%d * j + lane].w;", NCH));
-  o(fmt("  const float cf = kx_vtab[%d * j + lane].c;", NCH));
+  o(fmt("  const float cf = kx_vtab[%d * j + lane].c, cl = kx_vtab[%d * j + lane].cl;", NCH, NCH));
   o("  if (cf != 0.0f) {");
   o("    const int r = wv & 0x3fff, kind = (wv >> 14) & 3, k = (wv >> 16) & 0x7fff;");
   o("    kx_df mt;");
   o("    int et;");
-  o("    if (kind == 2) { const float2 gx = rx[r]; mt = kx_mk(gx.x, gx.y); et = re[r].z; }");
+  o("    if (kind == 2) { const float2 gx = rx[r]; mt = kx_df_mul_u(kx_mk(gx.x, gx.y), kx_mk(cf, cl)); et = re[r].z; }");
   o("    else {");
   o("      const float4 q = rf[r], iq = ic[k];");
   o("      mt = kx_df_mul_u(kind == 0 ? kx_mk(q.x, q.y) : kx_mk(q.z, q.w), kx_mk(iq.x, iq.y));");
   o("      et = (kind == 0 ? re[r].x : re[r].y) + __float_as_int(iq.z);");
+  o("      mt = kx_df_mulf(mt, cf);   // an integer stoichiometric coefficient");
   o("    }");
-  o("    kx_acc_add(acc, as, kx_df_mulf(mt, cf), et);");
+  o("    kx_acc_add(acc, as, mt, et);");
   o("  }");
   o("  if (wv < 0) { slot[sl++] = make_float4(acc.hi, acc.lo, __int_as_float(as), 0.0f); acc = kx_mk(0.0f, 0.0f); as = -100000; }");
   o("}");

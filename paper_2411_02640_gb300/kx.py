@@ -21,7 +21,7 @@ KX_ERR_NONFINITE_INPUT = 9   # kx_last_point_status: a point outside the domain 
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 KERNELS = ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "visc_fp64", "visc_mixed", "diff_fp64",
-           "diff_mixed", "vjp")
+           "diff_mixed", "vjp", "wdot_fp64_noalloc", "wdot_fp64_wc", "vjp_wc")
 
 
 class KxError(RuntimeError):

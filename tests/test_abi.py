@@ -61,7 +61,7 @@ def test_emitted_kernels_compile_for_sm103a(name, tmp_path):
     path = synth.mechanism_file(name, str(tmp_path))
     m = kx.Mechanism(path, compile_only=1, cache_dir=str(tmp_path / "cache"))
     for k in ("wdot_fp64", "wdot_mixed", "rop_fp64", "rop_mixed", "thermo", "visc_fp64", "visc_mixed", "diff_fp64",
-              "diff_mixed", "vjp"):
+              "diff_mixed", "vjp", "vjp_wc", "wdot_fp64_wc", "wdot_fp64_noalloc"):
         info = m.kernel_info(k)
         assert 0 < info["registers"] <= 255, (k, info)
     # a compile-only handle refuses launches

@@ -20,11 +20,12 @@ def torch():
     return torch_cuda()
 
 
-@pytest.mark.parametrize("opts", [{}, {"rates_arith": 1}, {"vjp_layout": 2}])
+@pytest.mark.parametrize("opts", [{"vjp_layout": 1}, {"rates_arith": 1}, {"vjp_layout": 2}])
 @pytest.mark.parametrize("name,n", [("h2o2_9_21", 300), ("gri_53_325", 256), ("large_160_900", 64)])
 def test_vjp_matches_oracle_jacobian(torch, name, n, opts):
-    """{}: the double-float adjoint, one thread per state (default); rates_arith 1: native
-    float64; vjp_layout 2: the warp-cooperative double-float adjoint."""
+    """vjp_layout 1: the double-float adjoint, one thread per state; rates_arith 1: native
+    float64; vjp_layout 2: the warp-cooperative double-float adjoint (the default's choice for
+    batches this small)."""
     T, p, Y = _states(name, n, start=1000)
     mech = mechanism(name, **opts)
     rng = np.random.default_rng(7)
@@ -42,7 +43,8 @@ def test_vjp_matches_oracle_jacobian(torch, name, n, opts):
         assert np.all(np.abs(got - ref) <= tol + 1e-9 * scale), (i, np.max(np.abs(got - ref) / (scale + 1e-300)))
 
 
-@pytest.mark.parametrize("opts", [{}, {"vjp_form": 1}, {"rates_arith": 1}, {"vjp_layout": 2}])
+@pytest.mark.parametrize("opts", [{"vjp_layout": 1}, {"vjp_layout": 1, "vjp_form": 1}, {"rates_arith": 1},
+                                  {"vjp_layout": 2}])
 def test_vjp_absent_and_negative_species(torch, opts):
     """States with species absent (Y_k = 0 exactly, as in a fresh mixture) and
     small negative mass fractions: the derivative with respect to an absent
@@ -70,6 +72,28 @@ def test_vjp_absent_and_negative_species(torch, opts):
         scale = np.abs(v[:, i]) @ np.abs(J)
         got = np.concatenate([[gT[i]], gY[:, i]])
         assert np.all(np.abs(got - ref) <= 1e-9 * scale.max() + 1e-9 * scale), (i, np.max(np.abs(got - ref) / (scale + 1e-300)))
+
+
+def test_automatic_adjoint_choice_follows_the_batch_size(torch):
+    """Below the crossover the default handle gives exactly the warp-cooperative
+    adjoint's results, above it exactly the thread-per-state adjoint's; the
+    two agree within the adjoint's bar on both sides."""
+    name = "gri_53_325"
+    auto, tps, wc = mechanism(name), mechanism(name, vjp_layout=1), mechanism(name, vjp_layout=2)
+    ns = auto.n_species
+    T, p, Y = synth.make_states_torch(ns, synth.STATE_SPECS[name], 1 << 18, seed=21)
+    v = torch.randn((ns, 1 << 18), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    for n, same in ((1 << 12, wc), (1 << 18, tps)):
+        args = (T[:n], p[:n], Y[:, :n].contiguous(), v[:, :n].contiguous())
+        a = auto.production_rates_vjp(*args)
+        b = same.production_rates_vjp(*args)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), n
+        c = (tps if same is wc else wc).production_rates_vjp(*args)
+        for x, y in zip(a, c):
+            # per state, relative to its largest entry (gY) or to the batch's largest (gT); measured
+            # ~1e-10 between the two kernels and each against native float64
+            sc = torch.abs(y).amax(0).clamp_min(1e-300)
+            assert torch.all(torch.abs(x - y) <= 1e-8 * sc), n
 
 
 def test_autograd_function_and_finite_differences(torch):

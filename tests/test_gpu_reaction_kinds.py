@@ -72,7 +72,7 @@ def test_rates_of_progress_all_kinds(kinds):
     assert (np.abs(qm - ref) / gross).max() <= 2e-4
 
 
-@pytest.mark.parametrize("opts", [{}, {"rates_arith": 1}, {"vjp_layout": 2}])
+@pytest.mark.parametrize("opts", [{"vjp_layout": 1}, {"rates_arith": 1}, {"vjp_layout": 2}])
 def test_adjoint_all_kinds(kinds, opts, tmp_path_factory):
     """Every reaction kind: the double-float adjoint (thread per state and warp-cooperative) and
     native float64."""

@@ -103,8 +103,10 @@ def test_gather_tables_every_group_size(group, tmp_path):
 
 def _vjp_replay(src, mech_obj, af, ar, gx, ic):
     m = re.search(r"kx_vtab\[(\d+)\] = \{(.*?)\};", src, re.S)
-    pairs = re.findall(r"\{(-?\d+),\(?([-+0-9.eE]+)f?\)?\}", m.group(2))
-    tab = [(int(w) & 0xffffffff, float(c)) for w, c in pairs][:-1]
+    num = r"\(?([-+0-9.eE]+)f?\)?"
+    entries = re.findall(r"\{(-?\d+),%s,%s,0\}" % (num, num), m.group(2))
+    tab = [(int(w) & 0xffffffff, float(np.float32(c)) + float(np.float32(cl))) for w, c, cl in entries][:-1]
+    svs = max(mech_obj.n_species + 1, (mech_obj.n_species + 33) // 2)
     chs = _array(src, "kx_vchs")[:-1]
     ws = np.array(_array(src, "kx_vslot")).reshape(-1, 2)[:mech_obj.n_species]
     nch = len(chs)
@@ -118,6 +120,7 @@ def _vjp_replay(src, mech_obj, af, ar, gx, ic):
                 r, kind, k = w & 0x3FFF, (w >> 14) & 3, (w >> 16) & 0x7FFF
                 acc += cf * (gx[r] if kind == 2 else (af[r] if kind == 0 else ar[r]) * ic[k])
             if w & 0x80000000:
+                assert sl < 2 * svs, "slot outside the species vectors"
                 slots[sl] = acc
                 sl, acc = sl + 1, 0.0
     return np.array([sum(slots[f + j] for j in range(c)) for f, c in ws])
@@ -150,4 +153,5 @@ def test_vjp_gather_tables_replay(name, tmp_path):
                     if e != r.default_eff:
                         want[k] += (e - r.default_eff) * gx[i]
     got = _vjp_replay(src, mech_obj, af, ar, gx, ic)
-    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-5)
+    # coefficients as float pairs: efficiency differences (0.7 - 1 and the like) to about 2^-48
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
