@@ -803,6 +803,40 @@ def run_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep_adjoint(args):
+    """Batch-size sweep of the adjoint (one call of kx_production_rates_vjp,
+    N(0,1) cotangents) on 9/21, 53/325 (2^8 .. 2^18 states) and 160/900
+    (2^8 .. 2^16): one thread per state (vjp_layout 1), one warp per state
+    (vjp_layout 2) and the default choice between them."""
+    import torch
+    from paper_2411_02640_gb300 import kx, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {"metric": "adjoint batch-size sweep", "unit": "ms per call", "rows": []}
+    for name, lmax in (("h2o2_9_21", 18), (MECH, 18), ("large_160_900", 16)):
+        path = synth.mechanism_file(name, os.path.join(CACHE, "mech"))
+        forms = {"tps": kx.Mechanism(path, cache_dir=CACHE, lazy=1, vjp_layout=1),
+                 "wc": kx.Mechanism(path, cache_dir=CACHE, lazy=1, vjp_layout=2),
+                 "default": kx.Mechanism(path, cache_dir=CACHE, lazy=1)}
+        ns = forms["tps"].n_species
+        spec = synth.STATE_SPECS[name]
+        T, p, Y = synth.make_states_torch(ns, spec, 1 << lmax, seed=spec.seed)
+        v = torch.randn((ns, 1 << lmax), dtype=torch.float64, device="cuda",
+                        generator=torch.Generator("cuda").manual_seed(1))
+        for lg in range(8, lmax + 1):
+            n = 1 << lg
+            a = (T[:n], p[:n], Y[:, :n].contiguous(), v[:, :n].contiguous())
+            row = {"mechanism": name, "points": n}
+            for key, m in forms.items():
+                g = m.production_rates_vjp(*a)
+                row[key + "_ms"] = time_calls(lambda: m.production_rates_vjp(*a, out=g), max(3, min(200, (1 << 20) // n)),
+                                              3, stream)
+            row["default_mpoints_s"] = n / (row["default_ms"] * 1e-3) / 1e6
+            out["rows"].append(row)
+        del T, p, Y, v
+    print(json.dumps(out), flush=True)
+
+
 def large_block(mech, dev, stream, K, W, sm_max, n=1 << 22, name="large_160_900"):
     """Production rates of the 160/900 mechanism at 2^22 states (states drawn on
     the device with torch's seeded generator): float64-accurate and mixed
@@ -838,7 +872,7 @@ def run_profile_rates(args):
     torch.cuda.set_device(0)
     spec = synth.STATE_SPECS[args.mech]
     opts = dict(rates_layout=args.rates_layout, rates_group=args.rates_group, maxrreg=args.maxrreg,
-                rates_arith=args.rates_arith, block=args.block, lazy=1)
+                rates_arith=args.rates_arith, block=args.block, vjp_layout=args.vjp_layout, lazy=1)
     m = kx.Mechanism(synth.mechanism_file(args.mech, os.path.join(CACHE, "mech")), cache_dir=CACHE, **opts)
     T, p, Y = synth.make_states_torch(m.n_species, spec, args.points, seed=spec.seed)
     if args.profile_call == "vjp":
@@ -878,6 +912,7 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="measure the arithmetic pipes' per-clock rates only")
     ap.add_argument("--write-peaks", action="store_true", help="with --peaks: store the record the roofline reads")
     ap.add_argument("--sweep", action="store_true", help="point-count sweep of the step on 9/21 and 53/325 only")
+    ap.add_argument("--sweep-adjoint", action="store_true", help="batch-size sweep of the adjoint's two kernels only")
     ap.add_argument("--profile-rates", action="store_true",
                     help="two production-rate calls on --mech at --points states (a driver for ncu captures)")
     ap.add_argument("--mech", default=MECH, help="mechanism of --profile-rates")
@@ -887,6 +922,8 @@ def main():
     ap.add_argument("--rates-layout", type=int, default=0,
                     help="float-pair rates: 0 by batch size, 1 thread per state, 2 warp-cooperative")
     ap.add_argument("--rates-group", type=int, default=0, help="warp-cooperative rates: states per warp (0: one)")
+    ap.add_argument("--vjp-layout", type=int, default=0,
+                    help="adjoint of --profile-call vjp: 0 by batch size, 1 thread per state, 2 warp-cooperative")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the native float64, 9/21 (4096 states) and 160/900 blocks of the default line")
     args = ap.parse_args()
@@ -900,6 +937,8 @@ def main():
         run_profile_rates(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.sweep_adjoint:
+        run_sweep_adjoint(args)
     elif args.serve:
         print(json.dumps({"metric": "serving", "serving": run_serve_suite(args, sweep=True)}), flush=True)
     else:

@@ -515,6 +515,18 @@ __device__ __forceinline__ kx_df kx_df_exp_m(kx_df x, int& p) {
   p = k >> 8;
   return kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
 }
+// m1 2^e1 - m2 2^e2 as a float pair times 2^e, e = max(e1, e2): the term with the smaller power of
+// two is brought to the larger's (dropped below 2^-126 of it), then one float-pair subtraction.  In
+// double-float arithmetic this is as accurate as forming the difference from the log-ratio of the two
+// terms: both lose relative precision as 1/|ln(m1 2^e1 / m2 2^e2)| near cancellation, from the
+// absolute error of the logarithms the terms come from.
+__device__ __forceinline__ kx_df kx_df_sub_m(kx_df m1, int e1, kx_df m2, int e2, int& e) {
+  e = max(e1, e2);
+  const int d1 = e1 - e, d2 = e2 - e;
+  const float s1 = d1 >= -126 ? __int_as_float((d1 + 127) << 23) : 0.0f;
+  const float s2 = d2 >= -126 ? __int_as_float((d2 + 127) << 23) : 0.0f;
+  return kx_df_sub(kx_mk(__fmul_rn(m1.hi, s1), __fmul_rn(m1.lo, s1)), kx_mk(__fmul_rn(m2.hi, s2), __fmul_rn(m2.lo, s2)));
+}
 // A running sum as a float pair under its own scale 2^-s, 16 bytes (one load and one store).
 struct __align__(16) kx_acc { float hi, lo; int s, pad; };
 __device__ __forceinline__ void kx_acc_add(kx_df& acc, int& s, kx_df m, int e);
@@ -2536,9 +2548,16 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c, bool recip) {
     for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
     for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
     o("  const int sf = " + sfx + ";");
-    o("  kx_df L = lf, fac = kx_mk(1.0f, 0.0f), lr = kx_mk(0.0f, 0.0f);");
-    o("  int sq = sf;   // sign of R_f - R_r");
+    o("  kx_df lr = kx_mk(0.0f, 0.0f);");
     c.fp32 += NC * (d.nre * kDfAdd);
+    // R_f = mfs 2^ef (signed); for reversible reactions R_r = mr 2^er (signed), and R_f - R_r and the
+    // temperature term from the two by aligned subtraction (two exponentials per reaction)
+    o("  int ef;");
+    o(fmt("  kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);   // |R_f| = mf 2^ef", shift.c_str()));
+    o("  if (lf.hi <= -740.0f) ef -= 2016;");
+    o("  const kx_df mfs = sf ? kx_df_neg(mf) : mf;");
+    c.fp32 += NC * kDfExp;
+    const bool need_q = tb;
     if (d.rev) {
       const int dn = d.npr - d.nre;
       o("  const int sr = " + srx + ";");
@@ -2549,46 +2568,27 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c, bool recip) {
       if (dn == 1 || dn == -1) o(fmt("  dl = kx_df_add_u(dl, %s);", dn == 1 ? "kx_df_neg(lnPRT)" : "lnPRT"));
       else if (dn != 0) o(fmt("  dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, %s));", F(-dn).c_str()));
       o("  lr = kx_df_add_u(lf, dl);");
-      o("  {");
-      o("    const bool rv = dl.hi > 0.0f;");
-      o("    if (rv) L = lr;");
-      o("    const kx_df ex = kx_df_exp_n(rv ? kx_df_neg(dl) : dl);");
-      o("    const float pm = sf == sr ? -1.0f : 1.0f;");
-      o("    const kx_df s1 = kx_qts(1.0f, pm * ex.hi);");
-      o("    fac = kx_mk(s1.hi, __fmaf_rn(pm, ex.lo, s1.lo));");
-      o("    if (sf == sr) sq = sf ^ (int)rv;");
-      o("  }");
-      c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 10);
-      // R_r = sign e^(lr): exponent and signed mantissa
       o("  int er;");
       o(fmt("  kx_df mr = kx_df_exp_m(lr.hi <= -740.0f ? kx_df_add(lr, %s) : lr, er);", shift.c_str()));
       o("  if (lr.hi <= -740.0f) er -= 2016;");
-      o("  if (sr) mr = kx_df_neg(mr);");
-      c.fp32 += NC * kDfExp;
-      (void)dn;
-    }
-    o("  int eq;");
-    o("  kx_df mq = kx_df_mul_u(kx_df_exp_m(L, eq), fac);   // R_f - R_r = mq 2^eq");
-    o("  if (sq) mq = kx_df_neg(mq);");
-    c.fp32 += NC * (kDfExp + kDfMul);
-    // d/dT at fixed concentrations and chemical potentials
-    o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mq), eq);", aq.c_str()));
-    c.fp32 += NC * (2 * kDfMul + 20);
-    if (d.rev) {
-      const int dn = d.npr - d.nre;
-      o("  // d/dT through R_r at fixed C: a c R_r / T (sum_k nu_k H_k/RT - dn), the first part being the");
-      o("  // chemical potentials' -dG_k/RT/dT = H_k/(R T^2) (Gibbs-Helmholtz) times d q/d(G_k/RT) = -c nu_k R_r");
-      o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(kx_df_mul_u(%s, mr), iT), %s), er);", aq.c_str(),
+      o("  if (sr) mr = kx_df_neg(mr);   // R_r = mr 2^er");
+      o("  // d/dT at fixed C: a c (dln k_f/dT (R_f - R_r) + R_r/T (sum_k nu_k H_k/RT - dn)), the second part");
+      o("  // the chemical potentials' -dG_k/RT/dT = H_k/(R T^2) (Gibbs-Helmholtz) times d q/d(G_k/RT) =");
+      o("  // -c nu_k R_r; as one term: a c (R_f dT - R_r (dT - (dh - dn)/T))");
+      o(fmt("  { int et; const kx_df t = kx_df_sub_m(kx_df_mul_u(mfs, dT), ef, kx_df_mul_u(mr, kx_df_sub(dT, kx_df_mul(iT, %s))), er, et);",
             dn != 0 ? fmt("kx_df_add(dh, kx_mk(%s, 0.0f))", F(-dn).c_str()).c_str() : "dh"));
-      c.fp32 += NC * (3 * kDfMul + kDfAdd + 20);
+      o(fmt("    kx_acc_add(gTa, sT, kx_df_mul_u(%s, t), et); }", aq.c_str()));
+      if (need_q) o("  int eq; const kx_df mq = kx_df_sub_m(mfs, ef, mr, er, eq);   // R_f - R_r = mq 2^eq");
+      c.fp32 += NC * ((E - 1) * kDfAdd + (dn ? kDfAdd + kDfMulf : 0) + kDfAdd + kDfExp + 4 * kDfMul + 2 * kDfAdd + 8 + 20);
+      if (need_q) c.fp32 += NC * (kDfAdd + 8);
+    } else {
+      o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mfs), ef);   // d/dT at fixed C: a c dln k_f/dT R_f", aq.c_str()));
+      if (need_q) o("  const int eq = ef; const kx_df mq = mfs;");
+      c.fp32 += NC * (2 * kDfMul + 20);
     }
     // d/dC_k: one term per entry, R/C_k with the sign of R/C_k: as |R| = m 2^e and 1/|C_k| = m' 2^e'
     // (per state), a product of mantissas (recip), or one log-space exponential exp(ln |R| - ln |C_k|)
     // per entry
-    o("  int ef;");
-    o(fmt("  kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);   // |R_f| = mf 2^ef", shift.c_str()));
-    o("  if (lf.hi <= -740.0f) ef -= 2016;");
-    c.fp32 += NC * kDfExp;
     if (!recip) {
       for (int j = 0; j < E; ++j) {
         const bool reac = j < d.nre;
@@ -2598,7 +2598,7 @@ void emit_vjp_df(Out& o, Out& g, const Mechanism& m, OpCounts& c, bool recip) {
         o(fmt("    kx_acc_add(gc[k%d], kx_df_mul_u(%s, mt), et); }", j, reac ? aq.c_str() : ("kx_df_neg(" + aq + ")").c_str()));
       }
     } else {
-      o(fmt("  { const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
+      o(fmt("  { const kx_df af = kx_df_mul_u(%s, mfs);", aq.c_str()));
       if (d.rev) o(fmt("    const kx_df ar = kx_df_mul_u(%s, mr);   // mr carries the sign of R_r", ("kx_df_neg(" + aq + ")").c_str()));
       for (int j = 0; j < E; ++j) {
         const bool reac = j < d.nre;
@@ -3617,7 +3617,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
 //   5. the chain to (T, Y) in float64 (lane sums reduced in a fixed butterfly order).
 struct VwLayout {
   int svs = 1, nw32 = 1;
-  int off_sv = 0, off_vh = 0, off_ic = 0, off_yv = 0, off_rf = 0, off_re = 0, off_rx = 0, off_nm = 0, warp_bytes = 0;
+  int off_sv = 0, off_vh = 0, off_ic = 0, off_yv = 0, off_rf = 0, off_re = 0, off_tb = 0, off_nm = 0, warp_bytes = 0;
 };
 
 VwLayout vjp_wc_layout(const Mechanism& m) {
@@ -3630,10 +3630,12 @@ VwLayout vjp_wc_layout(const Mechanism& m) {
   L.off_vh = L.off_sv + 16 * L.svs;
   L.off_ic = L.off_vh + 16 * L.svs;
   L.off_yv = L.off_ic + 16 * L.svs;
+  int ntb = 0;
+  for (auto& r : m.rx) ntb += r.third_body() ? 1 : 0;
   L.off_rf = up16(L.off_yv + 8 * L.svs);
   L.off_re = L.off_rf + 16 * nr;
-  L.off_rx = L.off_re + 16 * nr;
-  L.off_nm = up16(L.off_rx + 8 * nr);
+  L.off_tb = up16(L.off_re + 8 * nr);
+  L.off_nm = L.off_tb + 16 * std::max(ntb, 1);
   L.warp_bytes = up16(L.off_nm + 4 * L.nw32);
   return L;
 }
@@ -3645,6 +3647,13 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   const int SVS = L.svs, NW32 = L.nw32;
   std::vector<DfClass> cls = emit_class_tables(g, m, true);
   const std::string shift = DFc(2016.0 * std::log(2.0));
+  // third-body reactions' slots in the per-warp third-body array: consecutive in class order
+  std::vector<int> tbslot(nr, -1), tbbase(cls.size(), 0), tbreac;
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    tbbase[ci] = (int)tbreac.size();
+    if (m.rx[cls[ci].rx[0]].third_body())
+      for (int i : cls[ci].rx) { tbslot[i] = (int)tbreac.size(); tbreac.push_back(i); }
+  }
   // H/RT coefficients as float pairs per species and range
   {
     std::string hf, iwd;
@@ -3662,7 +3671,8 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   // ---- gather table: per species k, its reactant entries (kind 0: nu'_k a c R_f / C_k), product entries
   // of reversible reactions (kind 1: -nu''_k a c R_r / C_k) and third-body efficiencies (kind 2:
   // (eff_k - eff_default) a (R_f - R_r) [dln k_f/d[X]], or 1 for a named collider); entry bits:
-  // reaction 0-13, kind 14-15, species 16-30, "last of its slot" 31; the coefficient as a float pair
+  // reaction (kind 2: its third-body slot) 0-13, kind 14-15, species 16-30, "last of its slot" 31; the
+  // coefficient as a float pair
   // (stoichiometric coefficients are exact in its high part, efficiency differences such as 0.7 - 1
   // are not)
   struct GE { int r, kind, k; double coef; };
@@ -3676,8 +3686,8 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
       if (a) ent.push_back({i, 0, k, (double)a});
       if (b && r.reversible) ent.push_back({i, 1, k, (double)b});
       if (r.third_body()) {
-        if (r.collider >= 0) { if (r.collider == k) ent.push_back({i, 2, k, 1.0}); }
-        else for (auto& e : r.eff) if (e.first == k && e.second != r.default_eff) ent.push_back({i, 2, k, e.second - r.default_eff});
+        if (r.collider >= 0) { if (r.collider == k) ent.push_back({tbslot[i], 2, k, 1.0}); }
+        else for (auto& e : r.eff) if (e.first == k && e.second != r.default_eff) ent.push_back({tbslot[i], 2, k, e.second - r.default_eff});
       }
     }
   if (nr >= (1 << 14) || ns >= (1 << 15)) return "";
@@ -3707,6 +3717,9 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
     for (int ch = 0; ch < NCH; ++ch) cs += std::to_string(chslot[ch]) + ",";
     for (int k = 0; k < ns; ++k) ss += fmt("{%d,%d},", sfirst[k], scount[k]);
     g(fmt("__device__ const int kx_vchs[%d] = {%s0};", NCH + 1, cs.c_str()));
+    std::string tr;
+    for (int i : tbreac) tr += std::to_string(i) + ",";
+    g("// third-body slot -> reaction: {" + tr + "}");
     g(fmt("__device__ const int2 kx_vslot[%d] = {%s{0,0}};", ns + 1, ss.c_str()));
   }
   bool any_plog = false;
@@ -3724,8 +3737,8 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   o(fmt("float4* const ic = (float4*)(wsm + %d);   // 1/C_k: {signed mantissa, power of two}", L.off_ic));
   o(fmt("float2* const yv = (float2*)(wsm + %d);   // Y_k/W_k", L.off_yv));
   o(fmt("float4* const rf = (float4*)(wsm + %d);   // per reaction {a c R_f, -a c R_r} mantissas", L.off_rf));
-  o(fmt("int4* const re = (int4*)(wsm + %d);       // per reaction {their powers of two, the third-body term's}", L.off_re));
-  o(fmt("float2* const rx = (float2*)(wsm + %d);   // per reaction the third-body term's mantissa", L.off_rx));
+  o(fmt("int2* const re = (int2*)(wsm + %d);       // per reaction their powers of two", L.off_re));
+  o(fmt("float4* const rt = (float4*)(wsm + %d);   // per third-body reaction {its term's mantissa, power of two}", L.off_tb));
   o(fmt("unsigned* const nmk = (unsigned*)(wsm + %d);", L.off_nm));
   o(fmt("const long long nwarp = (long long)gridDim.x * %d;", opt.block / 32));
   o(fmt("for (long long i = (long long)blockIdx.x * %d + wib; i < n; i += nwarp) {", opt.block / 32));
@@ -3963,10 +3976,18 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
     for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
     for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
     o("const int sf = " + sfx + ";");
-    o("kx_df L = lf, fac = kx_mk(1.0f, 0.0f);");
-    o("int sq = sf;");
+    // R_f = mfs 2^ef (signed); for reversible reactions R_r = mr 2^er (signed), and R_f - R_r and the
+    // temperature term from the two by aligned subtraction (two exponentials per reaction)
+    o("int ef;");
+    o(fmt("kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);", shift.c_str()));
+    o("if (lf.hi <= -740.0f) ef -= 2016;");
+    o("const kx_df mfs = sf ? kx_df_neg(mf) : mf;");
+    o(fmt("const kx_df af = kx_df_mul_u(%s, mfs);", aq.c_str()));
     o("kx_df ar = kx_mk(0.0f, 0.0f);");
     o("int er = -100000;");
+    o("int eq = ef;");
+    o("kx_df mq = mfs;   // R_f - R_r = mq 2^eq");
+    c.fp32 += NC * (kDfExp + kDfMul + 10);
     if (d.rev) {
       o("const int sr = " + srx + ";");
       std::string first = d.nre > 0 ? "kx_df_neg(kx_mk(v0.z, v0.w))" : "kx_mk(v0.z, v0.w)";
@@ -3975,41 +3996,29 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
         o(fmt("dl = kx_df_add_u(dl, kx_mk(%sv%d.z, %sv%d.w));", j < d.nre ? "-" : "", j, j < d.nre ? "-" : "", j));
       o("dl = kx_df_add_u(dl, kx_df_mulf(lnPRT, f1.w));   // -dn ln(p_atm/RT), dn of this reaction");
       o("const kx_df lr = kx_df_add_u(lf, dl);");
-      o("{");
-      o("  const bool rv = dl.hi > 0.0f;");
-      o("  if (rv) L = lr;");
-      o("  const kx_df ex = kx_df_exp_n(rv ? kx_df_neg(dl) : dl);");
-      o("  const float pm = sf == sr ? -1.0f : 1.0f;");
-      o("  const kx_df s1 = kx_qts(1.0f, pm * ex.hi);");
-      o("  fac = kx_mk(s1.hi, __fmaf_rn(pm, ex.lo, s1.lo));");
-      o("  if (sf == sr) sq = sf ^ (int)rv;");
-      o("}");
       o(fmt("kx_df mr = kx_df_exp_m(lr.hi <= -740.0f ? kx_df_add(lr, %s) : lr, er);", shift.c_str()));
       o("if (lr.hi <= -740.0f) er -= 2016;");
       o("if (sr) mr = kx_df_neg(mr);");
-      o(fmt("kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(kx_df_mul_u(%s, mr), iT), kx_df_add(dh, kx_mk(f1.w, 0.0f))), er);", aq.c_str()));
+      o("// d/dT at fixed C: a c (R_f dT - R_r (dT - (sum_k nu_k H_k/RT - dn)/T)) (Gibbs-Helmholtz for the second part)");
+      o("{ int et; const kx_df t = kx_df_sub_m(kx_df_mul_u(mfs, dT), ef, "
+        "kx_df_mul_u(mr, kx_df_sub(dT, kx_df_mul(iT, kx_df_add(dh, kx_mk(f1.w, 0.0f))))), er, et);");
+      o(fmt("  kx_acc_add(gTa, sT, kx_df_mul_u(%s, t), et); }", aq.c_str()));
+      if (tb) o("mq = kx_df_sub_m(mfs, ef, mr, er, eq);");
       o(fmt("ar = kx_df_mul_u(kx_df_neg(%s), mr);", aq.c_str()));
-      c.fp32 += NC * ((E - 1) * kDfAdd + kDfAdd + kDfMulf + kDfAdd + 2 * kDfExp + 10 + 4 * kDfMul + kDfAdd + 20);
+      c.fp32 += NC * ((E - 1) * kDfAdd + kDfAdd + kDfMulf + kDfExp + 10 + 5 * kDfMul + 3 * kDfAdd + 8 + 20);
+      if (tb) c.fp32 += NC * (kDfAdd + 8);
+    } else {
+      o(fmt("kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mfs), ef);", aq.c_str()));
+      c.fp32 += NC * (2 * kDfMul + 20);
     }
-    o("int eq;");
-    o("kx_df mq = kx_df_mul_u(kx_df_exp_m(L, eq), fac);   // R_f - R_r = mq 2^eq");
-    o("if (sq) mq = kx_df_neg(mq);");
-    o(fmt("kx_acc_add(gTa, sT, kx_df_mul_u(kx_df_mul_u(%s, dT), mq), eq);", aq.c_str()));
-    o("int ef;");
-    o(fmt("kx_df mf = kx_df_exp_m(lf.hi <= -740.0f ? kx_df_add(lf, %s) : lf, ef);", shift.c_str()));
-    o("if (lf.hi <= -740.0f) ef -= 2016;");
-    o(fmt("const kx_df af = kx_df_mul_u(%s, sf ? kx_df_neg(mf) : mf);", aq.c_str()));
-    c.fp32 += NC * (2 * kDfExp + 4 * kDfMul + 20);
     if (tb) {
       o(d.kind == Kind::ThreeBody ? "const kx_df gX = kx_df_mul_u(av, mq);" : "const kx_df gX = kx_df_mul_u(kx_df_mul_u(av, mq), dX);");
       o("if (e.y >= 0) kx_acc_add(gMa, sM, kx_df_mul_u(kx_mk(f2.x, f2.y), gX), eq);");
-      o("rx[ri] = make_float2(gX.hi, gX.lo);");
+      o(fmt("rt[%d + r] = make_float4(gX.hi, gX.lo, __int_as_float(eq), 0.0f);", tbbase[ci]));
       c.fp32 += NC * (3 * kDfMul + 20);
-    } else {
-      o("rx[ri] = make_float2(0.0f, 0.0f);");
     }
     o("rf[ri] = make_float4(af.hi, af.lo, ar.hi, ar.lo);");
-    o("re[ri] = make_int4(ef, er, eq, 0);");
+    o("re[ri] = make_int2(ef, er);");
     --o.ind;
     o("}");
   }
@@ -4032,7 +4041,7 @@ std::string emit_vjp_wc(const Mechanism& m, const EmitOptions& opt, OpCounts& c,
   o("    const int r = wv & 0x3fff, kind = (wv >> 14) & 3, k = (wv >> 16) & 0x7fff;");
   o("    kx_df mt;");
   o("    int et;");
-  o("    if (kind == 2) { const float2 gx = rx[r]; mt = kx_df_mul_u(kx_mk(gx.x, gx.y), kx_mk(cf, cl)); et = re[r].z; }");
+  o("    if (kind == 2) { const float4 gx = rt[r]; mt = kx_df_mul_u(kx_mk(gx.x, gx.y), kx_mk(cf, cl)); et = __float_as_int(gx.z); }");
   o("    else {");
   o("      const float4 q = rf[r], iq = ic[k];");
   o("      mt = kx_df_mul_u(kind == 0 ? kx_mk(q.x, q.y) : kx_mk(q.z, q.w), kx_mk(iq.x, iq.y));");

@@ -109,6 +109,8 @@ def _vjp_replay(src, mech_obj, af, ar, gx, ic):
     svs = max(mech_obj.n_species + 1, (mech_obj.n_species + 33) // 2)
     chs = _array(src, "kx_vchs")[:-1]
     ws = np.array(_array(src, "kx_vslot")).reshape(-1, 2)[:mech_obj.n_species]
+    tbr = [int(x) for x in re.search(r"// third-body slot -> reaction: \{([0-9,]*)\}", src).group(1).split(",") if x]
+    assert sorted(tbr) == [i for i, r in enumerate(mech_obj.reactions) if r.uses_third_body()]
     nch = len(chs)
     cl = len(tab) // nch
     slots = {}
@@ -118,7 +120,7 @@ def _vjp_replay(src, mech_obj, af, ar, gx, ic):
             w, cf = tab[j * nch + ch]
             if cf != 0.0:
                 r, kind, k = w & 0x3FFF, (w >> 14) & 3, (w >> 16) & 0x7FFF
-                acc += cf * (gx[r] if kind == 2 else (af[r] if kind == 0 else ar[r]) * ic[k])
+                acc += cf * (gx[tbr[r]] if kind == 2 else (af[r] if kind == 0 else ar[r]) * ic[k])
             if w & 0x80000000:
                 assert sl < 2 * svs, "slot outside the species vectors"
                 slots[sl] = acc
