@@ -515,6 +515,39 @@ __device__ __forceinline__ kx_df kx_df_exp_m(kx_df x, int& p) {
   p = k >> 8;
   return kx_df_fma_u(kx_mk(tj.x, tj.y), s, kx_mk(tj.x, tj.y));   // unnormalised: feeds products and sums
 }
+// Element k of a per-thread vector kept in global scratch at stride s.
+template <typename V> struct kx_strided {
+  V* p;
+  long long s;
+  __device__ __forceinline__ V& operator[](int k) const { return p[(long long)k * s]; }
+};
+// nu q for a coefficient nu in {-2, -1, 1, 2}: an exact scaling of both parts
+// (larger coefficients take the float-pair product kx_df_mulf)
+__device__ __forceinline__ kx_df kx_df_scale2(kx_df q, float nu) { return kx_mk(__fmul_rn(q.hi, nu), __fmul_rn(q.lo, nu)); }
+// (a.hi + a.lo) 2^S as a double: one float64 addition, the power of two
+// added to the exponent field (ldexp only when the result leaves the normal
+// range)
+__device__ __forceinline__ double kx_df2d_s(kx_df a, int S) {
+  if (a.hi == 0.0f && a.lo == 0.0f) return 0.0;   // (an unnormalised sum may hold its value in lo alone)
+  if (!(fabsf(a.hi) < KX_INF_F)) return (double)a.hi;
+  const double d = kx_f2d(a.hi) + kx_f2d(a.lo);
+  if (d == 0.0) return 0.0;
+  const int hi = __double2hiint(d);
+  const int E = ((hi >> 20) & 0x7ff) + S;
+  if (E > 0 && E < 0x7ff) return __hiloint2double(hi + (int)((unsigned)S << 20), __double2loint(d));
+  return ldexp(d, S);
+}
+// ln(1 + y) for 0 <= y <= 1 (absolute error about 1e-15)
+__device__ __forceinline__ kx_df kx_df_log1p(kx_df y) {
+  const kx_df s = kx_qts(1.0f, y.hi);
+  return kx_df_log(kx_qts(s.hi, __fadd_rn(s.lo, y.lo)));
+}
+#endif  // KX_TDFR
+)KXPRE";
+
+// Device helpers of the adjoint kernels only (emitted after the common prelude in those kernels,
+// so that the other kernels' sources, and their source hashes, do not carry them).
+const char* kAdjointPrelude = R"KXADJ(
 // m1 2^e1 - m2 2^e2 as a float pair times 2^e, e = max(e1, e2): the term with the smaller power of
 // two is brought to the larger's (dropped below 2^-126 of it), then one float-pair subtraction.  In
 // double-float arithmetic this is as accurate as forming the difference from the log-ratio of the two
@@ -564,35 +597,7 @@ __device__ __forceinline__ void kx_acc_add(kx_df& acc, int& s, kx_df m, int e) {
     acc = kx_df_add_u(acc, kx_mk(__fmul_rn(m.hi, sc), __fmul_rn(m.lo, sc)));
   }
 }
-// Element k of a per-thread vector kept in global scratch at stride s.
-template <typename V> struct kx_strided {
-  V* p;
-  long long s;
-  __device__ __forceinline__ V& operator[](int k) const { return p[(long long)k * s]; }
-};
-// nu q for a coefficient nu in {-2, -1, 1, 2}: an exact scaling of both parts
-// (larger coefficients take the float-pair product kx_df_mulf)
-__device__ __forceinline__ kx_df kx_df_scale2(kx_df q, float nu) { return kx_mk(__fmul_rn(q.hi, nu), __fmul_rn(q.lo, nu)); }
-// (a.hi + a.lo) 2^S as a double: one float64 addition, the power of two
-// added to the exponent field (ldexp only when the result leaves the normal
-// range)
-__device__ __forceinline__ double kx_df2d_s(kx_df a, int S) {
-  if (a.hi == 0.0f && a.lo == 0.0f) return 0.0;   // (an unnormalised sum may hold its value in lo alone)
-  if (!(fabsf(a.hi) < KX_INF_F)) return (double)a.hi;
-  const double d = kx_f2d(a.hi) + kx_f2d(a.lo);
-  if (d == 0.0) return 0.0;
-  const int hi = __double2hiint(d);
-  const int E = ((hi >> 20) & 0x7ff) + S;
-  if (E > 0 && E < 0x7ff) return __hiloint2double(hi + (int)((unsigned)S << 20), __double2loint(d));
-  return ldexp(d, S);
-}
-// ln(1 + y) for 0 <= y <= 1 (absolute error about 1e-15)
-__device__ __forceinline__ kx_df kx_df_log1p(kx_df y) {
-  const kx_df s = kx_qts(1.0f, y.hi);
-  return kx_df_log(kx_qts(s.hi, __fadd_rn(s.lo, y.lo)));
-}
-#endif  // KX_TDFR
-)KXPRE";
+)KXADJ";
 
 namespace {
 
@@ -4183,7 +4188,7 @@ std::string emit_vjp_wc_kernel(const Mechanism& m, const EmitOptions& opt, const
   s << "// mechanism " << m.name << ": " << m.ns << " species, " << m.nr() << " reactions\n";
   s << "#define P_ATM_R " << D(P_ATM / R_U) << "\n";
   s << "#define KX_T64 0\n#define KX_TDF 1\n#define KX_TDFR 1\n";
-  s << kTables << "\n" << kDevicePrelude << "\n";
+  s << kTables << "\n" << kDevicePrelude << "\n" << kAdjointPrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   s << "__device__ unsigned long long kx_bad_first = 0xffffffffffffffffull;\n";
@@ -4264,6 +4269,7 @@ std::string emit_kernel(const Mechanism& m, KernelKind kind, const EmitOptions& 
   s << "#define KX_TDF " << tdf << "\n";
   s << "#define KX_TDFR " << (df_rates || mixed_unrolled || vjp_df || kind == KernelKind::Thermo) << "\n";
   s << kTables << "\n" << kDevicePrelude << "\n";
+  if (vjp_df) s << kAdjointPrelude << "\n";
   s << "extern __shared__ __align__(16) unsigned char kx_dyn[];\n";
   s << globals.o.str();
   // the smallest index of a point outside the domain since the host last read and reset it
