@@ -261,18 +261,24 @@ def run_kx(args):
 
     n = args.points
     path = synth.mechanism_file(MECH, os.path.join(CACHE, "mech"))
-    # the handles of the extra blocks compile in background threads while the main step is timed
-    # (NVRTC is host work; each thread makes this rank's device current before loading)
+    # the kernels of the extra blocks compile in background threads while the main step is timed:
+    # compile-only handles (NVRTC, host work with no CUDA call) fill the kernel cache, and the
+    # handles are loaded onto the device from it after the timed regions (a load into the context
+    # while the end-to-end pipeline runs stalled single steps of it by 30-50 ms)
     import concurrent.futures as cf
     extra = {}
     pool = cf.ThreadPoolExecutor(max_workers=3)
+    extra_opts = {"native": (MECH, {"rates_arith": 1, "tr_mode": 1}), "c1": ("h2o2_9_21", {}), "large": ("large_160_900", {})}
+
+    def load_extra(key):
+        mname, o = extra_opts[key]
+        extra[key].result()
+        return kx.Mechanism(synth.mechanism_file(mname, os.path.join(CACHE, "mech")), cache_dir=CACHE, **o)
     if rank == 0 and not args.no_extra:
-        def load(mname, **o):
-            torch.cuda.set_device(local)
-            return kx.Mechanism(synth.mechanism_file(mname, os.path.join(CACHE, "mech")), cache_dir=CACHE, **o)
-        extra["native"] = pool.submit(load, MECH, rates_arith=1, tr_mode=1)
-        extra["c1"] = pool.submit(load, "h2o2_9_21")
-        extra["large"] = pool.submit(load, "large_160_900")
+        def compile_only(mname, o):
+            kx.Mechanism(synth.mechanism_file(mname, os.path.join(CACHE, "mech")), cache_dir=CACHE, compile_only=1, **o)
+        for key, (mname, o) in extra_opts.items():
+            extra[key] = pool.submit(compile_only, mname, o)
     mech = kx.Mechanism(path, cache_dir=CACHE, maxrreg=args.maxrreg, rates_mode=args.rates_mode,
                         rates_arith=args.rates_arith, tr_layout=args.tr_layout, block=args.block,
                         diff_mode=args.diff_mode, rates_layout=args.rates_layout, rates_group=args.rates_group)
@@ -457,20 +463,21 @@ def run_kx(args):
             # the plain float64 GPU form of the same step: native float64 production rates
             # (rates_arith 1, fully unrolled) and native float64 transport (tr_mode 1); thermo has
             # only its double-float kernel
-            nat = extra["native"].result()
+            nat = load_extra("native")
             nb = step_block(nat, MECH, n, dev, stream, args.steps, args.warmup, "fp64", sm_max, Td, pd, Yd)
             nb["dtype"] = "f64 (thermo f32x2)"
             nb["roofline"] = kernel_roofline(nat, "wdot_fp64", n, nb["kernel_ms"]["wdot_fp64"], sm_max)
             nb["speedup_of_float_pair_step"] = nb["ms_per_step"] / ms
             nb["speedup_of_mixed_step"] = nb["ms_per_step"] / mms
             line["fp64_native"] = nb
-            c1 = extra["c1"].result()
+            c1 = load_extra("c1")
             cb = {"workload": "h2o2_9_21: synthetic 9 species / 21 reactions (4 three-body, 2 Troe), 4096 states, "
                               "T U[300,2500] K, p = 1 atm, Y Dirichlet(0.5); all outputs"}
             for prec in ("fp64", "mixed"):
                 cb[prec] = step_block(c1, "h2o2_9_21", 4096, dev, stream, max(args.steps, 50), args.warmup, prec, sm_max)
             line["c1_h2o2_9_21_4096"] = cb
-            line["large_160_900"] = large_block(extra["large"].result(), dev, stream, args.steps, args.warmup, sm_max)
+            line["large_160_900"] = large_block(load_extra("large"), dev, stream, args.steps, args.warmup, sm_max)
+            line["adjoint"] = adjoint_block(mech, Td, pd, Yd, stream, args.warmup)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         if world == 1 and not args.no_serve:
@@ -835,6 +842,22 @@ def run_sweep_adjoint(args):
             out["rows"].append(row)
         del T, p, Y, v
     print(json.dumps(out), flush=True)
+
+
+def adjoint_block(mech, T, p, Y, stream, W):
+    """The adjoint v^T d wdot/d(T, Y) of the bench mechanism (kx_production_rates_vjp, N(0,1)
+    cotangents) on the first 2^18 and 4096 of the bench states: Mpoints/s of one call, the
+    library's choice of kernel by batch size."""
+    import torch
+    out = {"workload": f"{MECH}: the first n of the bench states, cotangents N(0,1) (seeded)"}
+    for n, key, K in ((1 << 18, "n_262144", 10), (4096, "n_4096", 200)):
+        a = (T[:n], p[:n], Y[:, :n].contiguous(),
+             torch.randn((mech.n_species, n), dtype=torch.float64, device=T.device,
+                         generator=torch.Generator(T.device).manual_seed(1)))
+        g = mech.production_rates_vjp(*a)
+        ms = time_calls(lambda: mech.production_rates_vjp(*a, out=g), K, max(W, 3), stream)
+        out[key] = {"ms": ms, "mpoints_s": n / (ms * 1e-3) / 1e6}
+    return out
 
 
 def large_block(mech, dev, stream, K, W, sm_max, n=1 << 22, name="large_160_900"):
