@@ -1921,8 +1921,6 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
       if (mx) {
         emit_class_mixed_body(o, d, (int)ci, E, c);
       } else {
-        o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
-                   : "  kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
         if (tb) {
           o(fmt("  const int2 e = kx_e%d[r];", (int)ci));
           o("  const float4 f2 = f[2];");
@@ -1940,8 +1938,73 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  }");
           c.fp32 += d.rx.size() * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
         }
+        // Elementary and three-body reactions of a warp whose states all have this reaction's rate
+        // below 2^-40 of their scale's anchor (2^(S+62), the largest rate so far; with the bounding
+        // pass, the state's largest rate) take float32: their contribution is bounded by that rate,
+        // and float32's relative error (~1e-4 with the logarithms' absolute error) leaves an error
+        // below 1e-16 of the largest rate per reaction, three orders under the float-pair path's own
+        // error on the largest rates.  The estimates take the float pairs' high parts.
+        // Falloff and chemically activated reactions estimate their blended ln k in float32 (the
+        // same formulas as the float-pair path below, with the fast exponential and logarithm).
+        const bool fastp = !rop && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
+        if (fastp) {
+          if (fo) {
+            o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+            o("  float lfe = fmaf(f0.z, lnT.hi, fmaf(f1.x, iT.hi, f0.x));   // ln k_inf (float32)");
+            o("  const float lk0e = fmaf(f3.x, lnT.hi, fmaf(f3.z, iT.hi, f2.z));   // ln k_0");
+            o("  const float lpe = lk0e - lfe + __logf(X.hi);   // ln Pr (nan for [X] < 0: no float32 path)");
+            if (d.blend == Blend::Troe) {
+              o("  const float lFc = __logf(f4.x * __expf(Td.hi * f5.x) + f4.z * __expf(Td.hi * f5.z) + __expf(f6.x * iT.hi)) * 0.434294482f;");
+              o("  const float xe = fmaf(lpe, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
+              o("  const float fe = __fdividef(xe, fmaf(-0.14f, xe, fmaf(-1.27f, lFc, 0.75f)));");
+              o("  const float lFe = __fdividef(2.30258509f * lFc, fmaf(fe, fe, 1.0f));   // ln F (Troe)");
+            } else if (d.blend == Blend::Sri) {
+              o("  const float lPe = lpe * 0.434294482f;");
+              o("  const float lFe = f5.z + f6.x * lnT.hi + __fdividef(__logf(f4.x * __expf(f4.z * iT.hi) + __expf(Td.hi * f5.x)), "
+                "fmaf(lPe, lPe, 1.0f));   // ln F (SRI)");
+            } else {
+              o("  const float lFe = 0.0f;");
+            }
+            o("  const float l1e = __logf(1.0f + __expf(-fabsf(lpe)));   // ln(1 + e^-|ln Pr|)");
+            o(d.kind == Kind::Falloff ? "  lfe += (lpe < 0.0f ? lpe - l1e : -l1e) + lFe;   // k_inf Pr/(1+Pr) F"
+                                      : "  lfe = lk0e + lFe - (lpe < 0.0f ? l1e : lpe + l1e);   // k_0 F/(1+Pr)");
+            c.fp32 += d.rx.size() * 40.0;
+          } else {
+            o(d.kconst ? "  float lfe = f0.x;" : "  float lfe = fmaf(f0.z, lnT.hi, fmaf(f1.x, iT.hi, f0.x));   // ln |R_f| (float32)");
+          }
+          for (int j = 0; j < d.nre; ++j) o(fmt("  lfe += v%d.x;", j));
+          o(d.kind == Kind::ThreeBody ? "  const float lxe = __logf(X.hi);   // ln [X] (nan for [X] <= 0: no float32 path)"
+                                      : "  const float lxe = 0.0f;");
+          o("  float lme = lfe + lxe;");
+          if (d.rev) {
+            const int dn = d.npr - d.nre;
+            std::string t = dn == 0 ? std::string("0.0f") : fmt("%s * lnPRT.hi", F(-dn).c_str());
+            for (int j = 0; j < d.nre; ++j) t += fmt(" - v%d.z", j);
+            for (int j = d.nre; j < E; ++j) t += fmt(" + v%d.z", j);
+            o("  const float lre = lfe + (" + t + ");   // ln |R_r| (float32)");
+            o("  lme = fmaxf(lme, lre + lxe);");
+          }
+          std::string sfx = "0", srx = "0";
+          for (int j = 0; j < d.nre; ++j) sfx += fmt(" ^ KX_NEG(k%d)", j);
+          for (int j = d.nre; j < E; ++j) srx += fmt(" ^ KX_NEG(k%d)", j);
+          o("  kx_df q;");
+          o("  if (__all_sync(__activemask(), lme < __fmul_rn(kx_i2f(S + 22), 0.693147182f))) {");
+          o("    const float sl = __fmul_rn(kx_i2f(S), 0.693147182f);   // the rate scaled by 2^-S");
+          o("    float qf = __expf(lfe - sl);");
+          o("    if (anyneg && (" + sfx + ")) qf = -qf;");
+          if (d.rev) {
+            o("    float qr = __expf(lre - sl);");
+            o("    if (anyneg && (" + srx + ")) qr = -qr;");
+            o("    qf -= qr;");
+          }
+          o("    q = kx_mk(qf, 0.0f);");
+          o("  } else {");
+          c.fp32 += d.rx.size() * (6.0 + d.nre + (d.rev ? E + 3 : 0));
+        }
+        o(d.kconst ? "  kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
+                   : "  kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
         if (fo) {
-          o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+          if (!fastp) o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
           o("  const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
           o("  kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
           o("  if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
@@ -2020,11 +2083,12 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, Sr, __fmul_rn(kx_i2f(Sr), 0.693147182f)), fac);");
           c.fp32 += d.rx.size() * 4;
         } else {
+          const std::string qd = fastp ? "q" : "kx_df q";
           if (bounded) {
-            o("  kx_df q = kx_df_mul_u(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S (the products and sums after it take hi + lo as is)");
+            o("  " + qd + " = kx_df_mul_u(kx_df_exp_sc(L, S, lnSf), fac);   // |R| 2^-S (the products and sums after it take hi + lo as is)");
           } else {
           o("  int ex;");
-          o("  kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex (products and sums after it take hi + lo as is)");
+          o("  " + qd + " = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex (products and sums after it take hi + lo as is)");
           o("  if (ex > S + 96) {   // the state's first rate, or one 2^34 above its scale's anchor: raise the scale");
           o("    const int d = S - (ex - 62);");
           o("    const float f = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f;");
@@ -2038,6 +2102,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           }
         }
         o("  if (sf) q = kx_df_neg(q);");
+        if (fastp) o("  }");
         if (d.kind == Kind::ThreeBody) { o("  q = kx_df_mul_u(q, X);"); c.fp32 += d.rx.size() * kDfMul; }
       }
       if (rop) {
