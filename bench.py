@@ -352,6 +352,10 @@ def run_kx(args):
         for q in ss:
             stream.wait_stream(q)
 
+    # the background compiles of the extra blocks (NVRTC on many host threads) finish first: the
+    # end-to-end loop needs its one host thread to keep the copy and launch queues fed
+    for f in extra.values():
+        f.result()
     for _ in range(args.warmup + 2):   # two more than the device loop: the first host-link steps run slow
         e2e_step()
     barrier()
