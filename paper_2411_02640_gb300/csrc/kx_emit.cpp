@@ -2783,13 +2783,31 @@ void emit_thermo(Out& o, const Mechanism& m, OpCounts& c) {
 //        scaled by log2(e) so each property is one exp2.
 double wilke_a(const Mechanism& m, int k, int j) { return 1.0 / std::sqrt(8.0 * (1.0 + m.W[k] / m.W[j])); }
 
-// p(L) = sum c_n L^n re-expanded about L0: d_m = sum_{n>=m} C(n,m) c_n L0^(n-m)
+// Double-double host arithmetic from error-free transformations (std::fma is exact IEEE arithmetic
+// on every host), so that the emitted constants are the same bits on every platform: long double is
+// 80-bit on x86-64 and 128-bit on aarch64.
+struct HostDD { double hi, lo; };
+HostDD hdd_norm(double a, double b) { const double s = a + b; return {s, b - (s - a)}; }
+HostDD hdd_add(HostDD a, HostDD b) {
+  const double s = a.hi + b.hi, bb = s - a.hi;
+  const double e = (a.hi - (s - bb)) + (b.hi - bb);
+  return hdd_norm(s, e + a.lo + b.lo);
+}
+HostDD hdd_mul(HostDD a, HostDD b) {
+  const double p = a.hi * b.hi;
+  return hdd_norm(p, std::fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi));
+}
+
+// p(L) = sum c_n L^n re-expanded about L0: d_m = sum_{n>=m} C(n,m) c_n L0^(n-m), in double-double
 void shift_poly(const double* cf, double L0, double scale, double out[5]) {
   static const double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  HostDD pw[5] = {{1.0, 0.0}};
+  for (int k = 1; k < 5; ++k) pw[k] = hdd_mul(pw[k - 1], {L0, 0.0});
   for (int mm = 0; mm < 5; ++mm) {
-    long double d = 0;
-    for (int n = mm; n < 5; ++n) d += (long double)binom[n][mm] * cf[n] * std::pow((long double)L0, n - mm);
-    out[mm] = (double)(d * scale);
+    HostDD d = {0.0, 0.0};
+    for (int n = mm; n < 5; ++n) d = hdd_add(d, hdd_mul(hdd_mul({binom[n][mm], 0.0}, {cf[n], 0.0}), pw[n - mm]));
+    d = hdd_mul(d, {scale, 0.0});
+    out[mm] = d.hi + d.lo;
   }
 }
 
@@ -2807,9 +2825,10 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
   else md = {TrMode::F64, "double", "double"};
   // direct fits (of eta, lambda, 1/D themselves) are evaluated without exponentials and, in every
   // arithmetic, in L = ln T - L0: their monomial form in ln T is badly conditioned (condition numbers
-  // up to ~1e6 for 1/D_kj); the re-expansion is computed in long double
+  // up to ~1e6 for 1/D_kj); the re-expansion is computed in double-double.  L0 = ln sqrt(300 * 3000),
+  // correctly rounded, as a literal (no host libm in the emitted constants)
   const bool direct = m.fit_direct;
-  const double L0 = (md.kind == TrMode::F64 && !direct) ? 0.0 : 0.5 * (std::log(300.0) + std::log(3000.0));
+  const double L0 = (md.kind == TrMode::F64 && !direct) ? 0.0 : 6.855075021153224;
   const double SC = (md.kind == TrMode::F32 && !direct) ? 1.4426950408889634 : 1.0;   // exp2 form for float32
   const int B = opt.block;
   // float64-accurate viscosity keeps two vectors per species (X, v = 1/u) in shared memory
@@ -2913,8 +2932,8 @@ void emit_transport(Out& o, Out& g, const Mechanism& m, const EmitOptions& opt, 
       }
       sqwp += lit(std::sqrt(m.W[k])) + ",";
       isqwp += lit(1.0 / std::sqrt(m.W[k])) + ",";
-      w4 += lit(std::pow(m.W[k], 0.25)) + ",";
-      iw4 += lit(std::pow(m.W[k], -0.25)) + ",";
+      w4 += lit(std::sqrt(std::sqrt(m.W[k]))) + ",";   // correctly rounded square roots: the same bits on every host
+      iw4 += lit(1.0 / std::sqrt(std::sqrt(m.W[k]))) + ",";
       w += D(m.W[k]) + ",";
       iw += D(1.0 / m.W[k]) + ",";
       sqw += D(std::sqrt(m.W[k])) + ",";
