@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 MECH = "gri_53_325"
 POINTS = 1 << 20
-E2E_CHUNK = 1 << 18     # states per chunk of the end-to-end host pipeline
+E2E_CHUNK = 1 << 19     # states per chunk of the end-to-end host pipeline (measured: 2^19 19.1-19.6 ms per 2^20-state step, 2^18 19.9)
 METRIC = "Mpoints/s wdot+thermo+transport (53sp/325rxn)"
 CACHE = os.environ.get("KX_CACHE_DIR", os.path.join(ROOT, ".kxcache"))
 

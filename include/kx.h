@@ -160,7 +160,14 @@ kx_status kx_mechanism_info(kx_handle h, int* n_species, int* n_reactions, doubl
 
 /* Net production rates wdot[N_s][ld] (Sec. A.2: Eq. (arrhenius), third-body
  * and falloff modifiers Eq. (c_i) and (blend), Eq. (K_p), Eq. (r_i) and the
- * stoichiometric sum wdot_k = sum_i nu_ki R_i). */
+ * stoichiometric sum wdot_k = sum_i nu_ki R_i).  KX_FP64 with the default
+ * double-float kernel evaluates a reaction in float32 when, for every state of
+ * a warp (32 consecutive states), its rate is below 2^-40 of that state's
+ * largest rate, where float32's error leaves the result far inside the
+ * float64 bar: a state's results can therefore differ, within the bar (~1e-11
+ * of the per-point scale), with the states it shares a warp with (a call on a
+ * sub-range that does not start at a multiple of 32 states, or a batch mixed
+ * with other states); the same batch gives the same bits. */
 kx_status kx_production_rates(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                               double* wdot, int64_t n, kx_precision precision, void* stream);
 

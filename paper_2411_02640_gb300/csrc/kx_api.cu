@@ -824,13 +824,22 @@ kx_status kx_evaluate_host(kx_handle h, const double* T, const double* p, const 
   cudaEvent_t* in_done = ev;          // inputs of the slot copied in
   cudaEvent_t* comp_done = ev + 2;    // kernels of the slot finished
   cudaEvent_t* out_done = ev + 4;     // outputs of the slot copied out
-  // chunk bounds: a first chunk of a quarter slot (the copy-in that nothing hides is short; its
-  // kernels share the GPU with the next chunk's, which run on the other stream), then full slots
+  // chunk bounds: a first and a last chunk of about a quarter slot (the copy-in and the copy-out
+  // that nothing hides are short; their kernels share the GPU with the neighbouring chunk's, which
+  // run on the other stream), full slots between them.  Every bound is a multiple of 256 states, so
+  // that each warp of a chunk holds the same states as in one call over all n: the float-pair rate
+  // kernel's float32 path is chosen per warp
   std::vector<int64_t> at{0};
   {
     int64_t pos = 0;
-    if (n > 2 * c && c >= 1024) at.push_back(pos = c / 4 / 256 * 256);
-    while (pos < n) at.push_back(pos = std::min(n, pos + c));
+    const bool ends = n > 2 * c && c >= 1024;
+    const int64_t q = c / 4 / 256 * 256;
+    if (ends) at.push_back(pos = q);
+    while (pos < n) {
+      int64_t next = std::min(n, pos + c);
+      if (ends && next == n && (n - q) / 256 * 256 > pos) next = (n - q) / 256 * 256;
+      at.push_back(pos = next);
+    }
   }
   const int64_t nchunks = (int64_t)at.size() - 1;
   auto slot = [&](int64_t i, double** dT, double** dp, double** dY, double** dw, double** dcp, double** dh, double** dmu,

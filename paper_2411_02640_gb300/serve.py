@@ -16,14 +16,14 @@ mechanisms.  A scheduler thread
   * completes a request's Future when its batch's event has fired, and
     records its latency (submit to completion).
 
-Every state's computation is independent of the others in its batch.  The
-mixed-precision rate kernel and the transport kernels run the same
+The mixed-precision rate kernel and the transport kernels run the same
 instruction sequence for a state wherever it lands, so those results are
 bit-identical alone and in the mix; the float64-accurate production rates
 use the warp-cooperative kernel for batches below the thread-per-state
-kernel's resident capacity and the thread-per-state kernel above it, so a
-request's result alone and in the mix agree within the float64 bar (about
-1e-11 of the per-point scale), not bit for bit.
+kernel's resident capacity and the thread-per-state kernel above it, and
+the latter evaluates a reaction in float32 when it is negligible for every
+state of a warp, so a request's result alone and in the mix agree within
+the float64 bar (about 1e-11 of the per-point scale), not bit for bit.
 """
 from __future__ import annotations
 
