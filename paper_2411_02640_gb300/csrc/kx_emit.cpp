@@ -3464,6 +3464,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
   o("  }");
   o("}");
   o("const bool grpneg = __any_sync(0xffffffffu, neg);");
+  if (G == 1) o("int emax = -32768;   // the largest power of two of the rates this lane has formed");
   o("__syncwarp();");
   c.fp32 += ns * (12 + kDfFma) + kDfDiv + kDfLog + ns * (45 + 2 * kDfAdd + 6 * kDfFma + kDfAdd);
 
@@ -3506,8 +3507,6 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
       o(fmt("const int ri = %s;", comp("c", E).c_str()));
       o(fmt("const float4* f = kx_f%d + %d * r;", (int)ci, NF));
       o("const float4 f0 = f[0], f1 = f[1];");
-      o(d.kconst ? "kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
-                 : "kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
       if (tb) {
         o(fmt("const int2 e = kx_e%d[r];", (int)ci));
         o("const float4 f2 = f[2];");
@@ -3525,8 +3524,73 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         o("}");
         c.fp32 += NC * (kDfFma + kDfMul + 3 * (kDfFma + kDfMul + 12));
       }
+      // The float32 path of the thread-per-state kernel, per round: one state per warp (G = 1), so
+      // the state's running largest power of two is a warp max of the lanes' own; a round whose
+      // reactions all have both rates below 2^-40 of it takes float32 (the rate scaled by 2^-emx,
+      // stored with the power of two emx)
+      const bool fastp = G == 1 && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
+      const int dnf = d.npr - d.nre;
+      auto negbit0 = [&](int j) { return fmt("((nmg[k%d >> 5] >> (k%d & 31)) & 1)", j, j); };
+      if (fastp) {
+        if (fo) {
+          o("const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+          o("float lfe = fmaf(f0.z, lnT.hi, fmaf(f1.x, iT.hi, f0.x));   // ln k_inf (float32)");
+          o("const float lk0e = fmaf(f3.x, lnT.hi, fmaf(f3.z, iT.hi, f2.z));");
+          o("const float lpe = lk0e - lfe + __logf(X.hi);");
+          if (d.blend == Blend::Troe) {
+            o("const float lFc = __logf(f4.x * __expf(Td.hi * f5.x) + f4.z * __expf(Td.hi * f5.z) + __expf(f6.x * iT.hi)) * 0.434294482f;");
+            o("const float xe = fmaf(lpe, 0.434294482f, fmaf(-0.67f, lFc, -0.4f));");
+            o("const float fe = __fdividef(xe, fmaf(-0.14f, xe, fmaf(-1.27f, lFc, 0.75f)));");
+            o("const float lFe = __fdividef(2.30258509f * lFc, fmaf(fe, fe, 1.0f));");
+          } else if (d.blend == Blend::Sri) {
+            o("const float lPe = lpe * 0.434294482f;");
+            o("const float lFe = f5.z + f6.x * lnT.hi + __fdividef(__logf(f4.x * __expf(f4.z * iT.hi) + __expf(Td.hi * f5.x)), "
+              "fmaf(lPe, lPe, 1.0f));");
+          } else {
+            o("const float lFe = 0.0f;");
+          }
+          o("const float l1e = __logf(1.0f + __expf(-fabsf(lpe)));");
+          o(d.kind == Kind::Falloff ? "lfe += (lpe < 0.0f ? lpe - l1e : -l1e) + lFe;"
+                                    : "lfe = lk0e + lFe - (lpe < 0.0f ? l1e : lpe + l1e);");
+        } else {
+          o(d.kconst ? "float lfe = f0.x;" : "float lfe = fmaf(f0.z, lnT.hi, fmaf(f1.x, iT.hi, f0.x));");
+        }
+        for (int j = 0; j < d.nre; ++j) o(fmt("lfe += v%d.x;", j));
+        o(d.kind == Kind::ThreeBody ? "const float lxe = __logf(X.hi);" : "const float lxe = 0.0f;");
+        o("float lme = lfe + lxe;");
+        std::string t = merged ? std::string("f1.w * lnPRT.hi") : (dnf == 0 ? std::string("0.0f") : fmt("%s * lnPRT.hi", F(-dnf).c_str()));
+        for (int j = 0; j < d.nre; ++j) t += fmt(" - v%d.z", j);
+        for (int j = d.nre; j < E; ++j) t += fmt(" + v%d.z", j);
+        if (d.rev) {
+          o("const float lre = lfe + (" + t + ");");
+          o("lme = fmaxf(lme, lre + lxe);");
+        }
+        std::string sfe = "0", sre = "0";
+        if (sgn) {
+          for (int j = 0; j < d.nre; ++j) sfe += " ^ " + negbit0(j);
+          for (int j = d.nre; j < E; ++j) sre += " ^ " + negbit0(j);
+        }
+        o("const int emx = __reduce_max_sync(__activemask(), emax);");
+        o("kx_df q;");
+        o("int ex;");
+        o("if (__all_sync(__activemask(), lme < __fmul_rn(kx_i2f(emx - 40), 0.693147182f))) {");
+        o("  const float sl = __fmul_rn(kx_i2f(emx), 0.693147182f);");
+        o("  float qf = __expf(lfe - sl);");
+        o("  if (" + sfe + ") qf = -qf;");
+        if (d.rev) {
+          o("  float qr = __expf(lre - sl);");
+          o("  if (" + sre + ") qr = -qr;");
+          o("  qf -= qr;");
+        }
+        o("  q = kx_mk(qf, 0.0f);");
+        o("  ex = emx;");
+        o("} else {");
+        c.fp32 += NC * (8.0 + d.nre + (d.rev ? E : 0) + (fo ? 40 : 0));
+      }
+      o(d.kconst ? "kx_df lk = kx_mk(f0.x, f0.y);   // k = A"
+                 : "kx_df lk = kx_df_fma_u(kx_mk(f0.z, f0.w), lnT, kx_df_fma_u(kx_mk(f1.x, f1.y), iT, kx_mk(f0.x, f0.y)));");
       if (fo) {
-        o("const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
+        if (!fastp) o("const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
         o("const kx_df lk0 = kx_df_fma(kx_mk(f3.x, f3.y), lnT, kx_df_fma(kx_mk(f3.z, f3.w), iT, kx_mk(f2.z, f2.w)));");
         o("kx_df lnPr = kx_df_add(kx_df_sub(lk0, lk), kx_df_log(X));");
         o("if (!(lnPr.hi > -690.775528f)) lnPr = kx_mk(-690.775528f, 0.0f);");
@@ -3606,9 +3670,16 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
         c.fp32 += (real_e - NC) * kDfAdd + NC * (kDfAdd + kDfMulf + kDfAdd + kDfExp + 10);
         (void)dn;
       }
-      o("int ex;");
-      o("kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex");
-      o("if (sf) q = kx_df_neg(q);");
+      if (fastp) {
+        o("q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex");
+        o("if (sf) q = kx_df_neg(q);");
+        o("emax = max(emax, ex);");
+        o("}");
+      } else {
+        o("int ex;");
+        o("kx_df q = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex");
+        o("if (sf) q = kx_df_neg(q);");
+      }
       if (d.kind == Kind::ThreeBody) { o("q = kx_df_mul_u(q, X);"); c.fp32 += NC * kDfMul; }
       o(fmt("qm[%d * g + ri] = make_float2(q.hi, q.lo);", nr));
       o(fmt("qe[%d * g + ri] = (short)ex;", nr));
