@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -257,8 +258,15 @@ kx_status launch(kx_mech* h, const char* name, void** args, int64_t n, void* str
   if (s != KX_OK) return s;
   const int spb = k->states_per_block > 0 ? k->states_per_block : k->eopt.block;
   const int64_t want = (n + spb - 1) / spb;
-  // warp-cooperative kernels: one resident wave, each warp looping over groups of states
-  const int grid = (int)std::min<int64_t>(want, (int64_t)k->max_blocks * (k->states_per_block > 0 ? 1 : 4));
+  // warp-cooperative kernels: one resident wave, each warp looping over groups of states (their
+  // per-warp shared-memory slices); one-state-per-thread kernels: one state per thread, the block
+  // scheduler balancing blocks of unequal cost (hot states against cold ones, whose reactions mostly
+  // take the rate kernels' float32 path).  Measured on 53/325 against a grid of four resident waves
+  // striding over the batch: production rates 5.68 -> 5.40 ms per 2^20 states and 35.1 -> 23.0 ms
+  // per 2^22 (the strided grid's blocks accumulated the imbalance over 13 states per thread);
+  // thermo and transport 0-10 % faster.
+  const int64_t cap = k->states_per_block > 0 ? (int64_t)k->max_blocks : (int64_t)INT_MAX;
+  const int grid = (int)std::min<int64_t>(want, cap);
   cudaError_t e =
       cudaLaunchKernel((const void*)k->fn, dim3(grid), dim3(k->eopt.block), args, k->smem, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
