@@ -143,6 +143,12 @@ typedef struct {
                          mechanisms whose warp slice exceeds 50 KB keep one thread per state
                          under 0 and are refused under 2).  The two agree to ~1e-10 of each
                          entry's term scale, not bit for bit. */
+  int rates_negligible; /* double-float KX_FP64 production rates: 0 (default) a reaction whose rate
+                         is below 2^-40 of its state's largest, for every state of a warp, is
+                         evaluated in float32 (its error is far inside the per-point bar, but a
+                         species all of whose reactions are that small gets wdot_k to ~1e-4 of
+                         itself); 1 every reaction in float pairs (wdot_k to ~1e-11 of itself
+                         where no cancellation intervenes: for finite differences of the rates) */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 
@@ -167,7 +173,10 @@ kx_status kx_mechanism_info(kx_handle h, int* n_species, int* n_reactions, doubl
  * float64 bar: a state's results can therefore differ, within the bar (~1e-11
  * of the per-point scale), with the states it shares a warp with (a call on a
  * sub-range that does not start at a multiple of 32 states, or a batch mixed
- * with other states); the same batch gives the same bits. */
+ * with other states); the same batch gives the same bits.  A species that
+ * only such reactions produce or consume gets its wdot_k to ~1e-4 of itself
+ * (still ~1e-16 of the per-point scale); kx_options.rates_negligible = 1
+ * evaluates every reaction in float pairs (for finite differences). */
 kx_status kx_production_rates(kx_handle h, const double* T, const double* p, const double* Y, int64_t ld,
                               double* wdot, int64_t n, kx_precision precision, void* stream);
 

@@ -346,6 +346,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
   if (h->opt.rates_layout < 0 || h->opt.rates_layout > 2) return fail(KX_ERR_ARG, "rates_layout must be 0, 1 or 2");
   if (h->opt.vjp_form < 0 || h->opt.vjp_form > 1) return fail(KX_ERR_ARG, "vjp_form must be 0 or 1");
   if (h->opt.vjp_layout < 0 || h->opt.vjp_layout > 2) return fail(KX_ERR_ARG, "vjp_layout must be 0, 1 or 2");
+  if (h->opt.rates_negligible < 0 || h->opt.rates_negligible > 1) return fail(KX_ERR_ARG, "rates_negligible must be 0 or 1");
   if (h->opt.rates_group < 0 || h->opt.rates_group > 32 || (h->opt.rates_group & (h->opt.rates_group - 1)))
     return fail(KX_ERR_ARG, "rates_group must be 0 or a power of two up to 32");
   h->cache_dir = h->opt.cache_dir ? h->opt.cache_dir : default_cache_dir();
@@ -385,6 +386,7 @@ kx_status kx_load_mechanism(const char* path, const kx_options* opt, kx_handle* 
     k->eopt.rates_group = h->opt.rates_group;
     k->eopt.vjp_form = h->opt.vjp_form;
     k->eopt.vjp_layout = h->opt.vjp_layout;
+    k->eopt.rates_negligible = h->opt.rates_negligible;
     const bool vjp_wc_spec = std::strcmp(sp.name, "vjp_wc") == 0;
     if (vjp_wc_spec) {
       // the warp-cooperative adjoint beside the default one, for small batches

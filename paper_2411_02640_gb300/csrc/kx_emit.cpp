@@ -1946,7 +1946,7 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
         // error on the largest rates.  The estimates take the float pairs' high parts.
         // Falloff and chemically activated reactions estimate their blended ln k in float32 (the
         // same formulas as the float-pair path below, with the fast exponential and logarithm).
-        const bool fastp = !rop && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
+        const bool fastp = !rop && opt.rates_negligible == 0 && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
         if (fastp) {
           if (fo) {
             o("  const float4 f3 = f[3], f4 = f[4], f5 = f[5], f6 = f[6];");
@@ -3528,7 +3528,7 @@ std::string emit_wdot_wc(const Mechanism& m, const EmitOptions& opt, const std::
       // the state's running largest power of two is a warp max of the lanes' own; a round whose
       // reactions all have both rates below 2^-40 of it takes float32 (the rate scaled by 2^-emx,
       // stored with the power of two emx)
-      const bool fastp = G == 1 && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
+      const bool fastp = G == 1 && opt.rates_negligible == 0 && (d.kind == Kind::Elementary || d.kind == Kind::ThreeBody || fo);
       const int dnf = d.npr - d.nre;
       auto negbit0 = [&](int j) { return fmt("((nmg[k%d >> 5] >> (k%d & 31)) & 1)", j, j); };
       if (fastp) {

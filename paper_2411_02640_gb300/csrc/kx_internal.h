@@ -80,6 +80,7 @@ struct EmitOptions {
   int vjp_form = 0;         // double-float adjoint, d/dC_k: 0 rate mantissa times a per-state reciprocal
                             // concentration, 1 one log-space exponential per entry
   int vjp_layout = 0;       // double-float adjoint: 0/1 thread per state, 2 warp-cooperative
+  int rates_negligible = 0; // double-float rates: 0 float32 for reactions negligible in every state of a warp, 1 never
 };
 
 // Launch shape of the warp-cooperative production-rate kernel.

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("rates_arith", ctypes.c_int), ("tr_layout", ctypes.c_int), ("maxrreg", ctypes.c_int),
                 ("block", ctypes.c_int), ("lazy", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("libmath", ctypes.c_int), ("compile_only", ctypes.c_int), ("rates_layout", ctypes.c_int),
-                ("rates_group", ctypes.c_int), ("vjp_form", ctypes.c_int), ("vjp_layout", ctypes.c_int), ("cache_dir", ctypes.c_char_p)]
+                ("rates_group", ctypes.c_int), ("vjp_form", ctypes.c_int), ("vjp_layout", ctypes.c_int), ("rates_negligible", ctypes.c_int),
+                ("cache_dir", ctypes.c_char_p)]
 
 
 def library_path() -> str:

@@ -54,6 +54,7 @@ def test_error_codes(tmp_path):
     assert _load(path, block=100)[0] == 4                             # KX_ERR_ARG
     assert b"multiple of 32" in kx.lib().kx_last_error()
     assert _load(path, kc_mode=7)[0] == 4
+    assert _load(path, rates_negligible=2)[0] == 4
 
 
 @pytest.mark.parametrize("name", ["h2o2_9_21"])
