@@ -129,3 +129,14 @@ def test_host_side_argument_checks_of_the_status_and_no_alloc_calls(tmp_path):
         assert L.kx_production_rates_noalloc(*args) == 0                              # n = 0: no-op
     finally:
         L.kx_free_mechanism(h)
+
+
+def test_options_struct_matches_the_header():
+    """The ctypes mirror of kx_options has the header's fields in the header's order and types
+    (a field added on one side only would shift every later option)."""
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kx.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} kx_options;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(const char\*|int)\s+(\w+);", body)
+    want = [(n, ctypes.c_char_p if t == "const char*" else ctypes.c_int) for t, n in fields]
+    assert [(n, t) for n, t in kx.Options._fields_] == want
