@@ -73,7 +73,9 @@ typedef enum {
                     float32's exponent range, run on the float32 pipe -- and
                     the production rates are formed in log space and
                     accumulated in float pairs under a per-state power-of-two
-                    scale; kx_options.rates_arith = 1 selects native float64
+                    scale, reactions negligible for every state of a warp in
+                    float32 (see kx_production_rates); kx_options.rates_arith
+                    = 1 selects native float64
                     production rates and rates of progress, tr_mode = 1
                     native float64 transport.  kx_thermo is always
                     double-float. */
@@ -328,8 +330,10 @@ int64_t kx_evaluate_host_bytes_per_state(kx_handle h, int outputs);
  * own); kx_free_mechanism releases them.  Chunks hold a whole number of
  * waves of the launched kernels (states that fill every SM's resident
  * blocks once) where the chunk bound allows one; when there are more than
- * two, the first is a quarter chunk, so that the copy-in nothing overlaps
- * is short.  T, p [n], Y [N_s][ld] are
+ * two, the first and the last are about a quarter chunk, so that the
+ * copy-in and the copy-out that nothing overlaps are short; every chunk
+ * starts at a multiple of 256 states, so the results are bit-identical to
+ * the single calls on the whole batch.  T, p [n], Y [N_s][ld] are
  * host inputs; wdot [N_s][ldo], cp, hmass, mu, lambda [n] and Dk [N_s][ldo]
  * are host outputs, those not selected by `outputs` may be NULL.
  * `workspace` is caller-owned device memory of `workspace_bytes`; the chunk
