@@ -15,8 +15,19 @@
 //    ln k_f (Eq. (k_f)), the falloff blend, ln |R_f| and the log ratio
 //    ln(|R_r|/|R_f|) = sum nu mu - dn ln(p_atm/(R T)) (Eq. (K_p)); the net
 //    rate from the larger rate and that ratio; wdot accumulated in float
-//    pairs under a per-state power-of-two scale.  The tables make the
-//    compile time independent of the mechanism's size.
+//    pairs under a per-state power-of-two scale.  A reaction whose rates
+//    are below 2^-40 of the scale's anchor for every state of a warp (a
+//    warp vote on float32 estimates) is evaluated in float32 instead: its
+//    error, bounded by its size, stays orders of magnitude under the
+//    float-pair path's own.  The tables make the compile time independent
+//    of the mechanism's size.
+//  * Production rates, warp-cooperative (emit_wdot_wc; small batches): the
+//    lanes of a warp share a state, species vectors and per-reaction rates
+//    in shared memory, wdot gathered species-major; the same float32 path
+//    per round of reactions.
+//  * Adjoint (emit_vjp_df one thread per state, emit_vjp_wc one warp per
+//    state): v^T d wdot/d(T, Y) in double-float arithmetic, each term a
+//    float-pair mantissa times a power of two under its own running scale.
 //  * Production rates, native float64 (rates_arith = 1, emit_rates64): one
 //    thread per point, fully unrolled, constants as immediates (the paper's
 //    per-thread model, Sec. 2.4): one ln T and 1/T shared by every
