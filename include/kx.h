@@ -149,8 +149,9 @@ typedef struct {
                          is below 2^-40 of its state's largest, for every state of a warp, is
                          evaluated in float32 (its error is far inside the per-point bar, but a
                          species all of whose reactions are that small gets wdot_k to ~1e-4 of
-                         itself); 1 every reaction in float pairs (wdot_k to ~1e-11 of itself
-                         where no cancellation intervenes: for finite differences of the rates) */
+                         itself); 1 every reaction in float pairs (wdot_k to ~1e-11 of the
+                         species' own gross rate, for the species within 1e-40 of their state's
+                         largest rate: for finite differences of the rates) */
   const char* cache_dir; /* directory for compiled kernels; NULL = $KX_CACHE_DIR or ~/.cache/kx */
 } kx_options;
 

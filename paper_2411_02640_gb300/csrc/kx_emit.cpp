@@ -2101,11 +2101,14 @@ void emit_rates_class_df(Out& o, Out& g, const Mechanism& m, const EmitOptions& 
           o("  int ex;");
           o("  " + qd + " = kx_df_mul_u(kx_df_exp_m(L, ex), fac);   // |R| = q 2^ex (products and sums after it take hi + lo as is)");
           o("  if (ex > S + 96) {   // the state's first rate, or one 2^34 above its scale's anchor: raise the scale");
-          o("    const int d = S - (ex - 62);");
-          o("    const float f = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f;");
-          o(fmt("    for (int k = 0; k < %d; ++k) w[k] = kx_mk(__fmul_rn(w[k].hi, f), __fmul_rn(w[k].lo, f));", ns));
-          for (int j = 0; j < E; ++j) o(fmt("    wl%d = kx_mk(__fmul_rn(wl%d.hi, f), __fmul_rn(wl%d.lo, f));", j, j, j));
-          o("    qp = kx_mk(__fmul_rn(qp.hi, f), __fmul_rn(qp.lo, f));");
+          o("    // 2^d in two exact steps (each at least 2^-126): sums still representable after a jump of more");
+          o("    // than 2^126 keep their value");
+          o("    const int d = S - (ex - 62), d1 = max(d, -126), d2 = d - d1;");
+          o("    const float f1 = __int_as_float((d1 + 127) << 23), f2 = d2 >= -126 ? __int_as_float((d2 + 127) << 23) : 0.0f;");
+          o(fmt("    for (int k = 0; k < %d; ++k) w[k] = kx_mk(__fmul_rn(__fmul_rn(w[k].hi, f1), f2), __fmul_rn(__fmul_rn(w[k].lo, f1), f2));", ns));
+          for (int j = 0; j < E; ++j)
+            o(fmt("    wl%d = kx_mk(__fmul_rn(__fmul_rn(wl%d.hi, f1), f2), __fmul_rn(__fmul_rn(wl%d.lo, f1), f2));", j, j, j));
+          o("    qp = kx_mk(__fmul_rn(__fmul_rn(qp.hi, f1), f2), __fmul_rn(__fmul_rn(qp.lo, f1), f2));");
           o("    S = ex - 62;");
           o("  }");
           o("  { const int d = ex - S; const float sc = d >= -126 ? __int_as_float((d + 127) << 23) : 0.0f; "
