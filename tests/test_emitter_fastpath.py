@@ -40,3 +40,12 @@ def test_rates_negligible_removes_the_path(tmp_path, kernel, layout):
 def test_rates_of_progress_never_take_it(tmp_path):
     src = _src(tmp_path, "rop_fp64")
     assert "lme <" not in src and "__expf(lfe" not in src
+
+
+def test_running_scale_rescales_in_two_steps(tmp_path):
+    """The thread-per-state kernel's running scale applies a rescale's power of two as two factors
+    of at least 2^-126 each (a single factor is zero below 2^-126 and zeroed sums that would
+    still be representable after a jump of more than 2^126)."""
+    src = _src(tmp_path, "wdot_fp64", rates_layout=1)
+    assert "d1 = max(d, -126), d2 = d - d1" in src
+    assert re.search(r"w\[k\] = kx_mk\(__fmul_rn\(__fmul_rn\(w\[k\]\.hi, f1\), f2\)", src)
